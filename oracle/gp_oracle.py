@@ -1,0 +1,398 @@
+"""FP64 CPU oracle for matrix-free GP inference (test infrastructure only).
+
+This module is test infrastructure. Only ``tests/``, ``__graft_entry__.smoke()``
+and the CPU-baseline leg of ``bench.py`` may import it; the CUDA library never
+does, and it shares no code, table or constant with the CUDA path. Inputs are
+the float32 arrays handed to the GPU, promoted to float64, so input rounding is
+not counted as error.
+
+What it computes, in the paper's notation (Sec. 2 Background):
+
+* ``K_y = K_ff + sigma_n^2 I`` and the product ``K_y V`` (the fused product of
+  Sec. 3 "GPU backends" and Table 3, here written out as an explicit matrix).
+* the exact solve ``K_y^{-1} B`` by Cholesky (Sec. 2 "Exact inference"),
+* ``log|K_y|`` and the log marginal likelihood
+  ``log p(y|X) = -1/2 [y^T K_y^{-1} y + log|K_y| + N log 2 pi]`` (Sec. 2),
+* the exact hyperparameter gradient ``1/2 tr((a a^T - K_y^{-1}) dK/dtheta)``
+  (the quantity the paper approximates by 2P+1 finite-difference fits, Sec. 5),
+* textbook unpreconditioned CG from x0 = 0 (Sec. 3 "Inference", Sec. 5 "our
+  simpler CG loop") with its coefficients, the Lanczos tridiagonal they define,
+  and the stochastic Lanczos log-determinant over Rademacher probes
+  (Sec. 3 "CG with stochastic Lanczos log-determinant", Sec. 4.3 probes),
+* the probe-conditioned targets of the two stochastic estimators (the values
+  the estimators converge to for the given probes as the Lanczos steps grow).
+
+Readings of points the paper leaves open (the paper names the kernels in
+Sec. 3 "Kernels" but prints no formula):
+
+* RBF: ``k = s^2 exp(-r^2 / 2)``, ``r^2 = sum_d ((x_d - x'_d) / l_d)^2``.
+* Matern-5/2: ``k = s^2 (1 + sqrt5 r + 5 r^2 / 3) exp(-sqrt5 r)``.
+* Hyperparameters live in log space in the order
+  ``(log l_1..log l_D, log s^2, log sigma^2)``; zero prior mean.
+* Probes: ``z[i, c] = +1`` if bit 63 of ``splitmix64(seed XOR (c * 2^32 + i))``
+  is 0, else ``-1`` (splitmix64: Steele, Lea & Flood, OOPSLA 2014).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+RBF = 0
+MATERN52 = 1
+SQRT5 = math.sqrt(5.0)
+
+
+@dataclass
+class Hyper:
+    kind: int
+    log_lengthscale: np.ndarray
+    log_outputscale: float
+    log_noise: float
+
+    @property
+    def lengthscale(self) -> np.ndarray:
+        return np.exp(np.asarray(self.log_lengthscale, dtype=np.float64))
+
+    @property
+    def s2(self) -> float:
+        return math.exp(float(self.log_outputscale))
+
+    @property
+    def noise(self) -> float:
+        return math.exp(float(self.log_noise))
+
+    @property
+    def P(self) -> int:
+        return len(self.log_lengthscale) + 2
+
+
+def hyper_of(p) -> Hyper:
+    """Hyperparameters of any object with kind / log_lengthscale / log_outputscale / log_noise."""
+    return Hyper(int(p.kind), np.asarray(p.log_lengthscale, dtype=np.float64).copy(),
+                 float(p.log_outputscale), float(p.log_noise))
+
+
+# --------------------------------------------------------------------------- kernel entries
+
+def phi(kind: int, r2: np.ndarray) -> np.ndarray:
+    """Unit-variance kernel profile as a function of the squared ARD distance r^2."""
+    r2 = np.asarray(r2, dtype=np.float64)
+    if kind == RBF:
+        return np.exp(-0.5 * r2)
+    if kind == MATERN52:
+        r = np.sqrt(r2)
+        return (1.0 + SQRT5 * r + (5.0 / 3.0) * r2) * np.exp(-SQRT5 * r)
+    raise ValueError(f"unknown kernel kind {kind}")
+
+
+def dphi_dr2(kind: int, r2: np.ndarray) -> np.ndarray:
+    """Derivative of ``phi`` with respect to r^2 (chain rule for the lengthscale gradient)."""
+    r2 = np.asarray(r2, dtype=np.float64)
+    if kind == RBF:
+        return -0.5 * np.exp(-0.5 * r2)
+    if kind == MATERN52:
+        # d phi / d r = -(5/3) r (1 + sqrt5 r) exp(-sqrt5 r);  d r / d r^2 = 1 / (2 r)
+        r = np.sqrt(r2)
+        return -(5.0 / 6.0) * (1.0 + SQRT5 * r) * np.exp(-SQRT5 * r)
+    raise ValueError(f"unknown kernel kind {kind}")
+
+
+def scaled_sqdist(Xa: np.ndarray, Xb: np.ndarray, lengthscale: np.ndarray) -> np.ndarray:
+    """r^2[i, j] = sum_d ((Xa[i, d] - Xb[j, d]) / l_d)^2 in float64, one dimension at a time."""
+    Xa = np.asarray(Xa, dtype=np.float64)
+    Xb = np.asarray(Xb, dtype=np.float64)
+    r2 = np.zeros((Xa.shape[0], Xb.shape[0]))
+    for d in range(Xa.shape[1]):
+        diff = (Xa[:, d][:, None] - Xb[:, d][None, :]) / lengthscale[d]
+        r2 += diff * diff
+    return r2
+
+
+def cross_kernel(Xa, Xb, hyp: Hyper) -> np.ndarray:
+    """K_ab[i, j] = s^2 phi(r^2(x_a,i, x_b,j)) (no noise)."""
+    return hyp.s2 * phi(hyp.kind, scaled_sqdist(Xa, Xb, hyp.lengthscale))
+
+
+def kernel_matrix(X, hyp: Hyper) -> np.ndarray:
+    """K_ff for the training inputs (Sec. 2)."""
+    return cross_kernel(X, X, hyp)
+
+
+def noisy_kernel_matrix(X, hyp: Hyper) -> np.ndarray:
+    """K_y = K_ff + sigma_n^2 I (Sec. 2)."""
+    K = kernel_matrix(X, hyp)
+    K[np.diag_indices_from(K)] += hyp.noise
+    return K
+
+
+# --------------------------------------------------------------------------- products
+
+def matvec(X, V, hyp: Hyper, block: int = 2048) -> np.ndarray:
+    """out = K_y V, the product of Table 3, row block by row block (memory O(block * N))."""
+    X = np.asarray(X, dtype=np.float64)
+    V = np.asarray(V, dtype=np.float64)
+    squeeze = V.ndim == 1
+    V2 = V[:, None] if squeeze else V
+    out = np.empty((X.shape[0], V2.shape[1]))
+    for a in range(0, X.shape[0], block):
+        b = min(a + block, X.shape[0])
+        out[a:b] = cross_kernel(X[a:b], X, hyp) @ V2
+    out += hyp.noise * V2
+    return out[:, 0] if squeeze else out
+
+
+def matvec_rows(X, V, hyp: Hyper, rows) -> np.ndarray:
+    """Rows ``rows`` of K_y V, for spot checks at sizes where the full product is too slow."""
+    X = np.asarray(X, dtype=np.float64)
+    V = np.asarray(V, dtype=np.float64)
+    rows = np.asarray(rows, dtype=np.int64)
+    V2 = V[:, None] if V.ndim == 1 else V
+    out = cross_kernel(X[rows], X, hyp) @ V2 + hyp.noise * V2[rows]
+    return out[:, 0] if V.ndim == 1 else out
+
+
+def dK_matrices(X, hyp: Hyper) -> list[np.ndarray]:
+    """Explicit dK_y/dtheta_p for theta = (log l_1..log l_D, log s^2, log sigma^2).
+
+    log l_d: s^2 dphi/dr^2 * dr^2/dlog l_d with dr^2/dlog l_d = -2 ((x_d - x'_d)/l_d)^2.
+    log s^2: K_ff.   log sigma^2: sigma^2 I.
+    """
+    X = np.asarray(X, dtype=np.float64)
+    ls = hyp.lengthscale
+    r2 = scaled_sqdist(X, X, ls)
+    g = hyp.s2 * dphi_dr2(hyp.kind, r2)
+    mats = []
+    for d in range(X.shape[1]):
+        rd2 = ((X[:, d][:, None] - X[:, d][None, :]) / ls[d]) ** 2
+        mats.append(g * (-2.0 * rd2))
+    mats.append(hyp.s2 * phi(hyp.kind, r2))
+    mats.append(hyp.noise * np.eye(X.shape[0]))
+    return mats
+
+
+def dK_matvec(X, W, hyp: Hyper) -> np.ndarray:
+    """Derivative blocks G[p] = (dK_y/dtheta_p) W, shape [P, N, t]."""
+    W = np.asarray(W, dtype=np.float64)
+    W2 = W[:, None] if W.ndim == 1 else W
+    return np.stack([M @ W2 for M in dK_matrices(X, hyp)])
+
+
+# --------------------------------------------------------------------------- exact inference
+
+def cholesky_solve(Ky: np.ndarray, B: np.ndarray) -> np.ndarray:
+    """K_y^{-1} B by a Cholesky factor and two triangular solves (Sec. 2 exact inference)."""
+    import scipy.linalg as sla
+    L = np.linalg.cholesky(Ky)
+    return sla.cho_solve((L, True), np.asarray(B, dtype=np.float64))
+
+
+def logdet(Ky: np.ndarray) -> float:
+    """log|K_y| = 2 sum log L_ii."""
+    L = np.linalg.cholesky(Ky)
+    return float(2.0 * np.sum(np.log(np.diag(L))))
+
+
+def lml_from(Ky: np.ndarray, y: np.ndarray) -> float:
+    """-1/2 [y^T K_y^{-1} y + log|K_y| + N log 2 pi] (Sec. 2)."""
+    y = np.asarray(y, dtype=np.float64)
+    a = cholesky_solve(Ky, y)
+    return float(-0.5 * (y @ a + logdet(Ky) + y.shape[0] * math.log(2.0 * math.pi)))
+
+
+def lml(X, y, hyp: Hyper) -> float:
+    return lml_from(noisy_kernel_matrix(X, hyp), y)
+
+
+def grad_exact(X, y, hyp: Hyper) -> np.ndarray:
+    """d LML / d theta_p = 1/2 a^T dK_p a - 1/2 tr(K_y^{-1} dK_p), a = K_y^{-1} y."""
+    Ky = noisy_kernel_matrix(X, hyp)
+    a = cholesky_solve(Ky, np.asarray(y, dtype=np.float64))
+    Kinv = cholesky_solve(Ky, np.eye(Ky.shape[0]))
+    return np.array([0.5 * a @ M @ a - 0.5 * np.sum(Kinv * M) for M in dK_matrices(X, hyp)])
+
+
+# --------------------------------------------------------------------------- probes
+
+_M64 = (1 << 64) - 1
+
+
+def splitmix64(x: int) -> int:
+    """One output of splitmix64 from state ``x`` (Steele, Lea & Flood 2014): advance, then mix."""
+    z = (x + 0x9E3779B97F4A7C15) & _M64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
+    return z ^ (z >> 31)
+
+
+def rademacher(seed: int, N: int, m: int) -> np.ndarray:
+    """[N, m] float64 +-1 probes: z[i, c] = 1 - 2 * bit63(splitmix64(seed ^ (c << 32 | i))).
+
+    Independent Rademacher probes are what the paper uses for its CG trace
+    estimator (Sec. 4.3). Vectorised uint64 arithmetic wraps modulo 2^64 as the
+    definition requires.
+    """
+    i = np.arange(N, dtype=np.uint64)[:, None]
+    c = np.arange(m, dtype=np.uint64)[None, :]
+    with np.errstate(over="ignore"):
+        key = np.uint64(seed & _M64) ^ ((c << np.uint64(32)) | i)
+        z = key + np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    return 1.0 - 2.0 * (z >> np.uint64(63)).astype(np.float64)
+
+
+# --------------------------------------------------------------------------- CG and Lanczos
+
+@dataclass
+class CGResult:
+    x: np.ndarray          # [N, t]
+    alphas: np.ndarray     # [max_iter, t] (0 after a column stops)
+    betas: np.ndarray      # [max_iter, t]
+    iters: np.ndarray      # [t] iterations taken per column
+    rel_resid: np.ndarray  # [t] recursive ||r|| / ||b|| at stop
+
+
+def cg(apply_A, B, tol: float, max_iter: int) -> CGResult:
+    """Textbook CG from x0 = 0, no preconditioner, one independent recurrence per column.
+
+    Column c stops when its recursive residual satisfies ||r||/||b|| <= tol (or
+    at max_iter). alpha_k = r_k^T r_k / p_k^T A p_k, beta_k = r_{k+1}^T r_{k+1} / r_k^T r_k.
+    """
+    B = np.asarray(B, dtype=np.float64)
+    B = B[:, None] if B.ndim == 1 else B
+    N, t = B.shape
+    x = np.zeros_like(B)
+    r = B.copy()
+    p = B.copy()
+    rr = np.sum(r * r, axis=0)
+    bnorm = np.sqrt(rr)
+    active = bnorm > 0
+    iters = np.zeros(t, dtype=np.int64)
+    alphas = np.zeros((max_iter, t))
+    betas = np.zeros((max_iter, t))
+    for k in range(max_iter):
+        if not active.any():
+            break
+        Ap = apply_A(p)
+        pAp = np.sum(p * Ap, axis=0)
+        alpha = np.where(active, rr / np.where(active, pAp, 1.0), 0.0)
+        x += alpha * p
+        r -= alpha * Ap
+        rr_new = np.sum(r * r, axis=0)
+        beta = np.where(active, rr_new / np.where(active, rr, 1.0), 0.0)
+        alphas[k] = alpha
+        betas[k] = beta
+        iters += active
+        p = np.where(active, r + beta * p, p)
+        rr = np.where(active, rr_new, rr)
+        active = active & (np.sqrt(rr) > tol * bnorm)
+    rel = np.sqrt(rr) / np.where(bnorm > 0, bnorm, 1.0)
+    return CGResult(x, alphas, betas, iters, rel)
+
+
+def lanczos_tridiag_from_cg(alphas: np.ndarray, betas: np.ndarray, m: int) -> np.ndarray:
+    """The m x m Lanczos tridiagonal that CG's coefficients define for one column.
+
+    T[k, k] = 1/alpha_k + beta_{k-1}/alpha_{k-1} (second term absent for k = 0),
+    T[k, k+1] = T[k+1, k] = sqrt(beta_k) / alpha_k
+    (the CG-Lanczos relation; Saad, Iterative Methods for Sparse Linear Systems, Sec. 6.7.3).
+    """
+    T = np.zeros((m, m))
+    for k in range(m):
+        T[k, k] = 1.0 / alphas[k] + (betas[k - 1] / alphas[k - 1] if k > 0 else 0.0)
+        if k + 1 < m:
+            T[k, k + 1] = T[k + 1, k] = math.sqrt(betas[k]) / alphas[k]
+    return T
+
+
+def quadrature_logdet(T: np.ndarray, znorm2: float) -> float:
+    """||z||^2 e_1^T log(T) e_1 = ||z||^2 sum_j Q[0, j]^2 log(lambda_j) (Gauss quadrature)."""
+    lam, Q = np.linalg.eigh(T)
+    return float(znorm2 * np.sum(Q[0, :] ** 2 * np.log(lam)))
+
+
+def lanczos_full_reorth(A: np.ndarray, z: np.ndarray, m: int) -> np.ndarray:
+    """m steps of Lanczos on A from z/||z|| with full reorthogonalisation (Golub & Van Loan 10.1)."""
+    N = A.shape[0]
+    Qb = np.zeros((N, m))
+    a = np.zeros(m)
+    b = np.zeros(max(m - 1, 0))
+    q = np.asarray(z, dtype=np.float64) / np.linalg.norm(z)
+    for k in range(m):
+        Qb[:, k] = q
+        w = A @ q
+        a[k] = q @ w
+        w -= Qb[:, :k + 1] @ (Qb[:, :k + 1].T @ w)
+        w -= Qb[:, :k + 1] @ (Qb[:, :k + 1].T @ w)
+        if k + 1 < m:
+            b[k] = np.linalg.norm(w)
+            q = w / b[k]
+    return np.diag(a) + np.diag(b, 1) + np.diag(b, -1)
+
+
+def slq_logdet_from_cg(res: CGResult, Z: np.ndarray, L: int, first_probe_col: int = 1) -> float:
+    """Stochastic Lanczos log-det: mean over probe columns of ||z_i||^2 e_1^T log(T_i) e_1.
+
+    T_i uses the first min(L, iterations of column i) CG steps of that column.
+    """
+    Z = np.asarray(Z, dtype=np.float64)
+    vals = []
+    for i in range(Z.shape[1]):
+        c = first_probe_col + i
+        m = int(min(L, res.iters[c]))
+        T = lanczos_tridiag_from_cg(res.alphas[:, c], res.betas[:, c], m)
+        vals.append(quadrature_logdet(T, float(Z[:, i] @ Z[:, i])))
+    return float(np.mean(vals))
+
+
+# --------------------------------------------------------------------------- estimators
+
+def probe_conditioned_targets(X, y, hyp: Hyper, Z: np.ndarray) -> dict:
+    """Exact values of the stochastic estimators for fixed probes Z ([N, m]).
+
+    logdet_Z = mean_i z_i^T log(K_y) z_i (via eigh), tr_Z(M) = mean_i (K_y^{-1} z_i)^T M z_i,
+    grad_Z[p] = 1/2 a^T dK_p a - 1/2 tr_Z(dK_p), lml_Z = -1/2 (y^T a + logdet_Z + N log 2 pi).
+    """
+    Ky = noisy_kernel_matrix(X, hyp)
+    y = np.asarray(y, dtype=np.float64)
+    Z = np.asarray(Z, dtype=np.float64)
+    lam, Q = np.linalg.eigh(Ky)
+    W = Q.T @ Z
+    logdet_Z = float(np.mean(np.sum(W * W * np.log(lam)[:, None], axis=0)))
+    a = cholesky_solve(Ky, y)
+    U = cholesky_solve(Ky, Z)
+    grad = np.array([0.5 * a @ M @ a - 0.5 * np.mean(np.sum(U * (M @ Z), axis=0))
+                     for M in dK_matrices(X, hyp)])
+    N = y.shape[0]
+    quad = float(y @ a)
+    return {"logdet": logdet_Z, "quad": quad, "lml": -0.5 * (quad + logdet_Z + N * math.log(2 * math.pi)),
+            "grad": grad, "logdet_exact": float(np.sum(np.log(lam)))}
+
+
+def estimator_fp64(X, y, hyp: Hyper, n_probes: int, lanczos_steps: int, seed: int,
+                   tol: float = 1e-6, max_iter: int | None = None) -> dict:
+    """The mBCG / stochastic-Lanczos LML and Hutchinson gradient, run in float64.
+
+    Batched CG on [y, z_1..z_m] gives a = K_y^{-1} y (quad term y^T a) and
+    u_i = K_y^{-1} z_i; each probe's CG coefficients give a Lanczos tridiagonal
+    for the log-det quadrature; the gradient is
+    g_p = 1/2 a^T dK_p a - 1/2 mean_i u_i^T dK_p z_i.
+    """
+    X64 = np.asarray(X, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    N = y.shape[0]
+    Z = rademacher(seed, N, n_probes)
+    B = np.concatenate([y[:, None], Z], axis=1)
+    Ky = noisy_kernel_matrix(X64, hyp)
+    res = cg(lambda P: Ky @ P, B, tol, max_iter or min(N, 1000))
+    a = res.x[:, 0]
+    U = res.x[:, 1:]
+    ld = slq_logdet_from_cg(res, Z, lanczos_steps)
+    quad = float(y @ a)
+    grad = np.array([0.5 * a @ M @ a - 0.5 * np.mean(np.sum(U * (M @ Z), axis=0))
+                     for M in dK_matrices(X64, hyp)])
+    return {"logdet": ld, "quad": quad, "lml": -0.5 * (quad + ld + N * math.log(2 * math.pi)),
+            "grad": grad, "iters": res.iters, "Z": Z, "cg": res}

@@ -1,0 +1,291 @@
+"""Pins for the FP64 oracle: checks against facts fixed outside the oracle itself.
+
+Each test compares an oracle routine with something it does not share code
+with: a published constant or test vector (tests/golden), a library routine
+computing the same quantity from another definition (SciPy densities, Bessel
+functions, LAPACK log-determinants), a brute-force loop, a finite difference,
+or an identity (Hadamard probes make Hutchinson exact; full-length Lanczos
+makes Gauss quadrature exact).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.special as sp
+import scipy.stats as st
+
+import oracle
+from oracle import gp_oracle as go
+import workloads as wl
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _hyp(kind, D, seed=0, los=0.3, ln=math.log(0.05)):
+    rng = np.random.default_rng(seed)
+    return go.Hyper(kind, np.log(rng.uniform(0.3, 2.0, D)), los, ln)
+
+
+def _points(N, D, seed=0):
+    return np.random.default_rng(seed + 100).uniform(0, 1, (N, D))
+
+
+# ----------------------------------------------------------------------------- kernel entries
+
+def test_kernel_closed_form_values():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "kernel_values.txt")) if l.strip() and l[0] != "#"]
+    for name, r, val in rows:
+        kind = go.RBF if name == "rbf" else go.MATERN52
+        got = go.phi(kind, np.array([float(r) ** 2]))[0]
+        assert got == pytest.approx(float(val), rel=1e-14, abs=1e-15), (name, r)
+
+
+def test_rbf_is_gaussian_density_ratio():
+    """ARD RBF = N(x; x', diag l^2) / N(x'; x', diag l^2) (SciPy's density, another definition)."""
+    D = 3
+    hyp = _hyp(go.RBF, D, seed=1, los=0.0)
+    X = _points(6, D, seed=1)
+    K = go.kernel_matrix(X, hyp)
+    for i in range(6):
+        mvn = st.multivariate_normal(mean=X[i], cov=np.diag(hyp.lengthscale ** 2))
+        ref = mvn.pdf(X) / mvn.pdf(X[i])
+        np.testing.assert_allclose(K[i], ref, rtol=1e-12)
+
+
+def test_matern52_is_bessel_form():
+    """Matern nu=5/2 from the modified Bessel function K_nu (Rasmussen & Williams Eq. 4.14)."""
+    nu = 2.5
+    r = np.linspace(0.01, 6.0, 200)
+    z = math.sqrt(2 * nu) * r
+    ref = 2 ** (1 - nu) / sp.gamma(nu) * z ** nu * sp.kv(nu, z)
+    np.testing.assert_allclose(go.phi(go.MATERN52, r * r), ref, rtol=1e-12)
+
+
+def test_ard_scaling_and_outputscale():
+    hyp = go.Hyper(go.MATERN52, np.log([2.0, 0.5]), math.log(3.0), math.log(0.1))
+    X = np.array([[0.0, 0.0], [2.0, 0.0], [0.0, 0.5]])
+    K = go.kernel_matrix(X, hyp)
+    # both off-diagonal pairs sit at ARD distance exactly 1; diagonal is s^2
+    expect = 3.0 * (1 + math.sqrt(5) + 5 / 3) * math.exp(-math.sqrt(5))
+    assert K[0, 1] == pytest.approx(expect, rel=1e-14)
+    assert K[0, 2] == pytest.approx(expect, rel=1e-14)
+    assert K[0, 0] == pytest.approx(3.0, rel=1e-15)
+
+
+@pytest.mark.parametrize("kind", [go.RBF, go.MATERN52])
+def test_symmetric_and_psd(kind):
+    hyp = _hyp(kind, 4, seed=2)
+    X = _points(120, 4, seed=2)
+    Ky = go.noisy_kernel_matrix(X, hyp)
+    assert np.array_equal(Ky, Ky.T)
+    assert np.linalg.eigvalsh(Ky).min() >= hyp.noise * (1 - 1e-10)
+
+
+# ----------------------------------------------------------------------------- products
+
+@pytest.mark.parametrize("kind", [go.RBF, go.MATERN52])
+def test_matvec_bruteforce_loop(kind):
+    N, D, t = 23, 3, 2
+    hyp = _hyp(kind, D, seed=3)
+    X = _points(N, D, seed=3)
+    V = np.random.default_rng(3).standard_normal((N, t))
+    ls = hyp.lengthscale
+    ref = np.zeros((N, t))
+    for i in range(N):
+        for j in range(N):
+            r2 = sum(((X[i, d] - X[j, d]) / ls[d]) ** 2 for d in range(D))
+            if kind == go.RBF:
+                k = hyp.s2 * math.exp(-r2 / 2)
+            else:
+                r = math.sqrt(r2)
+                k = hyp.s2 * (1 + math.sqrt(5) * r + 5 * r2 / 3) * math.exp(-math.sqrt(5) * r)
+            if i == j:
+                k += hyp.noise
+            for c in range(t):
+                ref[i, c] += k * V[j, c]
+    np.testing.assert_allclose(go.matvec(X, V, hyp, block=7), ref, rtol=1e-13, atol=1e-13)
+    rows = [0, 5, 22]
+    np.testing.assert_allclose(go.matvec_rows(X, V, hyp, rows), ref[rows], rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("kind", [go.RBF, go.MATERN52])
+def test_c_streaming_oracle_matches_dense(kind):
+    N, D, t = 300, 5, 3
+    hyp = _hyp(kind, D, seed=4)
+    X = _points(N, D, seed=4).astype(np.float32)
+    V = np.random.default_rng(4).standard_normal((N, t)).astype(np.float32)
+    ref = go.matvec(X, V, hyp)
+    got, used = oracle.kyv_rows_c(X, V, hyp)
+    assert used >= 1
+    np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12)
+    rows = np.array([299, 0, 17])
+    got_r, _ = oracle.kyv_rows_c(X, V, hyp, rows=rows)
+    np.testing.assert_allclose(got_r, ref[rows], rtol=1e-12, atol=1e-12)
+
+
+def test_dK_matvec_matches_finite_difference_of_K():
+    hyp = _hyp(go.MATERN52, 2, seed=5)
+    X = _points(30, 2, seed=5)
+    W = np.random.default_rng(5).standard_normal((30, 2))
+    G = go.dK_matvec(X, W, hyp)
+    theta = np.concatenate([hyp.log_lengthscale, [hyp.log_outputscale, hyp.log_noise]])
+    h = 1e-6
+    for p in range(len(theta)):
+        tp, tm = theta.copy(), theta.copy()
+        tp[p] += h
+        tm[p] -= h
+        Kp = go.noisy_kernel_matrix(X, go.Hyper(hyp.kind, tp[:-2], tp[-2], tp[-1]))
+        Km = go.noisy_kernel_matrix(X, go.Hyper(hyp.kind, tm[:-2], tm[-2], tm[-1]))
+        np.testing.assert_allclose(G[p], (Kp - Km) @ W / (2 * h), rtol=1e-6, atol=1e-8)
+
+
+# ----------------------------------------------------------------------------- exact inference
+
+def test_cg_matches_cholesky_solve():
+    hyp = _hyp(go.RBF, 3, seed=6, ln=math.log(0.1))
+    X = _points(150, 3, seed=6)
+    Ky = go.noisy_kernel_matrix(X, hyp)
+    B = np.random.default_rng(6).standard_normal((150, 3))
+    res = go.cg(lambda P: Ky @ P, B, 1e-12, 2000)
+    ref = go.cholesky_solve(Ky, B)
+    np.testing.assert_allclose(res.x, ref, rtol=1e-8, atol=1e-8)
+    assert np.linalg.norm(B - Ky @ ref) <= 1e-10 * np.linalg.norm(B)
+    assert (res.rel_resid <= 1e-12).all()
+
+
+def test_logdet_three_ways():
+    hyp = _hyp(go.MATERN52, 3, seed=7)
+    Ky = go.noisy_kernel_matrix(_points(100, 3, seed=7), hyp)
+    a = go.logdet(Ky)
+    b = float(np.sum(np.log(np.linalg.eigvalsh(Ky))))
+    sign, c = np.linalg.slogdet(Ky)
+    assert sign == 1.0
+    assert a == pytest.approx(b, rel=1e-10)
+    assert a == pytest.approx(c, rel=1e-10)
+
+
+@pytest.mark.parametrize("kind", [go.RBF, go.MATERN52])
+def test_lml_is_gaussian_logpdf(kind):
+    hyp = _hyp(kind, 2, seed=8)
+    X = _points(60, 2, seed=8)
+    y = np.random.default_rng(8).standard_normal(60)
+    Ky = go.noisy_kernel_matrix(X, hyp)
+    ref = st.multivariate_normal(mean=np.zeros(60), cov=Ky).logpdf(y)
+    assert go.lml(X, y, hyp) == pytest.approx(ref, rel=1e-11)
+
+
+def test_lml_single_point_closed_form():
+    hyp = go.Hyper(go.RBF, np.array([0.3]), math.log(2.0), math.log(0.5))
+    y = np.array([1.7])
+    v = 2.0 + 0.5
+    ref = -0.5 * (1.7 ** 2 / v + math.log(v) + math.log(2 * math.pi))
+    assert go.lml(np.array([[0.4]]), y, hyp) == pytest.approx(ref, rel=1e-14)
+
+
+@pytest.mark.parametrize("kind", [go.RBF, go.MATERN52])
+def test_gradient_matches_central_fd(kind):
+    D = 3
+    hyp = _hyp(kind, D, seed=9)
+    X = _points(80, D, seed=9)
+    y = np.sin(4 * X[:, 0]) + 0.1 * np.random.default_rng(9).standard_normal(80)
+    g = go.grad_exact(X, y, hyp)
+    theta = np.concatenate([hyp.log_lengthscale, [hyp.log_outputscale, hyp.log_noise]])
+    h = 1e-5
+    fd = []
+    for p in range(len(theta)):
+        tp, tm = theta.copy(), theta.copy()
+        tp[p] += h
+        tm[p] -= h
+        fp = go.lml(X, y, go.Hyper(kind, tp[:D], tp[D], tp[D + 1]))
+        fm = go.lml(X, y, go.Hyper(kind, tm[:D], tm[D], tm[D + 1]))
+        fd.append((fp - fm) / (2 * h))
+    np.testing.assert_allclose(g, fd, rtol=1e-6, atol=1e-7)
+
+
+def test_noise_gradient_closed_form():
+    hyp = _hyp(go.RBF, 2, seed=10)
+    X = _points(50, 2, seed=10)
+    y = np.random.default_rng(10).standard_normal(50)
+    Ky = go.noisy_kernel_matrix(X, hyp)
+    a = np.linalg.solve(Ky, y)
+    ref = 0.5 * hyp.noise * (a @ a - np.trace(np.linalg.inv(Ky)))
+    assert go.grad_exact(X, y, hyp)[-1] == pytest.approx(ref, rel=1e-10)
+
+
+# ----------------------------------------------------------------------------- probes and estimators
+
+def test_splitmix64_reference_vector():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "splitmix64_seed0.txt")) if l.strip() and l[0] != "#"]
+    state = 0
+    for idx, hexval in rows:
+        assert go.splitmix64(state) == int(hexval, 16), idx
+        state = (state + 0x9E3779B97F4A7C15) % (1 << 64)
+
+
+def test_rademacher_keying_and_balance():
+    seed = 0x1234ABCD5678
+    Z = go.rademacher(seed, 4096, 5)
+    assert set(np.unique(Z)) == {-1.0, 1.0}
+    for (i, c) in [(0, 0), (4095, 4), (17, 3), (1000, 1)]:
+        bit = go.splitmix64(seed ^ ((c << 32) | i)) >> 63
+        assert Z[i, c] == 1.0 - 2.0 * bit
+    assert abs(Z.mean()) < 0.03
+
+
+def test_hadamard_probes_make_estimators_exact():
+    """With all N Hadamard columns as probes, Hutchinson traces are exact (Z Z^T = N I)."""
+    N = 64
+    hyp = _hyp(go.MATERN52, 2, seed=11)
+    X = _points(N, 2, seed=11)
+    y = np.random.default_rng(11).standard_normal(N)
+    H = sla.hadamard(N).astype(np.float64)
+    tg = go.probe_conditioned_targets(X, y, hyp, H)
+    assert tg["logdet"] == pytest.approx(tg["logdet_exact"], rel=1e-10)
+    np.testing.assert_allclose(tg["grad"], go.grad_exact(X, y, hyp), rtol=1e-9, atol=1e-10)
+    assert tg["lml"] == pytest.approx(go.lml(X, y, hyp), rel=1e-10)
+
+
+def test_full_length_lanczos_quadrature_is_exact():
+    """N Lanczos steps make Gauss quadrature exact: ||z||^2 e1^T log(T) e1 = z^T log(A) z."""
+    N = 24
+    hyp = _hyp(go.RBF, 2, seed=12, ln=math.log(0.5))
+    Ky = go.noisy_kernel_matrix(_points(N, 2, seed=12), hyp)
+    z = go.rademacher(99, N, 1)[:, 0]
+    lam, Q = np.linalg.eigh(Ky)
+    ref = float(np.sum((Q.T @ z) ** 2 * np.log(lam)))
+    T = go.lanczos_full_reorth(Ky, z, N)
+    assert go.quadrature_logdet(T, float(z @ z)) == pytest.approx(ref, rel=1e-9)
+    res = go.cg(lambda P: Ky @ P, z, 1e-14, N)
+    m = int(res.iters[0])
+    Tc = go.lanczos_tridiag_from_cg(res.alphas[:, 0], res.betas[:, 0], m)
+    assert go.quadrature_logdet(Tc, float(z @ z)) == pytest.approx(ref, rel=1e-7)
+
+
+def test_cg_coefficients_give_the_lanczos_tridiagonal():
+    """The tridiagonal from CG coefficients equals the one Lanczos builds directly.
+
+    Checked over the first steps, before the Krylov space has captured the few
+    large eigenvalues of K_y and the recurrences become dominated by rounding.
+    """
+    N, m = 200, 6
+    hyp = _hyp(go.MATERN52, 3, seed=13, ln=math.log(0.2))
+    Ky = go.noisy_kernel_matrix(_points(N, 3, seed=13), hyp)
+    z = go.rademacher(5, N, 1)[:, 0]
+    res = go.cg(lambda P: Ky @ P, z, 1e-14, m)
+    Tc = go.lanczos_tridiag_from_cg(res.alphas[:, 0], res.betas[:, 0], m)
+    Tl = go.lanczos_full_reorth(Ky, z, m)
+    np.testing.assert_allclose(np.diag(Tc), np.diag(Tl), rtol=1e-8)
+    np.testing.assert_allclose(np.abs(np.diag(Tc, 1)), np.abs(np.diag(Tl, 1)), rtol=1e-7)
+
+
+def test_fp64_estimator_hits_probe_conditioned_targets():
+    """Converged FP64 mBCG + SLQ with enough steps reproduces the probe-conditioned targets."""
+    p = wl.cfg3(N=400, t=9, seed=14)
+    hyp = go.hyper_of(p)
+    est = go.estimator_fp64(p.X, p.y, hyp, n_probes=8, lanczos_steps=400, seed=77, tol=1e-12, max_iter=400)
+    tg = go.probe_conditioned_targets(p.X, p.y, hyp, est["Z"])
+    assert est["quad"] == pytest.approx(tg["quad"], rel=1e-8)
+    assert est["logdet"] == pytest.approx(tg["logdet"], rel=1e-6)
+    np.testing.assert_allclose(est["grad"], tg["grad"], rtol=1e-6, atol=1e-6 * np.abs(tg["grad"]).max())
