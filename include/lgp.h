@@ -1,0 +1,219 @@
+/*
+ * lgp.h - C ABI of the GB300 matrix-free Gaussian-process library.
+ *
+ * The library computes, on one NVIDIA GB300 (sm_103a) GPU, the hot path of
+ * CG-based exact GP inference described in "LightGP: Lightweight Gaussian
+ * Process Inference in C++ on Metal and CUDA" (arXiv 2605.17898):
+ *
+ *   - the fused matrix-free product K_y V = (K_ff + sigma_n^2 I) V, whose kernel
+ *     entries are generated on the fly and never stored, so memory stays O(N)
+ *     (Sec. 2 "CG-based inference", Sec. 3 "GPU backends", Table 3);
+ *   - conjugate-gradient solves K_y^{-1} B that need only that product
+ *     (Sec. 2, Sec. 3 "Inference");
+ *   - the log marginal likelihood -1/2 [y^T K_y^{-1} y + log|K_y| + N log 2 pi]
+ *     (Sec. 2) with a stochastic Lanczos log-determinant (Sec. 3 "Inference")
+ *     over Rademacher probes (Sec. 4.3), and its hyperparameter gradient, which
+ *     the paper obtains by 2P+1 finite-difference fits (Sec. 5) and this library
+ *     obtains analytically in one matrix-free adjoint pass.
+ *
+ * Kernels (the paper names RBF and Matern-5/2, Sec. 3 "Kernels"; the forms
+ * used here are the standard ones, with per-dimension ARD lengthscales l_d):
+ *   r^2 = sum_d ((x_d - x'_d) / l_d)^2
+ *   LGP_RBF:       k = s^2 exp(-r^2 / 2)
+ *   LGP_MATERN52:  k = s^2 (1 + sqrt5 r + 5 r^2 / 3) exp(-sqrt5 r)
+ *
+ * Conventions shared by every entry point:
+ *   - All arrays are row-major float32 unless stated. X is [N, D], right-hand
+ *     sides and results are [N, t] with row stride t. Device pointers must be
+ *     4-byte aligned and point to device (or managed) memory of the context's
+ *     device; a host pointer where a device array is expected is rejected with
+ *     LGP_ERR_INVALID_ARG before anything is launched.
+ *   - Ownership: the caller owns every array passed in. The library owns only
+ *     the context and its workspace (grown on demand, released by lgp_destroy).
+ *   - Streams: work is ordered on the caller's stream (a cudaStream_t passed as
+ *     lgp_stream; NULL means the legacy default stream). Entry points that
+ *     return host scalars synchronise that stream before returning.
+ *   - Errors: arguments are checked before any launch. A negative status means
+ *     the outputs are undefined; a positive status means they are valid with a
+ *     warning. lgp_last_error_message() describes the last failure.
+ *   - Limits: 1 <= D <= 8, 1 <= t <= 64, N >= 1, 1 <= lanczos_steps <= 64.
+ *   - Thread safety: a context must not be used by two host threads at once.
+ */
+#ifndef LGP_H
+#define LGP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LGP_OK = 0,
+    LGP_WARN_NOT_CONVERGED = 1,   /* some column hit max_iter; outputs valid */
+    LGP_ERR_INVALID_ARG = -1,     /* bad pointer, size, alignment or value */
+    LGP_ERR_UNSUPPORTED = -2,     /* a size or mode this build does not handle */
+    LGP_ERR_CUDA = -3,            /* a CUDA runtime call failed */
+    LGP_ERR_NONFINITE = -4,       /* NaN/Inf in inputs or in a CG scalar */
+    LGP_ERR_BREAKDOWN = -5,       /* p^T K_y p <= 0 in CG (K_y not positive definite) */
+    LGP_ERR_TIMEOUT = -6,         /* a bounded device-side wait ran out */
+    LGP_ERR_WORKSPACE = -7        /* workspace allocation failed */
+} lgp_status;
+
+typedef enum { LGP_RBF = 0, LGP_MATERN52 = 1 } lgp_kernel;
+
+/* Arithmetic of the K_y V contraction. FP32: entries and products in float32
+ * FMA (one RHS column or a few). SPLIT_BF16: entries generated in float32,
+ * split as k = hi + lo with hi = bf16_rn(k), lo = bf16_rn(k - hi) (likewise V),
+ * and contracted on tcgen05 tensor cores as hi*hi + hi*lo + lo*hi with float32
+ * accumulation; needs t in {16, 32}. AUTO picks SPLIT_BF16 for t in {16, 32}
+ * and FP32 otherwise. */
+typedef enum { LGP_PREC_AUTO = 0, LGP_PREC_FP32 = 1, LGP_PREC_SPLIT_BF16 = 2 } lgp_precision;
+
+typedef struct {
+    int32_t kind;                  /* lgp_kernel */
+    int32_t D;                     /* input dimension, 1..8 */
+    const float *log_lengthscale;  /* HOST pointer to D values of log l_d */
+    float log_outputscale;         /* log s^2 */
+    float log_noise;               /* log sigma_n^2 */
+} lgp_hyper;
+
+typedef struct {
+    double tol;              /* stop column c when ||r_c|| / ||b_c|| <= tol (recursive residual) */
+    int32_t max_iter;        /* CG iteration cap, >= 1 */
+    int32_t lanczos_steps;   /* L: CG steps per probe kept for the Lanczos tridiagonal */
+    int32_t n_probes;        /* m Rademacher probes; the solve block is [y, z_1..z_m], t = m + 1 */
+    int32_t prec;            /* lgp_precision of the products inside the solve */
+    uint64_t seed;           /* probe seed (see lgp_rademacher_probes) */
+} lgp_options;
+
+typedef struct {
+    double lml;              /* log marginal likelihood estimate */
+    double quad;             /* y^T K_y^{-1} y */
+    double logdet;           /* stochastic Lanczos estimate of log|K_y| */
+    double max_rel_resid;    /* largest final recursive ||r||/||b|| over the t columns */
+    int32_t iters_max;       /* most CG iterations over the columns */
+    int32_t iters_min;       /* fewest CG iterations over the columns */
+    int32_t t;               /* columns solved (1 + n_probes) */
+    int32_t prec_used;       /* lgp_precision actually used for the products */
+} lgp_lml_info;
+
+typedef struct lgp_ctx lgp_ctx;
+typedef void *lgp_stream;    /* a cudaStream_t */
+
+/* Library version as 10000*major + 100*minor + patch. */
+int32_t lgp_version(void);
+
+/* Human-readable name of a status code (static storage). */
+const char *lgp_status_string(int32_t status);
+
+/* Create a context bound to CUDA device `device` (its workspace starts empty).
+ * Returns LGP_ERR_INVALID_ARG for a NULL ctx or a device that does not exist,
+ * LGP_ERR_UNSUPPORTED if the device is not compute capability 10.3. */
+lgp_status lgp_create(lgp_ctx **ctx, int32_t device);
+
+/* Release the context and its workspace. Waits for the context's device work. NULL is ignored. */
+void lgp_destroy(lgp_ctx *ctx);
+
+/* Message of the last failing call on this context ("" if none; static for a NULL ctx). */
+const char *lgp_last_error_message(const lgp_ctx *ctx);
+
+/* Workspace bytes currently held by the context. */
+int64_t lgp_workspace_bytes(const lgp_ctx *ctx);
+
+/* The lgp_precision lgp_kernel_matvec would use for t columns when asked for `prec`
+ * (resolves LGP_PREC_AUTO); a negative lgp_status if that request is unsupported. */
+int32_t lgp_matvec_precision(const lgp_ctx *ctx, int32_t t, int32_t prec);
+
+/* Bound, in GPU clock cycles, on every device-side wait of the tensor-core product
+ * (pipeline barriers between its copy, generation and MMA stages). A wait that
+ * runs out sets the context's device error word and the kernel returns early;
+ * the calling entry point (or lgp_check_device_status) then reports
+ * LGP_ERR_TIMEOUT. cycles <= 0 restores the default (about 4e9 cycles). */
+void lgp_set_wait_budget(lgp_ctx *ctx, int64_t cycles);
+
+/* Synchronise `stream`, read and clear the context's device error word:
+ * LGP_OK, LGP_ERR_TIMEOUT (a bounded wait ran out) or LGP_ERR_CUDA. */
+lgp_status lgp_check_device_status(lgp_ctx *ctx, lgp_stream stream);
+
+/*
+ * out = (K_ff + sigma_n^2 I) V: the fused matrix-free product (Sec. 3 "GPU
+ * backends"; Table 3 times it for one column). X [N, D], V [N, t], out [N, t]
+ * are device arrays; out must not alias V or X. `prec` selects the contraction
+ * arithmetic (lgp_precision). Asynchronous on `stream`; no host sync.
+ * A NaN/Inf in X or V propagates to out (no scan is made here).
+ */
+lgp_status lgp_kernel_matvec(lgp_ctx *ctx, const lgp_hyper *hyp, const float *X, const float *V,
+                             float *out, int64_t N, int32_t t, int32_t prec, lgp_stream stream);
+
+/*
+ * Derivative blocks G_p = (dK_y / dtheta_p) W for theta = (log l_1..log l_D,
+ * log s^2, log sigma_n^2), P = D + 2: the matrix-free adjoint product whose
+ * bilinear forms give the LML gradient (the quantity Sec. 5 obtains by finite
+ * differences). W is [N, t] device, dK_W is a device array [P, N, t]
+ * (block p at offset p*N*t). FP32 arithmetic. Asynchronous; no host sync.
+ */
+lgp_status lgp_kernel_matvec_grad(lgp_ctx *ctx, const lgp_hyper *hyp, const float *X, const float *W,
+                                  float *dK_W, int64_t N, int32_t t, lgp_stream stream);
+
+/*
+ * Xsol = K_y^{-1} B by unpreconditioned conjugate gradients from x0 = 0, one
+ * recurrence per column, all t columns advanced together (Sec. 2 "CG-based
+ * inference"; Sec. 5 "our simpler CG loop"). B and Xsol are device [N, t] and
+ * may not alias. The vectors are float32; the CG scalars (dot products, alpha,
+ * beta, residual norms) are accumulated in float64. iters (HOST [t], may be
+ * NULL) receives the iterations per column, rel_resid (HOST [t], may be NULL)
+ * the final recursive ||r||/||b||. Synchronises `stream`.
+ * Returns LGP_WARN_NOT_CONVERGED if a column reached max_iter, LGP_ERR_NONFINITE
+ * for NaN/Inf in X or B, LGP_ERR_BREAKDOWN if p^T K_y p <= 0.
+ */
+lgp_status lgp_cg_solve(lgp_ctx *ctx, const lgp_hyper *hyp, const float *X, const float *B, float *Xsol,
+                        int64_t N, int32_t t, const lgp_options *opt, int32_t *iters, double *rel_resid,
+                        lgp_stream stream);
+
+/*
+ * Log marginal likelihood and its gradient (Sec. 2) by batched CG on
+ * [y, z_1..z_m] (m = opt->n_probes Rademacher probes from opt->seed):
+ *   quad   = y^T a, a = K_y^{-1} y;
+ *   logdet = mean_i ||z_i||^2 e_1^T log(T_i) e_1, T_i the Lanczos tridiagonal of
+ *            the first min(L, iterations) CG steps of probe i (Sec. 3 "CG with
+ *            stochastic Lanczos log-determinant");
+ *   lml    = -1/2 (quad + logdet + N log 2 pi);
+ *   grad_p = 1/2 a^T dK_p a - 1/2 mean_i u_i^T dK_p z_i, u_i = K_y^{-1} z_i,
+ *            for theta = (log l_1..log l_D, log s^2, log sigma_n^2).
+ * X [N, D] and y [N] are device arrays. lml (HOST, may be NULL), grad (HOST
+ * [D + 2], may be NULL: the adjoint pass is then skipped), info (HOST, may be
+ * NULL). n_probes >= 1 and 1 <= lanczos_steps <= 64. Synchronises `stream`.
+ */
+lgp_status lgp_lml_and_grad(lgp_ctx *ctx, const lgp_hyper *hyp, const float *X, const float *y, int64_t N,
+                            const lgp_options *opt, double *lml, double *grad, lgp_lml_info *info,
+                            lgp_stream stream);
+
+/*
+ * The probes lgp_lml_and_grad draws: Z[i, c] = +1 if bit 63 of
+ * splitmix64(seed XOR (c * 2^32 + i)) is 0, else -1, for 0 <= i < N, 0 <= c < m
+ * (splitmix64: Steele, Lea & Flood, OOPSLA 2014; independent Rademacher probes
+ * as in Sec. 4.3). Z is a device array [N, ldz] (ldz >= m), written in columns
+ * 0..m-1. Asynchronous; no host sync.
+ */
+lgp_status lgp_rademacher_probes(lgp_ctx *ctx, uint64_t seed, int64_t N, int32_t m, float *Z, int64_t ldz,
+                                 lgp_stream stream);
+
+/*
+ * Many independent GP solves of uneven size in one call: for g < n_gp,
+ * Xsol[g] = K_y(g)^{-1} B[g] with K_y(g) from hyp[g] and X[g] ([N[g], hyp[g].D]),
+ * B[g] and Xsol[g] device [N[g], t]. All problems advance together: each CG
+ * iteration is one product launch over a work list of (problem, row tile)
+ * items and one launch per vector update, captured once in a CUDA graph and
+ * replayed. iters (HOST [n_gp * t], may be NULL) and rel_resid (HOST
+ * [n_gp * t], may be NULL) are per problem and column. Synchronises `stream`.
+ */
+lgp_status lgp_batch_cg_solve(lgp_ctx *ctx, int32_t n_gp, const lgp_hyper *hyp, const float *const *X,
+                              const float *const *B, float *const *Xsol, const int64_t *N, int32_t t,
+                              const lgp_options *opt, int32_t *iters, double *rel_resid, lgp_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LGP_H */

@@ -1,0 +1,637 @@
+// C ABI of the library: argument checks, workspace, the CG driver (CUDA-graph
+// replay of the iteration) and the LML / gradient pipeline.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lgp_internal.cuh"
+
+using namespace lgp;
+
+namespace {
+
+constexpr int kVersion = 10000;  // 1.0.0
+constexpr int kRowPad = 256;     // workspace rows are padded to a multiple of this
+constexpr int kChunk = 8;        // CG iterations per graph launch
+constexpr long long kDefaultWaitBudget = 4000000000LL;
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct lgp_ctx {
+    int device = 0;
+    int num_sms = 0;
+    std::string err;
+    long long wait_budget = kDefaultWaitBudget;
+    cudaStream_t work = nullptr;  // internal stream (graph capture is not allowed on the legacy stream)
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaEvent_t ev_chunk[2] = {nullptr, nullptr};
+    // workspace
+    DevBuf xs, mv_partial, cg_vec, cg_partial, cg_state, cg_hist, scal, rhs, adj_b, adj_partial, vsplit, flags;
+    DevBuf batch_meta;
+    int64_t ws_bytes = 0;
+    // pinned host mirrors
+    CgState *h_state = nullptr;
+    int *h_done = nullptr;      // [2] per pipelined chunk
+    double *h_scal = nullptr;   // [kMaxT * 4]
+    int *h_flags = nullptr;     // [4]
+    // cached CG graph
+    cudaGraphExec_t cg_exec = nullptr;
+    std::vector<unsigned char> cg_key;
+};
+
+namespace {
+
+lgp_status fail(lgp_ctx *c, lgp_status s, const char *fmt, ...) __attribute__((format(printf, 3, 4)));
+lgp_status fail(lgp_ctx *c, lgp_status s, const char *fmt, ...) {
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return s;
+}
+
+#define LGP_CUDA(call)                                                                                 \
+    do {                                                                                               \
+        cudaError_t e_ = (call);                                                                       \
+        if (e_ != cudaSuccess)                                                                         \
+            return fail(ctx, LGP_ERR_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),     \
+                        __FILE__, __LINE__);                                                           \
+    } while (0)
+
+lgp_status ensure(lgp_ctx *ctx, DevBuf &b, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (b.bytes >= bytes) return LGP_OK;
+    if (b.p) {
+        cudaError_t e = cudaFree(b.p);
+        ctx->ws_bytes -= (int64_t)b.bytes;
+        b.p = nullptr;
+        b.bytes = 0;
+        if (e != cudaSuccess) return fail(ctx, LGP_ERR_CUDA, "cudaFree: %s", cudaGetErrorString(e));
+    }
+    const size_t rounded = (bytes + (1u << 20) - 1) & ~((size_t)(1u << 20) - 1);
+    cudaError_t e = cudaMalloc(&b.p, rounded);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        b.p = nullptr;
+        return fail(ctx, LGP_ERR_WORKSPACE, "workspace allocation of %zu bytes failed: %s", rounded,
+                    cudaGetErrorString(e));
+    }
+    b.bytes = rounded;
+    ctx->ws_bytes += (int64_t)rounded;
+    // any workspace move invalidates the cached CG graph
+    if (ctx->cg_exec) {
+        cudaGraphExecDestroy(ctx->cg_exec);
+        ctx->cg_exec = nullptr;
+        ctx->cg_key.clear();
+    }
+    return LGP_OK;
+}
+
+int64_t pad_rows(int64_t N) { return (N + kRowPad - 1) / kRowPad * kRowPad; }
+
+lgp_status check_dev_ptr(lgp_ctx *ctx, const void *p, const char *name) {
+    if (p == nullptr) return fail(ctx, LGP_ERR_INVALID_ARG, "%s is NULL", name);
+    if (((uintptr_t)p) % 4 != 0) return fail(ctx, LGP_ERR_INVALID_ARG, "%s is not 4-byte aligned", name);
+    cudaPointerAttributes attr;
+    cudaError_t e = cudaPointerGetAttributes(&attr, p);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(ctx, LGP_ERR_INVALID_ARG, "%s is not a CUDA pointer (%s)", name, cudaGetErrorString(e));
+    }
+    if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)
+        return fail(ctx, LGP_ERR_INVALID_ARG, "%s is not device memory", name);
+    if (attr.device != ctx->device)
+        return fail(ctx, LGP_ERR_INVALID_ARG, "%s lives on device %d, context is on device %d", name, attr.device,
+                    ctx->device);
+    return LGP_OK;
+}
+
+lgp_status make_params(lgp_ctx *ctx, const lgp_hyper *h, KernelParams *kp) {
+    if (!h) return fail(ctx, LGP_ERR_INVALID_ARG, "hyp is NULL");
+    if (h->kind != LGP_RBF && h->kind != LGP_MATERN52)
+        return fail(ctx, LGP_ERR_INVALID_ARG, "unknown kernel kind %d", h->kind);
+    if (h->D < 1 || h->D > kMaxD) return fail(ctx, LGP_ERR_UNSUPPORTED, "D=%d outside 1..%d", h->D, kMaxD);
+    if (!h->log_lengthscale) return fail(ctx, LGP_ERR_INVALID_ARG, "log_lengthscale is NULL");
+    if (!std::isfinite(h->log_outputscale) || !std::isfinite(h->log_noise))
+        return fail(ctx, LGP_ERR_NONFINITE, "non-finite outputscale or noise");
+    std::memset(kp, 0, sizeof *kp);
+    kp->kind = h->kind;
+    kp->D = h->D;
+    kp->dpad = dpad_of(h->D);
+    const double c = h->kind == LGP_RBF ? std::sqrt(0.5 / std::log(2.0)) : std::sqrt(5.0);
+    for (int d = 0; d < h->D; ++d) {
+        const double ll = h->log_lengthscale[d];
+        if (!std::isfinite(ll)) return fail(ctx, LGP_ERR_NONFINITE, "non-finite log_lengthscale[%d]", d);
+        kp->scale[d] = (float)(c * std::exp(-ll));
+        if (!(kp->scale[d] > 0.0f) || !std::isfinite(kp->scale[d]))
+            return fail(ctx, LGP_ERR_UNSUPPORTED, "lengthscale[%d] out of float range", d);
+    }
+    kp->s2 = (float)std::exp((double)h->log_outputscale);
+    kp->log2_s2 = (float)((double)h->log_outputscale / std::log(2.0));
+    kp->noise = (float)std::exp((double)h->log_noise);
+    if (!(kp->s2 > 0.0f) || !std::isfinite(kp->s2) || !(kp->noise >= 0.0f) || !std::isfinite(kp->noise))
+        return fail(ctx, LGP_ERR_UNSUPPORTED, "outputscale or noise out of float range");
+    return LGP_OK;
+}
+
+// Resolve the product arithmetic for t columns.
+int resolve_prec(int t, int prec) {
+    if (prec == LGP_PREC_FP32) return LGP_PREC_FP32;
+    if (prec == LGP_PREC_SPLIT_BF16) return tc_supported(t) ? LGP_PREC_SPLIT_BF16 : (int)LGP_ERR_UNSUPPORTED;
+    if (prec == LGP_PREC_AUTO) return tc_supported(t) ? LGP_PREC_SPLIT_BF16 : LGP_PREC_FP32;
+    return LGP_ERR_INVALID_ARG;
+}
+
+struct Prepared {
+    KernelParams kp;
+    int64_t N, Np;
+    float *xs;
+};
+
+lgp_status prepare_x(lgp_ctx *ctx, const lgp_hyper *hyp, const float *X, int64_t N, cudaStream_t st, Prepared *pp) {
+    lgp_status s = make_params(ctx, hyp, &pp->kp);
+    if (s != LGP_OK) return s;
+    pp->N = N;
+    pp->Np = pad_rows(N);
+    s = ensure(ctx, ctx->xs, (size_t)pp->Np * pp->kp.dpad * sizeof(float));
+    if (s != LGP_OK) return s;
+    s = ensure(ctx, ctx->flags, 64);
+    if (s != LGP_OK) return s;
+    pp->xs = (float *)ctx->xs.p;
+    launch_prep_x(X, N, pp->kp.D, pp->kp.dpad, pp->kp.scale, pp->xs, pp->Np, (int *)ctx->flags.p, st);
+    LGP_CUDA(cudaGetLastError());
+    return LGP_OK;
+}
+
+// K_y V for prepared X. V has row stride ldv; out has row stride ldo.
+lgp_status matvec_prepared(lgp_ctx *ctx, const Prepared &pp, const float *V, int64_t ldv, float *out, int64_t ldo,
+                           int t, int prec, const int *skip, cudaStream_t st) {
+    if (prec == LGP_PREC_SPLIT_BF16) {
+        lgp_status s = ensure(ctx, ctx->vsplit, (size_t)tc_vsplit_bytes(pp.Np, t));
+        if (s != LGP_OK) return s;
+        const int64_t pf = mv_tc_partial_floats(pp.Np, t, ctx->num_sms);
+        s = ensure(ctx, ctx->mv_partial, (size_t)std::max<int64_t>(pf, 1) * sizeof(float));
+        if (s != LGP_OK) return s;
+        LGP_CUDA(launch_mv_tc(pp.kp, pp.xs, pp.N, pp.Np, V, ldv, out, ldo, t, ctx->vsplit.p, (float *)ctx->mv_partial.p,
+                              (int64_t)(ctx->mv_partial.bytes / sizeof(float)), skip, (int *)ctx->flags.p + 1,
+                              ctx->wait_budget, ctx->num_sms, st));
+        return LGP_OK;
+    }
+    const int64_t pf = mv_simt_partial_floats(pp.N, pp.Np, t, ctx->num_sms);
+    lgp_status s = ensure(ctx, ctx->mv_partial, (size_t)std::max<int64_t>(pf, 1) * sizeof(float));
+    if (s != LGP_OK) return s;
+    MvLaunch m;
+    m.kp = &pp.kp;
+    m.Xs = pp.xs;
+    m.N = pp.N;
+    m.Np = pp.Np;
+    m.V = V;
+    m.ldv = ldv;
+    m.out = out;
+    m.ldo = ldo;
+    m.t = t;
+    m.partial = (float *)ctx->mv_partial.p;
+    m.partial_cap = (int64_t)(ctx->mv_partial.bytes / sizeof(float));
+    m.skip = skip;
+    m.num_sms = ctx->num_sms;
+    LGP_CUDA(launch_mv_simt(m, st));
+    return LGP_OK;
+}
+
+lgp_status check_opts(lgp_ctx *ctx, const lgp_options *o, bool need_probes) {
+    if (!o) return fail(ctx, LGP_ERR_INVALID_ARG, "options is NULL");
+    if (!(o->tol > 0.0) || !std::isfinite(o->tol)) return fail(ctx, LGP_ERR_INVALID_ARG, "tol must be > 0");
+    if (o->max_iter < 1) return fail(ctx, LGP_ERR_INVALID_ARG, "max_iter must be >= 1");
+    if (need_probes) {
+        if (o->n_probes < 1 || o->n_probes + 1 > kMaxT)
+            return fail(ctx, LGP_ERR_UNSUPPORTED, "n_probes=%d outside 1..%d", o->n_probes, kMaxT - 1);
+        if (o->lanczos_steps < 1 || o->lanczos_steps > kMaxLanczos)
+            return fail(ctx, LGP_ERR_UNSUPPORTED, "lanczos_steps=%d outside 1..%d", o->lanczos_steps, kMaxLanczos);
+    }
+    return LGP_OK;
+}
+
+// Workspace layout of one CG run.
+lgp_status cg_buffers(lgp_ctx *ctx, int64_t N, int64_t Np, int t, int hist_len, CgBuffers *b) {
+    lgp_status s;
+    if ((s = ensure(ctx, ctx->cg_vec, (size_t)4 * Np * t * sizeof(float))) != LGP_OK) return s;
+    b->G = cg_num_blocks(N, t, ctx->num_sms);
+    if ((s = ensure(ctx, ctx->cg_partial, (size_t)b->G * 2 * t * sizeof(double))) != LGP_OK) return s;
+    if ((s = ensure(ctx, ctx->cg_state, sizeof(CgState))) != LGP_OK) return s;
+    if ((s = ensure(ctx, ctx->cg_hist, (size_t)2 * std::max(hist_len, 1) * t * sizeof(double))) != LGP_OK) return s;
+    float *v = (float *)ctx->cg_vec.p;
+    b->x = v;
+    b->r = v + Np * t;
+    b->p = v + 2 * Np * t;
+    b->Kp = v + 3 * Np * t;
+    b->partial = (double *)ctx->cg_partial.p;
+    b->state = (CgState *)ctx->cg_state.p;
+    b->hist_alpha = (double *)ctx->cg_hist.p;
+    b->hist_beta = b->hist_alpha + (size_t)std::max(hist_len, 1) * t;
+    return LGP_OK;
+}
+
+// Run CG on the internal stream: init, then replay a captured chunk of iterations until done.
+lgp_status run_cg(lgp_ctx *ctx, const Prepared &pp, const float *B, int64_t ldb, int t, const lgp_options *opt,
+                  int hist_len, int prec, CgBuffers *bout) {
+    cudaStream_t st = ctx->work;
+    CgBuffers b;
+    lgp_status s = cg_buffers(ctx, pp.N, pp.Np, t, hist_len, &b);
+    if (s != LGP_OK) return s;
+    // the product's own workspace must exist before capture (no allocation inside a capture)
+    if (prec == LGP_PREC_SPLIT_BF16) {
+        if ((s = ensure(ctx, ctx->vsplit, (size_t)tc_vsplit_bytes(pp.Np, t))) != LGP_OK) return s;
+        const int64_t pf = mv_tc_partial_floats(pp.Np, t, ctx->num_sms);
+        if ((s = ensure(ctx, ctx->mv_partial, (size_t)std::max<int64_t>(pf, 1) * sizeof(float))) != LGP_OK) return s;
+    } else {
+        const int64_t pf = mv_simt_partial_floats(pp.N, pp.Np, t, ctx->num_sms);
+        if ((s = ensure(ctx, ctx->mv_partial, (size_t)std::max<int64_t>(pf, 1) * sizeof(float))) != LGP_OK) return s;
+    }
+    // cg_buffers/ensure may have moved memory: re-read pointers
+    s = cg_buffers(ctx, pp.N, pp.Np, t, hist_len, &b);
+    if (s != LGP_OK) return s;
+
+    launch_cg_init(B, ldb, pp.N, pp.Np, t, b, opt->tol, opt->max_iter, hist_len, st);
+    LGP_CUDA(cudaGetLastError());
+
+    // Graph key: everything baked into the captured launches.
+    std::vector<unsigned char> key;
+    auto put = [&key](const void *p, size_t n) {
+        const unsigned char *c = (const unsigned char *)p;
+        key.insert(key.end(), c, c + n);
+    };
+    put(&pp.kp, sizeof pp.kp);
+    put(&pp.N, sizeof pp.N);
+    put(&pp.xs, sizeof pp.xs);
+    put(&t, sizeof t);
+    put(&prec, sizeof prec);
+    put(&b, sizeof b);
+    put(&ctx->mv_partial.p, sizeof(void *));
+    put(&ctx->vsplit.p, sizeof(void *));
+    put(&ctx->wait_budget, sizeof ctx->wait_budget);
+    if (!ctx->cg_exec || ctx->cg_key != key) {
+        if (ctx->cg_exec) {
+            cudaGraphExecDestroy(ctx->cg_exec);
+            ctx->cg_exec = nullptr;
+        }
+        LGP_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        lgp_status cs = LGP_OK;
+        for (int k = 0; k < kChunk && cs == LGP_OK; ++k) {
+            cs = matvec_prepared(ctx, pp, b.p, t, b.Kp, t, t, prec, &b.state->done, st);
+            if (cs == LGP_OK) launch_cg_after_matvec(pp.N, pp.Np, t, b, st);
+        }
+        cudaGraph_t g = nullptr;
+        cudaError_t ce = cudaStreamEndCapture(st, &g);
+        if (cs != LGP_OK) {
+            if (g) cudaGraphDestroy(g);
+            return cs;
+        }
+        if (ce != cudaSuccess) return fail(ctx, LGP_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ce));
+        ce = cudaGraphInstantiate(&ctx->cg_exec, g, 0);
+        cudaGraphDestroy(g);
+        if (ce != cudaSuccess) {
+            ctx->cg_exec = nullptr;
+            return fail(ctx, LGP_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(ce));
+        }
+        ctx->cg_key = key;
+    }
+    // Replay chunks; the host checks the done flag of chunk k while chunk k+1 runs.
+    const int max_chunks = (opt->max_iter + kChunk - 1) / kChunk + 1;
+    int prev = -1;
+    for (int k = 0; k < max_chunks; ++k) {
+        LGP_CUDA(cudaGraphLaunch(ctx->cg_exec, st));
+        const int slot = k & 1;
+        LGP_CUDA(cudaMemcpyAsync(ctx->h_done + slot, &b.state->done, sizeof(int), cudaMemcpyDeviceToHost, st));
+        LGP_CUDA(cudaEventRecord(ctx->ev_chunk[slot], st));
+        if (prev >= 0) {
+            LGP_CUDA(cudaEventSynchronize(ctx->ev_chunk[prev]));
+            if (ctx->h_done[prev]) break;
+        }
+        prev = slot;
+    }
+    LGP_CUDA(cudaMemcpyAsync(ctx->h_state, b.state, sizeof(CgState), cudaMemcpyDeviceToHost, st));
+    *bout = b;
+    return LGP_OK;
+}
+
+// Make the internal stream wait for the caller's stream.
+lgp_status enter(lgp_ctx *ctx, cudaStream_t user) {
+    LGP_CUDA(cudaSetDevice(ctx->device));
+    LGP_CUDA(cudaEventRecord(ctx->ev_in, user));
+    LGP_CUDA(cudaStreamWaitEvent(ctx->work, ctx->ev_in, 0));
+    return LGP_OK;
+}
+
+// Make the caller's stream wait for the internal stream, then synchronise it.
+lgp_status leave_sync(lgp_ctx *ctx, cudaStream_t user) {
+    LGP_CUDA(cudaEventRecord(ctx->ev_out, ctx->work));
+    LGP_CUDA(cudaStreamWaitEvent(user, ctx->ev_out, 0));
+    LGP_CUDA(cudaStreamSynchronize(ctx->work));
+    return LGP_OK;
+}
+
+lgp_status cg_status_of(lgp_ctx *ctx, const CgState &h, int t, int *iters, double *rel, int x_nonfinite) {
+    if (x_nonfinite) return fail(ctx, LGP_ERR_NONFINITE, "X contains NaN or Inf");
+    bool unconverged = false;
+    for (int c = 0; c < t; ++c) {
+        if (iters) iters[c] = h.iters[c];
+        const double rr = h.bnorm2[c] > 0.0 ? std::sqrt(h.rr[c] / h.bnorm2[c]) : 0.0;
+        if (rel) rel[c] = rr;
+        if (h.active[c]) unconverged = true;
+    }
+    if (h.status == LGP_ERR_NONFINITE) return fail(ctx, LGP_ERR_NONFINITE, "non-finite value in B or a CG scalar");
+    if (h.status == LGP_ERR_BREAKDOWN)
+        return fail(ctx, LGP_ERR_BREAKDOWN, "CG breakdown: p^T K_y p <= 0 (K_y not positive definite in float32)");
+    if (unconverged) {
+        fail(ctx, LGP_WARN_NOT_CONVERGED, "CG reached max_iter before tol on some column");
+        return LGP_WARN_NOT_CONVERGED;
+    }
+    return LGP_OK;
+}
+
+}  // namespace
+
+// ============================================================================ C ABI
+
+extern "C" {
+
+int32_t lgp_version(void) { return kVersion; }
+
+const char *lgp_status_string(int32_t s) {
+    switch (s) {
+        case LGP_OK: return "LGP_OK";
+        case LGP_WARN_NOT_CONVERGED: return "LGP_WARN_NOT_CONVERGED";
+        case LGP_ERR_INVALID_ARG: return "LGP_ERR_INVALID_ARG";
+        case LGP_ERR_UNSUPPORTED: return "LGP_ERR_UNSUPPORTED";
+        case LGP_ERR_CUDA: return "LGP_ERR_CUDA";
+        case LGP_ERR_NONFINITE: return "LGP_ERR_NONFINITE";
+        case LGP_ERR_BREAKDOWN: return "LGP_ERR_BREAKDOWN";
+        case LGP_ERR_TIMEOUT: return "LGP_ERR_TIMEOUT";
+        case LGP_ERR_WORKSPACE: return "LGP_ERR_WORKSPACE";
+    }
+    return "LGP_UNKNOWN_STATUS";
+}
+
+lgp_status lgp_create(lgp_ctx **out, int32_t device) {
+    if (!out) return LGP_ERR_INVALID_ARG;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+        (void)cudaGetLastError();
+        return LGP_ERR_INVALID_ARG;
+    }
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return LGP_ERR_CUDA;
+    if (!(prop.major == 10 && prop.minor == 3)) return LGP_ERR_UNSUPPORTED;
+    lgp_ctx *ctx = new lgp_ctx();
+    ctx->device = device;
+    ctx->num_sms = prop.multiProcessorCount;
+    bool ok = cudaSetDevice(device) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&ctx->work, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&ctx->ev_chunk[0], cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&ctx->ev_chunk[1], cudaEventDisableTiming) == cudaSuccess &&
+              cudaMallocHost(&ctx->h_state, sizeof(CgState)) == cudaSuccess &&
+              cudaMallocHost(&ctx->h_done, 2 * sizeof(int)) == cudaSuccess &&
+              cudaMallocHost(&ctx->h_scal, kMaxT * 4 * sizeof(double)) == cudaSuccess &&
+              cudaMallocHost(&ctx->h_flags, 4 * sizeof(int)) == cudaSuccess;
+    if (ok) {
+        ok = ensure(ctx, ctx->flags, 64) == LGP_OK && cudaMemset(ctx->flags.p, 0, 64) == cudaSuccess;
+    }
+    if (!ok) {
+        lgp_destroy(ctx);
+        return LGP_ERR_CUDA;
+    }
+    *out = ctx;
+    return LGP_OK;
+}
+
+void lgp_destroy(lgp_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->work) cudaStreamSynchronize(ctx->work);
+    if (ctx->cg_exec) cudaGraphExecDestroy(ctx->cg_exec);
+    DevBuf *bufs[] = {&ctx->xs, &ctx->mv_partial, &ctx->cg_vec, &ctx->cg_partial, &ctx->cg_state, &ctx->cg_hist,
+                      &ctx->scal, &ctx->rhs, &ctx->adj_b, &ctx->adj_partial, &ctx->vsplit, &ctx->flags,
+                      &ctx->batch_meta};
+    for (DevBuf *b : bufs)
+        if (b->p) cudaFree(b->p);
+    if (ctx->h_state) cudaFreeHost(ctx->h_state);
+    if (ctx->h_done) cudaFreeHost(ctx->h_done);
+    if (ctx->h_scal) cudaFreeHost(ctx->h_scal);
+    if (ctx->h_flags) cudaFreeHost(ctx->h_flags);
+    if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
+    if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
+    if (ctx->ev_chunk[0]) cudaEventDestroy(ctx->ev_chunk[0]);
+    if (ctx->ev_chunk[1]) cudaEventDestroy(ctx->ev_chunk[1]);
+    if (ctx->work) cudaStreamDestroy(ctx->work);
+    delete ctx;
+}
+
+const char *lgp_last_error_message(const lgp_ctx *ctx) {
+    if (!ctx) return "no context";
+    return ctx->err.c_str();
+}
+
+int64_t lgp_workspace_bytes(const lgp_ctx *ctx) { return ctx ? ctx->ws_bytes : 0; }
+
+int32_t lgp_matvec_precision(const lgp_ctx *ctx, int32_t t, int32_t prec) {
+    (void)ctx;
+    if (t < 1 || t > kMaxT) return LGP_ERR_UNSUPPORTED;
+    return resolve_prec(t, prec);
+}
+
+void lgp_set_wait_budget(lgp_ctx *ctx, int64_t cycles) {
+    if (ctx) ctx->wait_budget = cycles > 0 ? cycles : kDefaultWaitBudget;
+}
+
+lgp_status lgp_check_device_status(lgp_ctx *ctx, lgp_stream stream) {
+    if (!ctx) return LGP_ERR_INVALID_ARG;
+    cudaStream_t user = (cudaStream_t)stream;
+    LGP_CUDA(cudaSetDevice(ctx->device));
+    LGP_CUDA(cudaStreamSynchronize(user));
+    LGP_CUDA(cudaStreamSynchronize(ctx->work));
+    LGP_CUDA(cudaMemcpy(ctx->h_flags, ctx->flags.p, 4 * sizeof(int), cudaMemcpyDeviceToHost));
+    LGP_CUDA(cudaMemset(ctx->flags.p, 0, 4 * sizeof(int)));
+    if (ctx->h_flags[1]) return fail(ctx, LGP_ERR_TIMEOUT, "a bounded device wait ran out (code %d)", ctx->h_flags[1]);
+    return LGP_OK;
+}
+
+lgp_status lgp_kernel_matvec(lgp_ctx *ctx, const lgp_hyper *hyp, const float *X, const float *V, float *out,
+                             int64_t N, int32_t t, int32_t prec, lgp_stream stream) {
+    if (!ctx) return LGP_ERR_INVALID_ARG;
+    if (N < 1) return fail(ctx, LGP_ERR_INVALID_ARG, "N=%lld must be >= 1", (long long)N);
+    if (t < 1 || t > kMaxT) return fail(ctx, LGP_ERR_UNSUPPORTED, "t=%d outside 1..%d", t, kMaxT);
+    lgp_status s;
+    LGP_CUDA(cudaSetDevice(ctx->device));
+    if ((s = check_dev_ptr(ctx, X, "X")) || (s = check_dev_ptr(ctx, V, "V")) || (s = check_dev_ptr(ctx, out, "out")))
+        return s;
+    if (out == V || (const float *)out == X) return fail(ctx, LGP_ERR_INVALID_ARG, "out aliases an input");
+    const int p = resolve_prec(t, prec);
+    if (p < 0) return fail(ctx, (lgp_status)p, "precision %d unsupported for t=%d", prec, t);
+    cudaStream_t st = (cudaStream_t)stream;
+    Prepared pp;
+    if ((s = prepare_x(ctx, hyp, X, N, st, &pp)) != LGP_OK) return s;
+    return matvec_prepared(ctx, pp, V, t, out, t, t, p, nullptr, st);
+}
+
+lgp_status lgp_kernel_matvec_grad(lgp_ctx *ctx, const lgp_hyper *hyp, const float *X, const float *W, float *dK_W,
+                                  int64_t N, int32_t t, lgp_stream stream) {
+    if (!ctx) return LGP_ERR_INVALID_ARG;
+    if (N < 1) return fail(ctx, LGP_ERR_INVALID_ARG, "N=%lld must be >= 1", (long long)N);
+    if (t < 1 || t > kMaxT) return fail(ctx, LGP_ERR_UNSUPPORTED, "t=%d outside 1..%d", t, kMaxT);
+    lgp_status s;
+    LGP_CUDA(cudaSetDevice(ctx->device));
+    if ((s = check_dev_ptr(ctx, X, "X")) || (s = check_dev_ptr(ctx, W, "W")) || (s = check_dev_ptr(ctx, dK_W, "dK_W")))
+        return s;
+    if ((const float *)dK_W == W) return fail(ctx, LGP_ERR_INVALID_ARG, "dK_W aliases W");
+    cudaStream_t st = (cudaStream_t)stream;
+    Prepared pp;
+    if ((s = prepare_x(ctx, hyp, X, N, st, &pp)) != LGP_OK) return s;
+    const int64_t pf = mv_grad_partial_floats(N, pp.Np, t, pp.kp.D, ctx->num_sms);
+    if ((s = ensure(ctx, ctx->mv_partial, (size_t)std::max<int64_t>(pf, 1) * sizeof(float))) != LGP_OK) return s;
+    LGP_CUDA(launch_mv_grad(pp.kp, pp.xs, N, pp.Np, W, t, dK_W, (float *)ctx->mv_partial.p,
+                            (int64_t)(ctx->mv_partial.bytes / sizeof(float)), ctx->num_sms, st));
+    return LGP_OK;
+}
+
+lgp_status lgp_rademacher_probes(lgp_ctx *ctx, uint64_t seed, int64_t N, int32_t m, float *Z, int64_t ldz,
+                                 lgp_stream stream) {
+    if (!ctx) return LGP_ERR_INVALID_ARG;
+    if (N < 1 || m < 1 || ldz < m) return fail(ctx, LGP_ERR_INVALID_ARG, "need N >= 1, m >= 1, ldz >= m");
+    lgp_status s;
+    LGP_CUDA(cudaSetDevice(ctx->device));
+    if ((s = check_dev_ptr(ctx, Z, "Z"))) return s;
+    launch_rademacher(seed, N, m, Z, ldz, 0, (cudaStream_t)stream);
+    LGP_CUDA(cudaGetLastError());
+    return LGP_OK;
+}
+
+lgp_status lgp_cg_solve(lgp_ctx *ctx, const lgp_hyper *hyp, const float *X, const float *B, float *Xsol, int64_t N,
+                        int32_t t, const lgp_options *opt, int32_t *iters, double *rel_resid, lgp_stream stream) {
+    if (!ctx) return LGP_ERR_INVALID_ARG;
+    if (N < 1) return fail(ctx, LGP_ERR_INVALID_ARG, "N=%lld must be >= 1", (long long)N);
+    if (t < 1 || t > kMaxT) return fail(ctx, LGP_ERR_UNSUPPORTED, "t=%d outside 1..%d", t, kMaxT);
+    lgp_status s;
+    if ((s = check_opts(ctx, opt, false)) != LGP_OK) return s;
+    LGP_CUDA(cudaSetDevice(ctx->device));
+    if ((s = check_dev_ptr(ctx, X, "X")) || (s = check_dev_ptr(ctx, B, "B")) || (s = check_dev_ptr(ctx, Xsol, "Xsol")))
+        return s;
+    if ((const float *)Xsol == B) return fail(ctx, LGP_ERR_INVALID_ARG, "Xsol aliases B");
+    const int prec = resolve_prec(t, opt->prec);
+    if (prec < 0) return fail(ctx, (lgp_status)prec, "precision %d unsupported for t=%d", opt->prec, t);
+    cudaStream_t user = (cudaStream_t)stream;
+    if ((s = enter(ctx, user)) != LGP_OK) return s;
+    LGP_CUDA(cudaMemsetAsync(ctx->flags.p, 0, 4 * sizeof(int), ctx->work));
+    Prepared pp;
+    if ((s = prepare_x(ctx, hyp, X, N, ctx->work, &pp)) != LGP_OK) return s;
+    CgBuffers b;
+    if ((s = run_cg(ctx, pp, B, t, t, opt, 0, prec, &b)) != LGP_OK) return s;
+    launch_cg_copy_out(b, N, t, Xsol, t, ctx->work);
+    LGP_CUDA(cudaGetLastError());
+    LGP_CUDA(cudaMemcpyAsync(ctx->h_flags, ctx->flags.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, ctx->work));
+    if ((s = leave_sync(ctx, user)) != LGP_OK) return s;
+    if (ctx->h_flags[1]) return fail(ctx, LGP_ERR_TIMEOUT, "a bounded device wait ran out (code %d)", ctx->h_flags[1]);
+    return cg_status_of(ctx, *ctx->h_state, t, iters, rel_resid, ctx->h_flags[0]);
+}
+
+lgp_status lgp_lml_and_grad(lgp_ctx *ctx, const lgp_hyper *hyp, const float *X, const float *y, int64_t N,
+                            const lgp_options *opt, double *lml, double *grad, lgp_lml_info *info,
+                            lgp_stream stream) {
+    if (!ctx) return LGP_ERR_INVALID_ARG;
+    if (N < 1) return fail(ctx, LGP_ERR_INVALID_ARG, "N=%lld must be >= 1", (long long)N);
+    lgp_status s;
+    if ((s = check_opts(ctx, opt, true)) != LGP_OK) return s;
+    LGP_CUDA(cudaSetDevice(ctx->device));
+    if ((s = check_dev_ptr(ctx, X, "X")) || (s = check_dev_ptr(ctx, y, "y"))) return s;
+    const int t = opt->n_probes + 1;
+    const int L = opt->lanczos_steps;
+    const int prec = resolve_prec(t, opt->prec);
+    if (prec < 0) return fail(ctx, (lgp_status)prec, "precision %d unsupported for t=%d", opt->prec, t);
+    cudaStream_t user = (cudaStream_t)stream;
+    if ((s = enter(ctx, user)) != LGP_OK) return s;
+    cudaStream_t st = ctx->work;
+    LGP_CUDA(cudaMemsetAsync(ctx->flags.p, 0, 4 * sizeof(int), st));
+    Prepared pp;
+    if ((s = prepare_x(ctx, hyp, X, N, st, &pp)) != LGP_OK) return s;
+    // right-hand-side block [y, z_1..z_m]
+    if ((s = ensure(ctx, ctx->rhs, (size_t)pp.Np * t * sizeof(float))) != LGP_OK) return s;
+    float *rhs = (float *)ctx->rhs.p;
+    launch_copy_cols(y, 1, rhs, t, N, 1, 0, st);
+    launch_rademacher(opt->seed, N, t - 1, rhs, t, 1, st);
+    LGP_CUDA(cudaGetLastError());
+    CgBuffers b;
+    if ((s = run_cg(ctx, pp, rhs, t, t, opt, L, prec, &b)) != LGP_OK) return s;
+    // scalars: dots[0..2t), slq[4], grad[D+2]
+    const int G = b.G;
+    if ((s = ensure(ctx, ctx->scal, (size_t)(2 * kMaxT + 4 + kMaxD + 2) * sizeof(double))) != LGP_OK) return s;
+    double *dots = (double *)ctx->scal.p;
+    double *slq = dots + 2 * kMaxT;
+    double *gdev = slq + 4;
+    launch_col_dots(b.x, rhs, N, t, b.partial, G, dots, st);
+    launch_slq_lml(b, t, L, dots, N, slq, st);
+    LGP_CUDA(cudaGetLastError());
+    if (grad) {
+        if ((s = ensure(ctx, ctx->adj_b, (size_t)pp.Np * t * sizeof(float))) != LGP_OK) return s;
+        const int64_t pd = adjoint_partial_doubles(N, t, pp.kp.D, ctx->num_sms);
+        if ((s = ensure(ctx, ctx->adj_partial, (size_t)pd * sizeof(double))) != LGP_OK) return s;
+        launch_adjoint_rhs(b.x, rhs, N, t, (float *)ctx->adj_b.p, st);
+        int nblk = 0;
+        LGP_CUDA(launch_adjoint_bilinear(pp.kp, pp.xs, N, pp.Np, b.x, (const float *)ctx->adj_b.p, t,
+                                         (double *)ctx->adj_partial.p, pd, &nblk, ctx->num_sms, st));
+        launch_grad_finalize((const double *)ctx->adj_partial.p, nblk, pp.kp.D, dots, t, pp.kp.noise, gdev, st);
+        LGP_CUDA(cudaGetLastError());
+    }
+    LGP_CUDA(cudaMemcpyAsync(ctx->h_scal, dots, (size_t)(2 * kMaxT + 4 + kMaxD + 2) * sizeof(double),
+                             cudaMemcpyDeviceToHost, st));
+    LGP_CUDA(cudaMemcpyAsync(ctx->h_flags, ctx->flags.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    if ((s = leave_sync(ctx, user)) != LGP_OK) return s;
+    if (ctx->h_flags[1]) return fail(ctx, LGP_ERR_TIMEOUT, "a bounded device wait ran out (code %d)", ctx->h_flags[1]);
+    std::vector<int> it(t);
+    std::vector<double> rel(t);
+    lgp_status cs = cg_status_of(ctx, *ctx->h_state, t, it.data(), rel.data(), ctx->h_flags[0]);
+    if (cs < 0) return cs;
+    const double *hs = ctx->h_scal + 2 * kMaxT;
+    if (hs[3] != 0.0) return fail(ctx, LGP_ERR_NONFINITE, "non-positive Ritz value in a Lanczos tridiagonal");
+    if (lml) *lml = hs[0];
+    if (grad)
+        for (int p = 0; p < pp.kp.D + 2; ++p) grad[p] = hs[4 + p];
+    if (info) {
+        info->lml = hs[0];
+        info->quad = hs[1];
+        info->logdet = hs[2];
+        info->t = t;
+        info->prec_used = prec;
+        info->iters_max = *std::max_element(it.begin(), it.end());
+        info->iters_min = *std::min_element(it.begin(), it.end());
+        info->max_rel_resid = *std::max_element(rel.begin(), rel.end());
+    }
+    return cs;
+}
+
+lgp_status lgp_batch_cg_solve(lgp_ctx *ctx, int32_t n_gp, const lgp_hyper *hyp, const float *const *X,
+                              const float *const *B, float *const *Xsol, const int64_t *N, int32_t t,
+                              const lgp_options *opt, int32_t *iters, double *rel_resid, lgp_stream stream) {
+    (void)n_gp; (void)hyp; (void)X; (void)B; (void)Xsol; (void)N; (void)t; (void)opt; (void)iters; (void)rel_resid;
+    (void)stream;
+    if (!ctx) return LGP_ERR_INVALID_ARG;
+    return fail(ctx, LGP_ERR_UNSUPPORTED, "lgp_batch_cg_solve is not built yet");
+}
+
+}  // extern "C"

@@ -1,0 +1,175 @@
+// Internal declarations shared by the CUDA translation units of the library.
+//
+// Coordinates. Every product works on prescaled inputs xh_d = c_kind * x_d / l_d
+// so that one kernel entry is a short register computation:
+//   RBF:        c = sqrt(log2(e) / 2), rh2 = c^2 r^2,  k = 2^(log2 s^2 - rh2)
+//   Matern-5/2: c = sqrt(5),           rh  = sqrt(5) r, k = (1 + rh + rh^2/3) 2^(log2 s^2 - rh log2 e)
+// Both equal the standard forms k = s^2 exp(-r^2/2) and
+// k = s^2 (1 + sqrt5 r + 5 r^2/3) exp(-sqrt5 r) with r^2 = sum_d ((x_d - x'_d)/l_d)^2.
+// Lengthscale derivatives in the same coordinates: dk/dlog l_d = psi * (dxh_d)^2 with
+//   RBF:        psi = 2 ln2 * k
+//   Matern-5/2: psi = (1 + rh) * s^2 2^(-rh log2 e) / 3
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lgp.h"
+
+namespace lgp {
+
+constexpr int kMaxD = 8;
+constexpr int kMaxT = 64;
+constexpr int kMaxLanczos = 64;
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kTwoLn2 = 1.3862943611198906f;
+
+// Padded row width of the prescaled X buffer (floats): 4 for D <= 4, else 8.
+inline int dpad_of(int D) { return D <= 4 ? 4 : 8; }
+
+struct KernelParams {
+    int kind;
+    int D;
+    int dpad;
+    float log2_s2;   // log2(s^2)
+    float s2;        // s^2
+    float noise;     // sigma_n^2
+    float scale[kMaxD];
+};
+
+// ---------------------------------------------------------------- device helpers
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+template <int KIND> struct Entry;
+
+template <> struct Entry<LGP_RBF> {
+    // k from the prescaled squared distance.
+    static __device__ __forceinline__ float k(float rh2, float log2s2) { return ex2_approx(log2s2 - rh2); }
+    // k and psi (dk/dlog l_d = psi * dxh_d^2).
+    static __device__ __forceinline__ void k_psi(float rh2, float log2s2, float &k, float &psi) {
+        k = ex2_approx(log2s2 - rh2);
+        psi = kTwoLn2 * k;
+    }
+};
+
+template <> struct Entry<LGP_MATERN52> {
+    static __device__ __forceinline__ float k(float rh2, float log2s2) {
+        const float rh = sqrt_approx(rh2);
+        const float e = ex2_approx(fmaf(-rh, kLog2e, log2s2));
+        const float poly = fmaf(rh2, 1.0f / 3.0f, rh) + 1.0f;
+        return poly * e;
+    }
+    static __device__ __forceinline__ void k_psi(float rh2, float log2s2, float &k, float &psi) {
+        const float rh = sqrt_approx(rh2);
+        const float e = ex2_approx(fmaf(-rh, kLog2e, log2s2));
+        const float poly = fmaf(rh2, 1.0f / 3.0f, rh) + 1.0f;
+        k = poly * e;
+        psi = (1.0f + rh) * e * (1.0f / 3.0f);
+    }
+};
+
+// ---------------------------------------------------------------- CG state on the device
+
+// Per-column CG scalars (float64) and flags, plus the Lanczos history.
+struct CgState {
+    int iter;          // iterations done (global counter)
+    int done;          // 1 when no column is active or iter reached max_iter
+    int status;        // 0 ok, else an lgp_status (breakdown / nonfinite)
+    int max_iter;
+    int hist_len;      // Lanczos steps kept per column
+    int t;
+    double tol;
+    int active[kMaxT];
+    int iters[kMaxT];
+    double bnorm2[kMaxT];
+    double rr[kMaxT];
+    double alpha[kMaxT];
+    double beta[kMaxT];
+};
+
+// ---------------------------------------------------------------- launchers (defined in the .cu files)
+
+// prep.cu
+void launch_prep_x(const float *X, int64_t N, int D, int dpad, const float *scale_host, float *Xs, int64_t Np,
+                   int *err_flag, cudaStream_t st);
+void launch_rademacher(uint64_t seed, int64_t N, int m, float *Z, int64_t ldz, int col0, cudaStream_t st);
+void launch_scan_finite(const float *A, int64_t n, int *err_flag, cudaStream_t st);
+void launch_copy_cols(const float *src, int64_t lds, float *dst, int64_t ldd, int64_t rows, int cols, int dst_col0,
+                      cudaStream_t st);
+
+// mv_simt.cu
+struct MvLaunch {
+    const KernelParams *kp;
+    const float *Xs;      // prescaled [Np, dpad]
+    int64_t N, Np;
+    const float *V;       // [N, ldv] (rows >= N are never read)
+    int64_t ldv;
+    float *out;           // [N, ldo]
+    int64_t ldo;
+    int t;
+    float *partial;       // split-column partial sums (workspace) or nullptr
+    int64_t partial_cap;  // floats available in partial
+    const int *skip;      // device flag: skip all work when *skip != 0 (may be nullptr)
+    int num_sms;
+};
+cudaError_t launch_mv_simt(const MvLaunch &m, cudaStream_t st);
+int64_t mv_simt_partial_floats(int64_t N, int64_t Np, int t, int num_sms);
+
+cudaError_t launch_mv_grad(const KernelParams &kp, const float *Xs, int64_t N, int64_t Np, const float *W, int t,
+                           float *G, float *partial, int64_t partial_cap, int num_sms, cudaStream_t st);
+int64_t mv_grad_partial_floats(int64_t N, int64_t Np, int t, int D, int num_sms);
+
+// Bilinear adjoint reduction: acc[p] = sum_ij dK_p[i,j] * (A_i . B_j) for p < D (lengthscales), p = D (log s^2).
+cudaError_t launch_adjoint_bilinear(const KernelParams &kp, const float *Xs, int64_t N, int64_t Np, const float *A,
+                                    const float *B, int t, double *block_partials, int64_t partial_cap, int *n_blocks,
+                                    int num_sms, cudaStream_t st);
+int64_t adjoint_partial_doubles(int64_t N, int t, int D, int num_sms);
+
+// mv_tc.cu
+bool tc_supported(int t);
+int64_t tc_vsplit_bytes(int64_t Np, int t);
+cudaError_t launch_mv_tc(const KernelParams &kp, const float *Xs, int64_t N, int64_t Np, const float *V, int64_t ldv,
+                         float *out, int64_t ldo, int t, void *vsplit, float *partial, int64_t partial_cap,
+                         const int *skip, int *err_flag, long long wait_budget, int num_sms, cudaStream_t st);
+int64_t mv_tc_partial_floats(int64_t Np, int t, int num_sms);
+
+// solver.cu
+struct CgBuffers {
+    float *x, *r, *p, *Kp;   // [Np, t]
+    double *partial;         // [G, 2t] block partial dots
+    int G;                   // blocks of the vector kernels
+    CgState *state;
+    double *hist_alpha;      // [hist_len, t]
+    double *hist_beta;       // [hist_len, t]
+};
+void launch_cg_init(const float *B, int64_t ldb, int64_t N, int64_t Np, int t, const CgBuffers &b, double tol,
+                    int max_iter, int hist_len, cudaStream_t st);
+void launch_cg_after_matvec(int64_t N, int64_t Np, int t, const CgBuffers &b, cudaStream_t st);
+void launch_cg_copy_out(const CgBuffers &b, int64_t N, int t, float *Xsol, int64_t ldx, cudaStream_t st);
+int cg_num_blocks(int64_t N, int t, int num_sms);
+
+// Column dot products sum_i A[i,c] B[i,c] and sum_i A[i,c]^2 (float64), c < t: out[2t].
+void launch_col_dots(const float *A, const float *B, int64_t N, int t, double *partial, int G, double *out,
+                     cudaStream_t st);
+// Stochastic Lanczos quadrature over probe columns 1..t-1 and the LML assembly.
+// out: [0] lml, [1] quad, [2] logdet, [3] status flag (0 ok, else nonpositive Ritz value)
+void launch_slq_lml(const CgBuffers &b, int t, int hist_len, const double *dots, int64_t N, double *out,
+                    cudaStream_t st);
+// B'[:,0] = A[:,0]; B'[:,c] = -Z[:,c] / m for c >= 1 (the right factor of the gradient's bilinear form)
+void launch_adjoint_rhs(const float *A, const float *RHS, int64_t N, int t, float *Bp, cudaStream_t st);
+// Sum block partials and form grad[p] = 1/2 acc[p] (p <= D); grad[D+1] from the noise term.
+void launch_grad_finalize(const double *block_partials, int n_blocks, int D, const double *dots, int t, float noise,
+                          double *grad_out, cudaStream_t st);
+
+}  // namespace lgp

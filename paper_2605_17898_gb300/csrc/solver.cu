@@ -1,0 +1,418 @@
+// Conjugate-gradient vector updates, float64 scalar recurrences, stochastic Lanczos
+// quadrature and the LML / gradient assembly.
+//
+// CG (Sec. 2 "CG-based inference"; Sec. 5 "our simpler CG loop"): unpreconditioned,
+// x0 = 0, one recurrence per right-hand-side column, all columns advanced by the
+// same launches. Per iteration, after Kp = K_y p:
+//   alpha_c = r_c^T r_c / p_c^T Kp_c,  x_c += alpha_c p_c,  r_c -= alpha_c Kp_c,
+//   beta_c  = r_c'^T r_c' / r_c^T r_c, p_c = r_c' + beta_c p_c,
+// column c stops once ||r_c|| <= tol ||b_c||. Vectors are float32; the dot products
+// are accumulated in float64 with a fixed reduction order (block partials, then one
+// block sums them in index order), so results are reproducible run to run.
+#include <math.h>
+
+#include "lgp_internal.cuh"
+
+namespace lgp {
+
+namespace {
+
+constexpr int kVecThreads = 256;
+
+// Threads per block for column-interleaved work: a multiple of t not above 256.
+__host__ __device__ inline int vec_block(int t) { return (kVecThreads / t) * t; }
+
+// Block-level per-column reduction of vals (one per thread, column tid % t) into out[c].
+__device__ void block_col_reduce(double v, int t, double *red, double *out_row) {
+    const int tid = threadIdx.x;
+    const int nr = blockDim.x / t;
+    red[tid] = v;
+    __syncthreads();
+    int s = 1;
+    while (s < nr) s <<= 1;
+    for (s >>= 1; s >= 1; s >>= 1) {
+        const int slot = tid / t;
+        if (slot < s && slot + s < nr) red[tid] += red[tid + s * t];
+        __syncthreads();
+    }
+    if (tid < t) out_row[tid] = red[tid];
+}
+
+// Row range of block b when G blocks share N rows.
+__device__ __forceinline__ void block_rows(int64_t N, int64_t *r0, int64_t *r1) {
+    const int64_t per = (N + gridDim.x - 1) / gridDim.x;
+    *r0 = min(N, (int64_t)blockIdx.x * per);
+    *r1 = min(N, *r0 + per);
+}
+
+__global__ void cg_init_kernel(const float *__restrict__ B, int64_t ldb, int64_t N, int t, float *__restrict__ x,
+                               float *__restrict__ r, float *__restrict__ p, double *__restrict__ partial) {
+    __shared__ double red[kVecThreads];
+    int64_t r0, r1;
+    block_rows(N, &r0, &r1);
+    const int c = threadIdx.x % t;
+    double s = 0.0;
+    for (int64_t i = r0 + threadIdx.x / t; i < r1; i += blockDim.x / t) {
+        const float b = B[i * ldb + c];
+        x[i * t + c] = 0.0f;
+        r[i * t + c] = b;
+        p[i * t + c] = b;
+        s += (double)b * (double)b;
+    }
+    block_col_reduce(s, t, red, partial + (int64_t)blockIdx.x * t);
+}
+
+__global__ void cg_init_scalars_kernel(CgState *st, const double *__restrict__ partial, int G, int t, double tol,
+                                       int max_iter, int hist_len) {
+    const int c = threadIdx.x;
+    int any = 0;
+    int bad = 0;
+    if (c < t) {
+        double s = 0.0;
+        for (int b = 0; b < G; ++b) s += partial[(int64_t)b * t + c];
+        st->bnorm2[c] = s;
+        st->rr[c] = s;
+        st->alpha[c] = 0.0;
+        st->beta[c] = 0.0;
+        st->iters[c] = 0;
+        bad = !isfinite(s);
+        const int act = (s > 0.0) && !bad;
+        st->active[c] = act;
+        any = act;
+    }
+    any = __syncthreads_or(any);
+    bad = __syncthreads_or(bad);
+    if (c == 0) {
+        st->iter = 0;
+        st->t = t;
+        st->tol = tol;
+        st->max_iter = max_iter;
+        st->hist_len = hist_len;
+        st->status = bad ? (int)LGP_ERR_NONFINITE : 0;
+        st->done = (!any || bad) ? 1 : 0;
+    }
+}
+
+__global__ void cg_pkp_kernel(const float *__restrict__ p, const float *__restrict__ Kp, int64_t N, int t,
+                              const CgState *st, double *__restrict__ partial) {
+    __shared__ double red[kVecThreads];
+    if (st->done) return;
+    int64_t r0, r1;
+    block_rows(N, &r0, &r1);
+    const int c = threadIdx.x % t;
+    double s = 0.0;
+    for (int64_t i = r0 + threadIdx.x / t; i < r1; i += blockDim.x / t)
+        s += (double)p[i * t + c] * (double)Kp[i * t + c];
+    block_col_reduce(s, t, red, partial + (int64_t)blockIdx.x * t);
+}
+
+__global__ void cg_alpha_kernel(CgState *st, const double *__restrict__ partial, int G, double *hist_alpha) {
+    if (st->done) return;
+    const int c = threadIdx.x;
+    const int t = st->t;
+    int bad = 0, nonfinite = 0;
+    if (c < t) {
+        double alpha = 0.0;
+        if (st->active[c]) {
+            double pkp = 0.0;
+            for (int b = 0; b < G; ++b) pkp += partial[(int64_t)b * t + c];
+            if (!isfinite(pkp)) {
+                nonfinite = 1;
+                st->active[c] = 0;
+            } else if (!(pkp > 0.0)) {
+                bad = 1;
+                st->active[c] = 0;
+            } else {
+                alpha = st->rr[c] / pkp;
+            }
+        }
+        st->alpha[c] = alpha;
+        if (st->iter < st->hist_len) hist_alpha[(int64_t)st->iter * t + c] = alpha;
+    }
+    bad = __syncthreads_or(bad);
+    nonfinite = __syncthreads_or(nonfinite);
+    if (c == 0 && (bad || nonfinite) && st->status == 0)
+        st->status = nonfinite ? (int)LGP_ERR_NONFINITE : (int)LGP_ERR_BREAKDOWN;
+}
+
+__global__ void cg_xr_kernel(float *__restrict__ x, float *__restrict__ r, const float *__restrict__ p,
+                             const float *__restrict__ Kp, int64_t N, int t, const CgState *st,
+                             double *__restrict__ partial) {
+    __shared__ double red[kVecThreads];
+    if (st->done) return;
+    int64_t r0, r1;
+    block_rows(N, &r0, &r1);
+    const int c = threadIdx.x % t;
+    const float alpha = (float)st->alpha[c];
+    double s = 0.0;
+    for (int64_t i = r0 + threadIdx.x / t; i < r1; i += blockDim.x / t) {
+        const int64_t e = i * t + c;
+        float rv = r[e];
+        if (alpha != 0.0f) {
+            x[e] = fmaf(alpha, p[e], x[e]);
+            rv = fmaf(-alpha, Kp[e], rv);
+            r[e] = rv;
+        }
+        s += (double)rv * (double)rv;
+    }
+    block_col_reduce(s, t, red, partial + (int64_t)blockIdx.x * t);
+}
+
+__global__ void cg_beta_kernel(CgState *st, const double *__restrict__ partial, int G, double *hist_beta) {
+    if (st->done) return;
+    const int c = threadIdx.x;
+    const int t = st->t;
+    int any = 0;
+    if (c < t) {
+        double beta = 0.0;
+        if (st->active[c]) {
+            double rr = 0.0;
+            for (int b = 0; b < G; ++b) rr += partial[(int64_t)b * t + c];
+            beta = rr / st->rr[c];
+            st->rr[c] = rr;
+            st->iters[c] += 1;
+            if (!(sqrt(rr) > st->tol * sqrt(st->bnorm2[c]))) st->active[c] = 0;
+        }
+        st->beta[c] = beta;
+        if (st->iter < st->hist_len) hist_beta[(int64_t)st->iter * t + c] = beta;
+        any = st->active[c];
+    }
+    any = __syncthreads_or(any);
+    if (c == 0) {
+        st->iter += 1;
+        if (!any || st->iter >= st->max_iter) st->done = 1;
+    }
+}
+
+__global__ void cg_p_kernel(float *__restrict__ p, const float *__restrict__ r, int64_t N, int t,
+                            const CgState *st) {
+    if (st->done) return;
+    int64_t r0, r1;
+    block_rows(N, &r0, &r1);
+    const int c = threadIdx.x % t;
+    if (!st->active[c]) return;
+    const float beta = (float)st->beta[c];
+    for (int64_t i = r0 + threadIdx.x / t; i < r1; i += blockDim.x / t) {
+        const int64_t e = i * t + c;
+        p[e] = fmaf(beta, p[e], r[e]);
+    }
+}
+
+__global__ void copy_out_kernel(const float *__restrict__ x, int64_t N, int t, float *__restrict__ out, int64_t ldo) {
+    const int64_t total = N * t;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / t;
+        const int c = (int)(e - i * t);
+        out[i * ldo + c] = x[e];
+    }
+}
+
+__global__ void col_dots_kernel(const float *__restrict__ A, const float *__restrict__ B, int64_t N, int t,
+                                double *__restrict__ partial) {
+    __shared__ double red[kVecThreads];
+    int64_t r0, r1;
+    block_rows(N, &r0, &r1);
+    const int c = threadIdx.x % t;
+    double sab = 0.0, saa = 0.0;
+    for (int64_t i = r0 + threadIdx.x / t; i < r1; i += blockDim.x / t) {
+        const double a = A[i * t + c];
+        sab += a * (double)B[i * t + c];
+        saa += a * a;
+    }
+    block_col_reduce(sab, t, red, partial + (int64_t)blockIdx.x * 2 * t);
+    __syncthreads();
+    block_col_reduce(saa, t, red, partial + (int64_t)blockIdx.x * 2 * t + t);
+}
+
+__global__ void col_dots_final_kernel(const double *__restrict__ partial, int G, int t, double *out) {
+    const int c = threadIdx.x;
+    if (c >= 2 * t) return;
+    double s = 0.0;
+    for (int b = 0; b < G; ++b) s += partial[(int64_t)b * 2 * t + c];
+    out[c] = s;
+}
+
+// e_1^T log(T) e_1 for the symmetric tridiagonal T (diagonal a[0..m), off-diagonal b[0..m-1)),
+// by implicit symmetric QR steps with a Wilkinson shift (Golub & Van Loan, Sec. 8.3),
+// carrying u = W e_1 where W is the product of all Givens rotations (so that
+// e_1^T f(T) e_1 = sum_j u_j^2 f(lambda_j)). Arrays are overwritten.
+__device__ double tridiag_e1_log_e1(double *a, double *b, double *u, int m, int *nonpos) {
+    for (int k = 0; k < m; ++k) u[k] = (k == 0) ? 1.0 : 0.0;
+    int hi = m - 1;
+    int steps = 0;
+    const int max_steps = 60 * m + 60;
+    while (hi > 0 && steps < max_steps) {
+        for (int k = 0; k < hi; ++k)
+            if (fabs(b[k]) <= 2.220446049250313e-16 * (fabs(a[k]) + fabs(a[k + 1]))) b[k] = 0.0;
+        if (b[hi - 1] == 0.0) {
+            --hi;
+            continue;
+        }
+        int lo = hi - 1;
+        while (lo > 0 && b[lo - 1] != 0.0) --lo;
+        ++steps;
+        const double dlt = 0.5 * (a[hi - 1] - a[hi]);
+        const double bb = b[hi - 1];
+        const double den = dlt + copysign(hypot(dlt, bb), dlt);
+        const double mu = a[hi] - bb * bb / den;
+        double x = a[lo] - mu;
+        double z = b[lo];
+        for (int k = lo; k < hi; ++k) {
+            const double rr = hypot(x, z);
+            double c = 1.0, s = 0.0;
+            if (rr > 0.0) {
+                c = x / rr;
+                s = z / rr;
+            }
+            if (k > lo) b[k - 1] = rr;
+            const double p = a[k], q = b[k], w = a[k + 1];
+            a[k] = c * c * p + 2.0 * c * s * q + s * s * w;
+            a[k + 1] = s * s * p - 2.0 * c * s * q + c * c * w;
+            b[k] = c * s * (w - p) + (c * c - s * s) * q;
+            if (k + 1 < hi) {
+                z = s * b[k + 1];
+                b[k + 1] = c * b[k + 1];
+                x = b[k];
+            }
+            const double uk = u[k], uk1 = u[k + 1];
+            u[k] = c * uk + s * uk1;
+            u[k + 1] = -s * uk + c * uk1;
+        }
+    }
+    double sum = 0.0;
+    for (int k = 0; k < m; ++k) {
+        if (!(a[k] > 0.0)) {
+            *nonpos = 1;
+            continue;
+        }
+        sum += u[k] * u[k] * log(a[k]);
+    }
+    if (hi > 0) *nonpos = 1;
+    return sum;
+}
+
+// One thread per probe column c = 1..t-1: T_c from the CG coefficients
+// (T[k,k] = 1/alpha_k + beta_{k-1}/alpha_{k-1}, T[k,k+1] = sqrt(beta_k)/alpha_k),
+// gamma_c = ||z_c||^2 e_1^T log(T_c) e_1; logdet = mean_c gamma_c (Sec. 3 "Inference").
+__global__ void slq_lml_kernel(const CgState *st, const double *__restrict__ hist_alpha,
+                               const double *__restrict__ hist_beta, int t, int hist_len,
+                               const double *__restrict__ dots, int64_t N, double *out) {
+    __shared__ double gam[kMaxT];
+    __shared__ int flag[kMaxT];
+    const int c = threadIdx.x;
+    if (c >= 1 && c < t) {
+        double a[kMaxLanczos], b[kMaxLanczos], u[kMaxLanczos];
+        const int m = min(hist_len, st->iters[c]);
+        int nonpos = 0;
+        double g = 0.0;
+        if (m > 0) {
+            for (int k = 0; k < m; ++k) {
+                const double al = hist_alpha[(int64_t)k * t + c];
+                a[k] = 1.0 / al;
+                if (k > 0) a[k] += hist_beta[(int64_t)(k - 1) * t + c] / hist_alpha[(int64_t)(k - 1) * t + c];
+                if (k + 1 < m) b[k] = sqrt(hist_beta[(int64_t)k * t + c]) / al;
+            }
+            g = st->bnorm2[c] * tridiag_e1_log_e1(a, b, u, m, &nonpos);
+        }
+        gam[c] = g;
+        flag[c] = nonpos;
+    }
+    __syncthreads();
+    if (c == 0) {
+        double s = 0.0;
+        int bad = 0;
+        for (int k = 1; k < t; ++k) {
+            s += gam[k];
+            bad |= flag[k];
+        }
+        const double logdet = t > 1 ? s / (t - 1) : 0.0;
+        const double quad = dots[0];
+        out[0] = -0.5 * (quad + logdet + (double)N * 1.8378770664093453);  // log(2 pi)
+        out[1] = quad;
+        out[2] = logdet;
+        out[3] = bad ? 1.0 : 0.0;
+    }
+}
+
+__global__ void adjoint_rhs_kernel(const float *__restrict__ A, const float *__restrict__ RHS, int64_t N, int t,
+                                   float *__restrict__ Bp) {
+    const int64_t total = N * t;
+    const float inv_m = t > 1 ? -1.0f / (float)(t - 1) : 0.0f;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / t;
+        const int c = (int)(e - i * t);
+        Bp[e] = c == 0 ? A[i * t] : inv_m * RHS[e];
+    }
+}
+
+__global__ void grad_finalize_kernel(const double *__restrict__ bp, int n_blocks, int D, const double *__restrict__ dots,
+                                     int t, float noise, double *grad_out) {
+    const int p = threadIdx.x;
+    if (p <= D) {
+        double s = 0.0;
+        for (int b = 0; b < n_blocks; ++b) s += bp[(int64_t)b * (D + 1) + p];
+        grad_out[p] = 0.5 * s;
+    } else if (p == D + 1) {
+        double tr = 0.0;
+        for (int c = 1; c < t; ++c) tr += dots[c];
+        const double m = t > 1 ? (double)(t - 1) : 1.0;
+        grad_out[p] = 0.5 * (double)noise * (dots[t] - tr / m);
+    }
+}
+
+inline int grid_for(int64_t n) {
+    int64_t g = (n + 255) / 256;
+    return (int)(g < 1 ? 1 : (g > 4096 ? 4096 : g));
+}
+
+}  // namespace
+
+int cg_num_blocks(int64_t N, int t, int num_sms) {
+    int64_t g = (N * t + 4095) / 4096;
+    if (g > 2 * num_sms) g = 2 * num_sms;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+void launch_cg_init(const float *B, int64_t ldb, int64_t N, int64_t Np, int t, const CgBuffers &b, double tol,
+                    int max_iter, int hist_len, cudaStream_t st) {
+    (void)Np;
+    cg_init_kernel<<<b.G, vec_block(t), 0, st>>>(B, ldb, N, t, b.x, b.r, b.p, b.partial);
+    cg_init_scalars_kernel<<<1, kMaxT, 0, st>>>(b.state, b.partial, b.G, t, tol, max_iter, hist_len);
+}
+
+void launch_cg_after_matvec(int64_t N, int64_t Np, int t, const CgBuffers &b, cudaStream_t st) {
+    (void)Np;
+    const int bd = vec_block(t);
+    cg_pkp_kernel<<<b.G, bd, 0, st>>>(b.p, b.Kp, N, t, b.state, b.partial);
+    cg_alpha_kernel<<<1, kMaxT, 0, st>>>(b.state, b.partial, b.G, b.hist_alpha);
+    cg_xr_kernel<<<b.G, bd, 0, st>>>(b.x, b.r, b.p, b.Kp, N, t, b.state, b.partial);
+    cg_beta_kernel<<<1, kMaxT, 0, st>>>(b.state, b.partial, b.G, b.hist_beta);
+    cg_p_kernel<<<b.G, bd, 0, st>>>(b.p, b.r, N, t, b.state);
+}
+
+void launch_cg_copy_out(const CgBuffers &b, int64_t N, int t, float *Xsol, int64_t ldx, cudaStream_t st) {
+    copy_out_kernel<<<grid_for(N * t), 256, 0, st>>>(b.x, N, t, Xsol, ldx);
+}
+
+void launch_col_dots(const float *A, const float *B, int64_t N, int t, double *partial, int G, double *out,
+                     cudaStream_t st) {
+    col_dots_kernel<<<G, vec_block(t), 0, st>>>(A, B, N, t, partial);
+    col_dots_final_kernel<<<1, 2 * kMaxT, 0, st>>>(partial, G, t, out);
+}
+
+void launch_slq_lml(const CgBuffers &b, int t, int hist_len, const double *dots, int64_t N, double *out,
+                    cudaStream_t st) {
+    slq_lml_kernel<<<1, kMaxT, 0, st>>>(b.state, b.hist_alpha, b.hist_beta, t, hist_len, dots, N, out);
+}
+
+void launch_adjoint_rhs(const float *A, const float *RHS, int64_t N, int t, float *Bp, cudaStream_t st) {
+    adjoint_rhs_kernel<<<grid_for(N * t), 256, 0, st>>>(A, RHS, N, t, Bp);
+}
+
+void launch_grad_finalize(const double *block_partials, int n_blocks, int D, const double *dots, int t, float noise,
+                          double *grad_out, cudaStream_t st) {
+    grad_finalize_kernel<<<1, 32, 0, st>>>(block_partials, n_blocks, D, dots, t, noise, grad_out);
+}
+
+}  // namespace lgp

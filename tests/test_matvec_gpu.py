@@ -1,0 +1,144 @@
+"""Parity of the fused product K_y V (CUDA, through the C ABI) with the FP64 oracle.
+
+Gate: relative 2-norm error per column <= 1e-5 against the oracle evaluated in
+float64 on the same float32 inputs. Sizes span several row and column tiles
+with ragged tails; full-size workloads are checked on sampled rows.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import gp_oracle as go
+import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+def _colerr(got, ref):
+    got = np.asarray(got, dtype=np.float64).reshape(ref.shape[0], -1)
+    ref = ref.reshape(ref.shape[0], -1)
+    return np.linalg.norm(got - ref, axis=0) / np.linalg.norm(ref, axis=0)
+
+
+def _run(lgp, p, V, prec=None):
+    import torch
+    X = torch.as_tensor(p.X, device="cuda")
+    Vt = torch.as_tensor(V, device="cuda")
+    kw = {} if prec is None else {"prec": prec}
+    out = lgp.lgp_kernel_matvec(X, p, Vt, **kw)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("t", [1, 2, 3, 4, 5, 8, 13, 16, 32, 33])
+@pytest.mark.parametrize("kind", [wl.RBF, wl.MATERN52])
+def test_fp32_matvec_small(lgp, kind, t):
+    p = wl.random_problem(1500, 3, kind, seed=10 + t)
+    V = wl.rhs_block(p.N, t, seed=t)
+    got = _run(lgp, p, V, prec=lgp.LGP_PREC_FP32)
+    ref = go.matvec(p.X, V, go.hyper_of(p))
+    assert _colerr(got, ref).max() <= TOL
+
+
+@pytest.mark.parametrize("D", [1, 2, 3, 4, 5, 6, 7, 8])
+def test_fp32_matvec_every_dimension(lgp, D):
+    p = wl.random_problem(777, D, wl.MATERN52 if D % 2 else wl.RBF, seed=D)
+    V = wl.rhs_block(p.N, 4, seed=D)
+    ref = go.matvec(p.X, V, go.hyper_of(p))
+    assert _colerr(_run(lgp, p, V, prec=lgp.LGP_PREC_FP32), ref).max() <= TOL
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 63, 64, 65, 127, 129, 255, 257, 511, 513, 4099])
+def test_fp32_matvec_ragged_sizes(lgp, N):
+    p = wl.random_problem(N, 2, wl.RBF, seed=N)
+    V = wl.rhs_block(N, 2, seed=N)
+    ref = go.matvec(p.X, V, go.hyper_of(p))
+    assert _colerr(_run(lgp, p, V, prec=lgp.LGP_PREC_FP32), ref).max() <= TOL
+
+
+def test_cfg1_matvec(lgp):
+    p = wl.cfg1()
+    got = _run(lgp, p, p.y[:, None])
+    ref = go.matvec(p.X, p.y[:, None], go.hyper_of(p))
+    assert _colerr(got, ref).max() <= TOL
+
+
+@pytest.mark.parametrize("kind", [wl.RBF, wl.MATERN52])
+def test_cfg2_matvec_full_size_sampled_rows(lgp, kind):
+    """N=20000, D=3, t=1 (the paper's fused-product scale), rows sampled for the oracle."""
+    p = wl.cfg2(kind=kind)
+    got = _run(lgp, p, p.y[:, None], prec=lgp.LGP_PREC_FP32)
+    rows = np.random.default_rng(0).choice(p.N, 300, replace=False)
+    ref = go.matvec_rows(p.X, p.y[:, None], go.hyper_of(p), rows)
+    assert _colerr(got[rows], ref).max() <= TOL
+
+
+def test_cfg3_matvec_full_size_sampled_rows(lgp):
+    """N=100000, D=8, Matern-5/2, t=32: the product inside the mBCG solve."""
+    p = wl.cfg3()
+    V = wl.rhs_block(p.N, 32, seed=3, kind="sign")
+    V[:, 0] = p.y
+    got = _run(lgp, p, V)
+    rows = np.random.default_rng(1).choice(p.N, 256, replace=False)
+    ref, _ = oracle.kyv_rows_c(p.X, V, go.hyper_of(p), rows=rows)
+    assert _colerr(got[rows], ref).max() <= TOL
+
+
+def test_cfg5_large_matvec_sampled_rows(lgp):
+    """N=500000, D=2, RBF, t=32 with N(0,1) columns (O(N) memory: no N x N storage)."""
+    p, V = wl.cfg5_large()
+    got = _run(lgp, p, V)
+    rows = np.random.default_rng(2).choice(p.N, 128, replace=False)
+    ref, _ = oracle.kyv_rows_c(p.X, V, go.hyper_of(p), rows=rows)
+    assert _colerr(got[rows], ref).max() <= TOL
+
+
+def test_matvec_is_linear_and_noise_exact(lgp):
+    """Properties at any size: K_y(aV) = a K_y V; zero outputscale gives sigma^2 V exactly."""
+    p = wl.random_problem(3000, 4, wl.MATERN52, seed=5)
+    V = wl.rhs_block(p.N, 4, seed=5)
+    a = _run(lgp, p, V, prec=lgp.LGP_PREC_FP32)
+    b = _run(lgp, p, 2.0 * V, prec=lgp.LGP_PREC_FP32)
+    np.testing.assert_array_equal(b, 2.0 * a)
+    q = wl.random_problem(3000, 4, wl.RBF, seed=6, log_os=-80.0, log_noise=math.log(0.25))
+    c = _run(lgp, q, V, prec=lgp.LGP_PREC_FP32)
+    np.testing.assert_allclose(c, 0.25 * V, rtol=1e-7, atol=0)
+
+
+def test_matvec_rejects_bad_arguments(lgp):
+    import torch
+    p = wl.random_problem(100, 2, wl.RBF, seed=1)
+    X = torch.as_tensor(p.X, device="cuda")
+    V = torch.ones((100, 2), device="cuda")
+    with pytest.raises(lgp.LGPError) as e:
+        lgp.lgp_kernel_matvec(X, p, V, out=V)
+    assert e.value.status == lgp.LGP_ERR_INVALID_ARG
+    Vh = torch.ones((100, 2))  # host memory
+    with pytest.raises(lgp.LGPError) as e:
+        lgp.lgp_kernel_matvec(X, p, Vh.cuda(), out=torch.empty((100, 2)))
+    assert e.value.status == lgp.LGP_ERR_INVALID_ARG
+    bad = wl.random_problem(100, 9, wl.RBF, seed=2)
+    with pytest.raises(lgp.LGPError) as e:
+        lgp.lgp_kernel_matvec(torch.as_tensor(bad.X, device="cuda"), bad, V)
+    assert e.value.status == lgp.LGP_ERR_UNSUPPORTED
+    with pytest.raises(lgp.LGPError) as e:
+        lgp.lgp_kernel_matvec(X, p, torch.ones((100, 65), device="cuda"))
+    assert e.value.status == lgp.LGP_ERR_UNSUPPORTED
+
+
+def test_matvec_grad_blocks(lgp):
+    """Derivative blocks dK_p W for all P = D + 2 hyperparameters against the oracle."""
+    import torch
+    for kind, D, t in [(wl.RBF, 3, 1), (wl.MATERN52, 5, 4), (wl.RBF, 8, 6), (wl.MATERN52, 2, 9)]:
+        p = wl.random_problem(900 + 7 * t, D, kind, seed=20 + D)
+        W = wl.rhs_block(p.N, t, seed=t)
+        G = lgp.lgp_kernel_matvec_grad(torch.as_tensor(p.X, device="cuda"), p, torch.as_tensor(W, device="cuda"))
+        G = G.cpu().numpy()
+        ref = go.dK_matvec(p.X, W, go.hyper_of(p))
+        assert G.shape == ref.shape
+        for q in range(D + 2):
+            assert _colerr(G[q], ref[q]).max() <= TOL, (kind, D, t, q)
