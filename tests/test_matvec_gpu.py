@@ -142,3 +142,55 @@ def test_matvec_grad_blocks(lgp):
         assert G.shape == ref.shape
         for q in range(D + 2):
             assert _colerr(G[q], ref[q]).max() <= TOL, (kind, D, t, q)
+
+
+# ----------------------------------------------------------------------------- split-BF16 tcgen05 path
+
+@pytest.mark.parametrize("t", [16, 32])
+@pytest.mark.parametrize("kind", [wl.RBF, wl.MATERN52])
+@pytest.mark.parametrize("N", [1, 100, 129, 1500, 4099])
+def test_split_bf16_matvec(lgp, kind, t, N):
+    p = wl.random_problem(N, 3, kind, seed=N + t)
+    V = wl.rhs_block(N, t, seed=N)
+    got = _run(lgp, p, V, prec=lgp.LGP_PREC_SPLIT_BF16)
+    ref = go.matvec(p.X, V, go.hyper_of(p))
+    err = _colerr(got, ref).max()
+    print(f"split-bf16 kind={kind} t={t} N={N}: max column rel err {err:.2e}")
+    assert err <= TOL
+
+
+@pytest.mark.parametrize("D", [1, 2, 3, 4, 5, 6, 7, 8])
+def test_split_bf16_every_dimension(lgp, D):
+    p = wl.random_problem(2000, D, wl.MATERN52 if D % 2 else wl.RBF, seed=40 + D)
+    V = wl.rhs_block(p.N, 32, seed=D, kind="sign")
+    ref = go.matvec(p.X, V, go.hyper_of(p))
+    assert _colerr(_run(lgp, p, V, prec=lgp.LGP_PREC_SPLIT_BF16), ref).max() <= TOL
+
+
+def test_split_bf16_selected_by_auto(lgp):
+    ctx = lgp.default_context()
+    assert ctx.matvec_precision(32) == lgp.LGP_PREC_SPLIT_BF16
+    assert ctx.matvec_precision(16) == lgp.LGP_PREC_SPLIT_BF16
+    assert ctx.matvec_precision(8) == lgp.LGP_PREC_FP32
+    assert ctx.matvec_precision(8, lgp.LGP_PREC_SPLIT_BF16) == lgp.LGP_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("kind", [wl.RBF, wl.MATERN52])
+def test_cfg2_split_bf16_t16_full_size(lgp, kind):
+    """N=20000, D=3, t=16 (y + 15 probes) on the tensor-core path, every row against the C oracle."""
+    p = wl.cfg2(kind=kind, t=16)
+    V = wl.rhs_block(p.N, 16, seed=7, kind="sign")
+    V[:, 0] = p.y
+    got = _run(lgp, p, V)
+    rows = np.random.default_rng(3).choice(p.N, 400, replace=False)
+    ref, _ = oracle.kyv_rows_c(p.X, V, go.hyper_of(p), rows=rows)
+    assert _colerr(got[rows], ref).max() <= TOL
+
+
+def test_split_bf16_agrees_with_fp32_path(lgp):
+    """Two independent GPU routes to the same product agree to the split-BF16 error level."""
+    p = wl.cfg3(N=6000, t=32)
+    V = wl.rhs_block(p.N, 32, seed=9)
+    a = _run(lgp, p, V, prec=lgp.LGP_PREC_FP32).astype(np.float64)
+    b = _run(lgp, p, V, prec=lgp.LGP_PREC_SPLIT_BF16).astype(np.float64)
+    assert (np.linalg.norm(a - b, axis=0) / np.linalg.norm(a, axis=0)).max() <= TOL
