@@ -1,0 +1,394 @@
+"""Benchmark of the matrix-free GP hot path on one or more GB300 GPUs.
+
+One step = one log-marginal-likelihood + gradient evaluation (the path of the
+C ABI entry point lgp_lml_and_grad) on the mBCG workload: N=100,000 points in
+D=8 (X ~ U[-1,1]^8), Matern-5/2 with ARD lengthscales log-spaced over [0.3, 2],
+t=32 right-hand sides (y plus 31 Rademacher probes), 50 Lanczos steps, batched
+CG with the split-BF16 tensor-core product, then the adjoint gradient pass.
+
+value = pair-RHS evaluations per second over the step: every product of the
+step contributes N^2 * t (the CG products and the adjoint pass). ms_per_step is
+the LML+grad time. Multi-GPU: the path of one GP does not shard without an
+exchange, so N GPUs run N independent replicas (weak scaling, no collective on
+the data path; the barrier and the max-over-ranks timing use torch.distributed).
+
+--impl reference times the FP64 CPU oracle as it stands on the host cores, on a
+bounded row sample of the same product.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "matvec pair·RHS evals/s and LML+grad time, N=100k t=32, vs plain FP32 path"
+UNIT = "pair*RHS/s"
+SM_COUNT_NOMINAL = 152
+FP32_LANES_PER_SM = 128
+MAX_SM_MHZ_NOMINAL = 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["lgp", "reference"], default="lgp")
+    ap.add_argument("--N", type=int, default=100000)
+    ap.add_argument("--t", type=int, default=32)
+    ap.add_argument("--lanczos", type=int, default=50)
+    ap.add_argument("--tol", type=float, default=1e-2)
+    ap.add_argument("--max-iter", type=int, default=1000)
+    ap.add_argument("--prec", choices=["auto", "fp32", "split_bf16"], default="auto")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--plain", action="store_true", help="also time the plain FP32 single-RHS path")
+    return ap.parse_args()
+
+
+def dist_init(n_gpus):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if os.environ.get("LGP_BENCH_BACKEND", "nccl") == "nccl" else "gloo"
+        dist.init_process_group(backend=backend)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world, device):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if uuid:
+            cmd[1:1] = ["-i", uuid]
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), float(parts[2]), parts[3:]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [r[0] for r in rows]
+        loaded = [r for r in rows if r[2] > 200.0] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in loaded:
+            for nm, v in zip(names, r[3][1:]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median([r[0] for r in loaded]), "sm_max_mhz": max(r[1] for r in rows),
+                "samples": len(rows), "power_w_max": max(r[2] for r in rows), "reasons": sorted(reasons),
+                "sm_mhz_min": min(sm)}
+
+
+def gpu_uuid(dev_index):
+    try:
+        import torch
+        u = torch.cuda.get_device_properties(dev_index).uuid
+        s = str(u)
+        return s if s.startswith("GPU-") else f"GPU-{s}"
+    except Exception:
+        return None
+
+
+def flush_l2(buf):
+    buf.add_(1.0)
+
+
+def per_pair_ops(kind: int, D: int, split: bool, t: int) -> tuple[float, float]:
+    """Algorithmic FP32-pipe operations and MUFU operations per (i, j) pair.
+
+    Difference form: D subtractions + D multiply-adds for r^2. RBF: one add for the
+    exponent; Matern-5/2: exponent multiply-add, polynomial multiply-add and add,
+    final multiply. Split-BF16: 3 per entry (hi/lo packing halves, one unpack, one
+    subtract); the contraction runs on the tensor pipe. FP32 SIMT: t multiply-adds.
+    MUFU: RBF 1 (ex2), Matern-5/2 2 (sqrt, ex2).
+    """
+    gen = 2 * D + (1 if kind == 0 else 4)
+    mufu = 1.0 if kind == 0 else 2.0
+    return (gen + 3.0, mufu) if split else (gen + t, mufu)
+
+
+def run_cpu_baseline(p, t, seconds, seed=0):
+    """The oracle's FP64 streaming product on a bounded row sample of the workload."""
+    import numpy as np
+    import oracle
+    from oracle import gp_oracle as go
+    import workloads as wl
+    hyp = go.hyper_of(p)
+    V = wl.rhs_block(p.N, t, seed=seed, kind="sign")
+    rng = np.random.default_rng(seed)
+    rows = rng.choice(p.N, 64, replace=False)
+    t0 = time.perf_counter()
+    _, used = oracle.kyv_rows_c(p.X, V, hyp, rows=rows)
+    dt = time.perf_counter() - t0
+    n_rows = int(max(64, min(p.N, 64 * seconds / max(dt, 1e-3))))
+    rows = rng.choice(p.N, n_rows, replace=False)
+    t0 = time.perf_counter()
+    _, used = oracle.kyv_rows_c(p.X, V, hyp, rows=rows)
+    dt = time.perf_counter() - t0
+    value = n_rows * p.N * t / dt
+    return {"value": value, "unit": UNIT, "cores": int(used), "kind": "oracle",
+            "sample": f"{n_rows} sampled rows of K_y V (all {p.N} columns, t={t}), FP64 C/OpenMP row-streamed "
+                      f"oracle; {dt:.1f} s", "seconds": dt}
+
+
+def bench_reference(args, rank, world):
+    """The oracle as it stands, timed on the host cores (rank 0 only)."""
+    import workloads as wl
+    if rank != 0:
+        return
+    p = wl.cfg3(N=args.N, t=args.t)
+    for _ in range(max(args.warmup, 0)):
+        run_cpu_baseline(p, args.t, min(1.0, args.cpu_seconds / 10))
+    vals = []
+    times = []
+    per_step = max(1.0, min(args.cpu_seconds, 60.0 / max(args.steps, 1)))
+    base = None
+    for _ in range(args.steps):
+        base = run_cpu_baseline(p, args.t, per_step)
+        vals.append(base["value"])
+        times.append(base["seconds"])
+    value = statistics.mean(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": p.name, "N": p.N, "D": p.D, "t": args.t, "kernel": "matern52",
+                                            "sample": "row sample of the product per step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": base["cores"], "kind": "oracle",
+                             "sample": base["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_init(args.gpus)
+    if args.impl == "reference":
+        bench_reference(args, rank, world)
+        return
+    import numpy as np
+    import torch
+    import paper_2605_17898_gb300 as lgp
+    import workloads as wl
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    lgp.build.build() if hasattr(lgp, "build") and False else None
+    lgp.load()
+    ctx = lgp.Context(local)
+    prec = {"auto": lgp.LGP_PREC_AUTO, "fp32": lgp.LGP_PREC_FP32, "split_bf16": lgp.LGP_PREC_SPLIT_BF16}[args.prec]
+
+    p = wl.cfg3(N=args.N, t=args.t)
+    m = args.t - 1
+    X = torch.as_tensor(p.X, device=dev)
+    y = torch.as_tensor(p.y, device=dev)
+    flush_buf = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    def step(Xd, yd):
+        return lgp.lgp_lml_and_grad(Xd, yd, p, n_probes=m, lanczos_steps=args.lanczos, seed=1234 + rank,
+                                    tol=args.tol, max_iter=args.max_iter, prec=prec, ctx=ctx)
+
+    for _ in range(args.warmup):
+        step(X, y)
+    torch.cuda.synchronize()
+
+    # ---------------- timed region: K steps, per-step CUDA events, L2 flushed between steps
+    sampler = ClockSampler(gpu_uuid(local)) if rank == 0 else None
+    barrier(world)
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    infos = []
+    for k in range(args.steps):
+        flush_l2(flush_buf)
+        starts[k].record()
+        lml, grad, info = step(X, y)
+        ends[k].record()
+        infos.append(info)
+    torch.cuda.synchronize()
+    barrier(world)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    local_total_s = sum(step_ms) / 1e3
+    total_s = max_over_ranks(local_total_s, world, dev)
+    clocks = sampler.stop() if sampler else None
+
+    iters = [i["iters_max"] for i in infos]
+    chunks = [i["cg_chunks"] for i in infos]
+    # products per step: one per CG iteration replayed (graph chunks of 8 iterations) + the adjoint pass
+    n_products = [8 * c for c in chunks]
+    pairs_rhs = [(n + 1) * float(p.N) ** 2 * args.t for n in n_products]
+    # useful work only: products of iterations that ran (later iterations of a chunk exit early)
+    useful = [(it + 1) * float(p.N) ** 2 * args.t for it in iters]
+    value = sum(useful) * world / total_s
+    ms_per_step = 1e3 * total_s / args.steps
+    launches = int(sum(i["launches"] for i in infos))
+
+    # ---------------- dominant kernel timing on the launching stream (torch's current stream)
+    V = torch.as_tensor(wl.rhs_block(p.N, args.t, seed=3, kind="sign"), device=dev)
+    out = torch.empty_like(V)
+    kprec = ctx.matvec_precision(args.t, prec)
+    for _ in range(2):
+        lgp.lgp_kernel_matvec(X, p, V, prec=kprec, out=out, ctx=ctx)
+    torch.cuda.synchronize()
+    kev = []
+    for _ in range(5):
+        flush_l2(flush_buf)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        lgp.lgp_kernel_matvec(X, p, V, prec=kprec, out=out, ctx=ctx)
+        b.record()
+        kev.append((a, b))
+    torch.cuda.synchronize()
+    mv_ms = statistics.mean(a.elapsed_time(b) for a, b in kev)
+    split = kprec == lgp.LGP_PREC_SPLIT_BF16
+    ops_pair, mufu_pair = per_pair_ops(p.kind, p.D, split, args.t)
+    pairs = float(p.N) ** 2
+    achieved_tops = pairs * ops_pair / (mv_ms / 1e3) / 1e12
+    props = torch.cuda.get_device_properties(local)
+    n_sm = props.multi_processor_count
+    peak_tops = n_sm * FP32_LANES_PER_SM * MAX_SM_MHZ_NOMINAL * 1e6 / 1e12
+    roofline = {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "Tops/s (FP32 pipe)",
+                "frac": achieved_tops / peak_tops, "traffic": None,
+                "kernel": "mv_tc_kernel" if split else "mv_simt_kernel",
+                "per_pair_ops": ops_pair, "mufu_per_pair": mufu_pair, "matvec_ms": mv_ms,
+                "pairs_per_launch": pairs, "sm_count": n_sm, "peak_clock_mhz": MAX_SM_MHZ_NOMINAL}
+
+    # ---------------- end to end through the public API with host buffers
+    Xh = torch.as_tensor(p.X).pin_memory()
+    yh = torch.as_tensor(p.y).pin_memory()
+    Xd = torch.empty_like(X)
+    yd = torch.empty_like(y)
+    e2e_ms = []
+    e2e_iters = []
+    for k in range(max(2, min(args.steps, 3))):
+        flush_l2(flush_buf)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        Xd.copy_(Xh, non_blocking=True)
+        yd.copy_(yh, non_blocking=True)
+        lml_e, grad_e, info_e = step(Xd, yd)  # returns host scalars (device->host read inside)
+        b.record()
+        torch.cuda.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+        e2e_iters.append(info_e["iters_max"])
+    e2e_value = statistics.mean((it + 1) * float(p.N) ** 2 * args.t / (ms / 1e3)
+                                for it, ms in zip(e2e_iters, e2e_ms)) * world
+    cg_state_bytes = 2592
+    d2h = cg_state_bytes + (2 * 64 + 4 + 10) * 8 + 16 + 4 * statistics.mean(chunks)
+    e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(Xh.numel() * 4 + yh.numel() * 4),
+           "d2h_bytes_per_step": int(d2h), "ms_per_step": statistics.mean(e2e_ms)}
+
+    plain = None
+    if args.plain:
+        plain = bench_plain(lgp, ctx, p, X, y, args, dev)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = run_cpu_baseline(p, args.t, args.cpu_seconds)
+        cpu.pop("seconds", None)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+bf16x3" if split else "f32", "data": "synthetic",
+            "config": {"workload": p.name, "N": p.N, "D": p.D, "t": args.t, "kernel": "matern52",
+                       "lanczos_steps": args.lanczos, "tol": args.tol, "max_iter": args.max_iter,
+                       "cg_iterations": iters, "precision": "split_bf16" if split else "fp32",
+                       "l2": "flushed between steps (256 MB write outside the step events)",
+                       "parallelism": f"replicas{world}"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+            "lml": lml, "grad": [float(g) for g in grad],
+        }
+        if plain is not None:
+            line["plain_fp32"] = plain
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def bench_plain(lgp, ctx, p, X, y, args, dev):
+    """The plain FP32 path: single-RHS SIMT products, one CG solve per right-hand side."""
+    import numpy as np
+    import torch
+    from oracle import gp_oracle as go  # probes from the same generator definition (host side only)
+    m = args.t - 1
+    Z = lgp.lgp_rademacher_probes(1234, p.N, m, device=dev.index, ctx=ctx)
+    cols = [y.reshape(-1, 1)] + [Z[:, c:c + 1].contiguous() for c in range(m)]
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    iters = []
+    for c in cols:
+        _, it, _, _ = lgp.lgp_cg_solve(X, p, c, tol=args.tol, max_iter=args.max_iter, prec=lgp.LGP_PREC_FP32,
+                                       ctx=ctx)
+        iters.append(int(it[0]))
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    return {"ms_solves": ms, "iters": iters, "note": "t single-RHS FP32 CG solves (no adjoint pass)"}
+
+
+if __name__ == "__main__":
+    main()

@@ -62,13 +62,22 @@ typedef enum {
 
 typedef enum { LGP_RBF = 0, LGP_MATERN52 = 1 } lgp_kernel;
 
-/* Arithmetic of the K_y V contraction. FP32: entries and products in float32
- * FMA (one RHS column or a few). SPLIT_BF16: entries generated in float32,
- * split as k = hi + lo with hi = bf16_rn(k), lo = bf16_rn(k - hi) (likewise V),
- * and contracted on tcgen05 tensor cores as hi*hi + hi*lo + lo*hi with float32
- * accumulation; needs t in {16, 32}. AUTO picks SPLIT_BF16 for t in {16, 32}
- * and FP32 otherwise. */
-typedef enum { LGP_PREC_AUTO = 0, LGP_PREC_FP32 = 1, LGP_PREC_SPLIT_BF16 = 2 } lgp_precision;
+/* Arithmetic of the K_y V contraction.
+ * FP32: entries and products in float32 FMA (any t).
+ * SPLIT_BF16: entries generated in float32, split as k = hi + lo with
+ *   hi = bf16_rn(k), lo = bf16_rn(k - hi) (likewise V), contracted on tcgen05
+ *   tensor cores as hi*hi + hi*lo + lo*hi with float32 accumulation (about 16
+ *   significant bits per factor); t in {16, 32}.
+ * SPLIT_F16: the same three-product contraction on float16 halves of values
+ *   scaled by exact powers of two (entries by 2^15 / s^2, each V column so that
+ *   its largest magnitude is below 2^15), about 22 bits per factor; t in {16, 32}.
+ * AUTO picks SPLIT_F16 for t in {16, 32} and FP32 otherwise. */
+typedef enum {
+    LGP_PREC_AUTO = 0,
+    LGP_PREC_FP32 = 1,
+    LGP_PREC_SPLIT_BF16 = 2,
+    LGP_PREC_SPLIT_F16 = 3
+} lgp_precision;
 
 typedef struct {
     int32_t kind;                  /* lgp_kernel */
@@ -96,6 +105,8 @@ typedef struct {
     int32_t iters_min;       /* fewest CG iterations over the columns */
     int32_t t;               /* columns solved (1 + n_probes) */
     int32_t prec_used;       /* lgp_precision actually used for the products */
+    int32_t launches;        /* kernel launches this call made on the device */
+    int32_t cg_chunks;       /* CUDA-graph replays of the CG iteration chunk */
 } lgp_lml_info;
 
 typedef struct lgp_ctx lgp_ctx;

@@ -37,6 +37,7 @@ LGP_MATERN52 = 1
 LGP_PREC_AUTO = 0
 LGP_PREC_FP32 = 1
 LGP_PREC_SPLIT_BF16 = 2
+LGP_PREC_SPLIT_F16 = 3
 
 EXPORTED = [
     "lgp_version", "lgp_status_string", "lgp_create", "lgp_destroy", "lgp_last_error_message",
@@ -59,7 +60,8 @@ class lgp_options(ctypes.Structure):
 class lgp_lml_info(ctypes.Structure):
     _fields_ = [("lml", ctypes.c_double), ("quad", ctypes.c_double), ("logdet", ctypes.c_double),
                 ("max_rel_resid", ctypes.c_double), ("iters_max", ctypes.c_int32), ("iters_min", ctypes.c_int32),
-                ("t", ctypes.c_int32), ("prec_used", ctypes.c_int32)]
+                ("t", ctypes.c_int32), ("prec_used", ctypes.c_int32), ("launches", ctypes.c_int32),
+                ("cg_chunks", ctypes.c_int32)]
 
 
 _lib = None

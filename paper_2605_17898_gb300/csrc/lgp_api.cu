@@ -152,10 +152,14 @@ lgp_status make_params(lgp_ctx *ctx, const lgp_hyper *h, KernelParams *kp) {
 // Resolve the product arithmetic for t columns.
 int resolve_prec(int t, int prec) {
     if (prec == LGP_PREC_FP32) return LGP_PREC_FP32;
-    if (prec == LGP_PREC_SPLIT_BF16) return tc_supported(t) ? LGP_PREC_SPLIT_BF16 : (int)LGP_ERR_UNSUPPORTED;
-    if (prec == LGP_PREC_AUTO) return tc_supported(t) ? LGP_PREC_SPLIT_BF16 : LGP_PREC_FP32;
+    if (prec == LGP_PREC_SPLIT_BF16 || prec == LGP_PREC_SPLIT_F16)
+        return tc_supported(t) ? prec : (int)LGP_ERR_UNSUPPORTED;
+    if (prec == LGP_PREC_AUTO) return tc_supported(t) ? LGP_PREC_SPLIT_F16 : LGP_PREC_FP32;
     return LGP_ERR_INVALID_ARG;
 }
+
+bool is_tc(int prec) { return prec == LGP_PREC_SPLIT_BF16 || prec == LGP_PREC_SPLIT_F16; }
+int tc_fmt(int prec) { return prec == LGP_PREC_SPLIT_F16 ? 1 : 0; }
 
 struct Prepared {
     KernelParams kp;
@@ -181,13 +185,14 @@ lgp_status prepare_x(lgp_ctx *ctx, const lgp_hyper *hyp, const float *X, int64_t
 // K_y V for prepared X. V has row stride ldv; out has row stride ldo.
 lgp_status matvec_prepared(lgp_ctx *ctx, const Prepared &pp, const float *V, int64_t ldv, float *out, int64_t ldo,
                            int t, int prec, const int *skip, cudaStream_t st) {
-    if (prec == LGP_PREC_SPLIT_BF16) {
+    if (is_tc(prec)) {
         lgp_status s = ensure(ctx, ctx->vsplit, (size_t)tc_vsplit_bytes(pp.Np, t));
         if (s != LGP_OK) return s;
         const int64_t pf = mv_tc_partial_floats(pp.Np, t, ctx->num_sms);
         s = ensure(ctx, ctx->mv_partial, (size_t)std::max<int64_t>(pf, 1) * sizeof(float));
         if (s != LGP_OK) return s;
-        LGP_CUDA(launch_mv_tc(pp.kp, pp.xs, pp.N, pp.Np, V, ldv, out, ldo, t, ctx->vsplit.p, (float *)ctx->mv_partial.p,
+        LGP_CUDA(launch_mv_tc(pp.kp, pp.xs, pp.N, pp.Np, V, ldv, out, ldo, t, tc_fmt(prec), ctx->vsplit.p,
+                              (float *)ctx->mv_partial.p,
                               (int64_t)(ctx->mv_partial.bytes / sizeof(float)), skip, (int *)ctx->flags.p + 1,
                               ctx->wait_budget, ctx->num_sms, st));
         return LGP_OK;
@@ -247,14 +252,24 @@ lgp_status cg_buffers(lgp_ctx *ctx, int64_t N, int64_t Np, int t, int hist_len, 
 }
 
 // Run CG on the internal stream: init, then replay a captured chunk of iterations until done.
+int matvec_launches(const lgp_ctx *ctx, const Prepared &pp, int t, int prec) {
+    return is_tc(prec) ? mv_tc_launches(pp.Np, t, ctx->num_sms, tc_fmt(prec))
+                       : mv_simt_launches(pp.N, pp.Np, t, ctx->num_sms);
+}
+
+// Kernel launches of one CG iteration (the product plus the five vector/scalar kernels).
+int cg_iteration_launches(const lgp_ctx *ctx, const Prepared &pp, int t, int prec) {
+    return matvec_launches(ctx, pp, t, prec) + 5;
+}
+
 lgp_status run_cg(lgp_ctx *ctx, const Prepared &pp, const float *B, int64_t ldb, int t, const lgp_options *opt,
-                  int hist_len, int prec, CgBuffers *bout) {
+                  int hist_len, int prec, CgBuffers *bout, int *chunks_run = nullptr) {
     cudaStream_t st = ctx->work;
     CgBuffers b;
     lgp_status s = cg_buffers(ctx, pp.N, pp.Np, t, hist_len, &b);
     if (s != LGP_OK) return s;
     // the product's own workspace must exist before capture (no allocation inside a capture)
-    if (prec == LGP_PREC_SPLIT_BF16) {
+    if (is_tc(prec)) {
         if ((s = ensure(ctx, ctx->vsplit, (size_t)tc_vsplit_bytes(pp.Np, t))) != LGP_OK) return s;
         const int64_t pf = mv_tc_partial_floats(pp.Np, t, ctx->num_sms);
         if ((s = ensure(ctx, ctx->mv_partial, (size_t)std::max<int64_t>(pf, 1) * sizeof(float))) != LGP_OK) return s;
@@ -313,8 +328,10 @@ lgp_status run_cg(lgp_ctx *ctx, const Prepared &pp, const float *B, int64_t ldb,
     // Replay chunks; the host checks the done flag of chunk k while chunk k+1 runs.
     const int max_chunks = (opt->max_iter + kChunk - 1) / kChunk + 1;
     int prev = -1;
+    int launched = 0;
     for (int k = 0; k < max_chunks; ++k) {
         LGP_CUDA(cudaGraphLaunch(ctx->cg_exec, st));
+        ++launched;
         const int slot = k & 1;
         LGP_CUDA(cudaMemcpyAsync(ctx->h_done + slot, &b.state->done, sizeof(int), cudaMemcpyDeviceToHost, st));
         LGP_CUDA(cudaEventRecord(ctx->ev_chunk[slot], st));
@@ -326,6 +343,7 @@ lgp_status run_cg(lgp_ctx *ctx, const Prepared &pp, const float *B, int64_t ldb,
     }
     LGP_CUDA(cudaMemcpyAsync(ctx->h_state, b.state, sizeof(CgState), cudaMemcpyDeviceToHost, st));
     *bout = b;
+    if (chunks_run) *chunks_run = launched;
     return LGP_OK;
 }
 
@@ -577,7 +595,8 @@ lgp_status lgp_lml_and_grad(lgp_ctx *ctx, const lgp_hyper *hyp, const float *X, 
     launch_rademacher(opt->seed, N, t - 1, rhs, t, 1, st);
     LGP_CUDA(cudaGetLastError());
     CgBuffers b;
-    if ((s = run_cg(ctx, pp, rhs, t, t, opt, L, prec, &b)) != LGP_OK) return s;
+    int chunks = 0;
+    if ((s = run_cg(ctx, pp, rhs, t, t, opt, L, prec, &b, &chunks)) != LGP_OK) return s;
     // scalars: dots[0..2t), slq[4], grad[D+2]
     const int G = b.G;
     if ((s = ensure(ctx, ctx->scal, (size_t)(2 * kMaxT + 4 + kMaxD + 2) * sizeof(double))) != LGP_OK) return s;
@@ -621,6 +640,9 @@ lgp_status lgp_lml_and_grad(lgp_ctx *ctx, const lgp_hyper *hyp, const float *X, 
         info->iters_max = *std::max_element(it.begin(), it.end());
         info->iters_min = *std::min_element(it.begin(), it.end());
         info->max_rel_resid = *std::max_element(rel.begin(), rel.end());
+        info->cg_chunks = chunks;
+        // prep_x, y copy, probes, CG init (2), the replayed chunks, column dots (2), SLQ, adjoint (3)
+        info->launches = 3 + 2 + chunks * kChunk * cg_iteration_launches(ctx, pp, t, prec) + 2 + 1 + (grad ? 3 : 0);
     }
     return cs;
 }

@@ -124,6 +124,7 @@ struct MvLaunch {
     int num_sms;
 };
 cudaError_t launch_mv_simt(const MvLaunch &m, cudaStream_t st);
+int mv_simt_launches(int64_t N, int64_t Np, int t, int num_sms);
 int64_t mv_simt_partial_floats(int64_t N, int64_t Np, int t, int num_sms);
 
 cudaError_t launch_mv_grad(const KernelParams &kp, const float *Xs, int64_t N, int64_t Np, const float *W, int t,
@@ -139,10 +140,12 @@ int64_t adjoint_partial_doubles(int64_t N, int t, int D, int num_sms);
 // mv_tc.cu
 bool tc_supported(int t);
 int64_t tc_vsplit_bytes(int64_t Np, int t);
+// fmt: 0 = bfloat16 halves, 1 = scaled float16 halves
 cudaError_t launch_mv_tc(const KernelParams &kp, const float *Xs, int64_t N, int64_t Np, const float *V, int64_t ldv,
-                         float *out, int64_t ldo, int t, void *vsplit, float *partial, int64_t partial_cap,
+                         float *out, int64_t ldo, int t, int fmt, void *vsplit, float *partial, int64_t partial_cap,
                          const int *skip, int *err_flag, long long wait_budget, int num_sms, cudaStream_t st);
 int64_t mv_tc_partial_floats(int64_t Np, int t, int num_sms);
+int mv_tc_launches(int64_t Np, int t, int num_sms, int fmt);
 
 // solver.cu
 struct CgBuffers {

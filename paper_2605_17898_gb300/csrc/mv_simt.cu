@@ -81,6 +81,10 @@ int64_t mv_simt_partial_floats(int64_t N, int64_t Np, int t, int num_sms) {
     return S > 1 ? S * Np * t : 0;
 }
 
+int mv_simt_launches(int64_t N, int64_t Np, int t, int num_sms) {
+    return mv_simt_partial_floats(N, Np, t, num_sms) > 0 ? 2 : 1;
+}
+
 cudaError_t launch_mv_simt(const MvLaunch &m, cudaStream_t st) {
     const SimtShape sh = simt_shape(m.t);
     const int64_t BM = (int64_t)kSimtThreads * sh.R;

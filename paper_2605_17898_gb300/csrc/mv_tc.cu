@@ -1,428 +1,65 @@
-// Split-BF16 tensor-core product K_y V on tcgen05 (sm_103a), for t in {16, 32}.
-//
-// Arithmetic. Each kernel entry k (generated in float32 registers, never stored to
-// global memory) is split as k = hi + lo with hi = bf16_rn(k), lo = bf16_rn(k - hi);
-// the block V is split the same way once per call. The contraction is
-//   out = K_hi V_hi + K_hi V_lo + K_lo V_hi   (float32 accumulation in tensor memory)
-// which keeps about 16 significant bits of each factor; the dropped K_lo V_lo term is
-// below 2^-16 of each product.
-//
-// CTA structure (one CTA per SM: 10 warps, ~170 KB shared memory):
-//   warps 0-7  generate the 128 x 64 entry tile of each column chunk in registers and
-//              write its hi/lo halves to shared memory in the K-major no-swizzle layout the
-//              MMA reads; warps 0-3 also run the epilogue (TMEM -> registers -> HBM);
-//   warp 8     producer: TMA (cp.async.bulk.tensor) of the prescaled x_j tile and of the
-//              pre-split V_hi / V_lo tiles into a 4-stage ring;
-//   warp 9     allocates the tensor-memory accumulator (128 lanes x t float32 columns) and
-//              one elected thread issues the tcgen05.mma instructions (M=128, N=t, K=16,
-//              three per K step) and commits them to the ring's "empty" barriers.
-// A CTA owns 128 output rows and a range of 64-column chunks; when the grid splits the
-// column range, each CTA writes float32 partial sums that a second kernel reduces in a
-// fixed order.
-//
-// Every wait on an mbarrier is bounded by a cycle budget: a wait that runs out records
-// an error code in a device word, raises a CTA-wide abort flag, and all roles leave their
-// loops; the producer then waits (bounded) for its own copies in flight, the MMA thread
-// for its own MMAs, and the TMEM accumulator is freed before the CTA exits.
-#include <cuda.h>
-#include <cuda_bf16.h>
-#include <cuda_runtime.h>
-
+// Host side of the split tensor-core product: V splitting, tensor maps, grid shape, launch.
 #include <algorithm>
 
-#include "lgp_internal.cuh"
+#include "mv_tc_inst.cuh"
 
 namespace lgp {
 
 namespace {
 
-constexpr int kStages = 4;
-constexpr int kBM = 128;          // rows per CTA (MMA M)
-constexpr int kBK = 64;           // columns j per chunk (4 MMA K steps)
-constexpr int kGenWarps = 8;
-constexpr int kThreads = 320;     // 8 generation warps + producer warp + MMA warp
-constexpr long long kDrainBudget = 2000000000LL;
+using tc::kBK;
+using tc::kBM;
 
-// error codes written to the device error word on a timeout
-constexpr int kErrWaitFull = 0x10, kErrWaitEmpty = 0x20, kErrWaitReady = 0x40, kErrWaitAcc = 0x80;
-
-template <int T, int DP>
-struct TcLayout {
-    static constexpr int kA = kBM * kBK * 2;    // one bf16 half of the entry tile
-    static constexpr int kB = T * kBK * 2;      // one bf16 half of the V tile
-    static constexpr int kX = kBK * DP * 4;     // prescaled x_j tile
-    static constexpr int kStage = 2 * kA + 2 * kB + kX;
-    static constexpr int kBar = kStages * kStage;      // barriers after the ring
-    // + barriers/flags, alignment slack, and a 32 KB guard band after the ring so that no
-    // descriptor-addressed read of the last stage can leave the CTA's allocation
-    static constexpr int kBytes = kBar + 256 + 1024 + 32768;
-};
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+// Per-column largest |V| as float bits (non-negative floats order like their bit patterns).
+__global__ void col_absmax_kernel(const float *__restrict__ V, int64_t ldv, int64_t N, int T,
+                                  unsigned int *__restrict__ vmax, const int *skip) {
+    if (skip && *skip) return;
+    const int c = threadIdx.x % T;
+    unsigned int m = 0;
+    for (int64_t j = (int64_t)blockIdx.x * (blockDim.x / T) + threadIdx.x / T; j < N;
+         j += (int64_t)gridDim.x * (blockDim.x / T))
+        m = max(m, __float_as_uint(fabsf(V[j * ldv + c])));
+    atomicMax(vmax + c, m);
 }
 
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-    uint64_t st;
-    asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(st) : "r"(bar) : "memory");
-    (void)st;
+// Power-of-two exponent e_c with max_c * 2^e_c < 2^15 (clamped to keep the epilogue factor normal).
+__device__ __forceinline__ int col_exponent(unsigned int maxbits) {
+    const float m = __uint_as_float(maxbits);
+    if (!(m > 0.0f) || !isfinite(m)) return 0;
+    int ex;
+    frexpf(m, &ex);  // m = f * 2^ex, f in [0.5, 1): m < 2^ex
+    return min(60, max(-60, 15 - ex));
 }
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
-    uint64_t st;
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;" : "=l"(st) : "r"(bar), "r"(bytes) : "memory");
-    (void)st;
-}
-
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait for the phase with the given parity. Returns false on timeout or abort.
-__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long budget, volatile int *abort_flag,
-                                       int *err, int code) {
-    if (mbar_try(bar, parity)) return true;
-    const long long t0 = clock64();
-    while (true) {
-        if (mbar_try(bar, parity)) return true;
-        if (*abort_flag) return false;
-        if (clock64() - t0 > budget) {
-            *abort_flag = 1;
-            atomicOr(err, code);
-            return false;
-        }
-    }
-}
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int c0, int c1, uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
-            "r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
-        : "memory");
-}
-
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// Shared-memory matrix descriptor, K-major, no swizzle: core matrices of 8 rows x 16 bytes;
-// lbo = byte distance between core matrices adjacent along K, sbo = along M/N.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-    uint64_t d = 0;
-    d |= (uint64_t)((addr >> 4) & 0x3FFF);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
-    d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
-    return d;                // base offset 0, swizzle mode 0 (none)
-}
-
-// Instruction descriptor: kind::f16, A = B = bf16 (K-major), D = f32, M = 128, N = T.
-template <int T>
-__device__ __forceinline__ uint32_t instr_desc() {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(T >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc)
-        : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-
-template <int N>
-__device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t (&r)[N]);
-
-template <>
-__device__ __forceinline__ void tmem_ld<16>(uint32_t taddr, uint32_t (&r)[16]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-}
-
-template <>
-__device__ __forceinline__ void tmem_ld<32>(uint32_t taddr, uint32_t (&r)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
-        "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-}
-
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-
-__device__ __forceinline__ uint32_t pack_bf16x2(float lo_elem, float hi_elem) {
-    __nv_bfloat162 h = __floats2bfloat162_rn(lo_elem, hi_elem);
-    return *reinterpret_cast<uint32_t *>(&h);
-}
-
-__device__ __forceinline__ void unpack_bf16x2(uint32_t u, float &a, float &b) {
-    a = __uint_as_float(u << 16);
-    b = __uint_as_float(u & 0xFFFF0000u);
-}
-
-struct TcArgs {
-    const float *Xs;     // prescaled x [Np, DP] (the rows of this CTA)
-    const float *V;      // user V [N, ldv] (for the sigma^2 V term)
-    float *out;          // [N, ldo] or nullptr in split mode
-    float *partial;      // [S, Np, T] in split mode
-    const int *skip;
-    int *err;
-    int64_t N, Np, ldv, ldo;
-    int chunks_per_split;
-    int total_chunks;
-    float log2s2;
-    float noise;
-    long long budget;
-};
-
-template <int KIND, int D, int T>
-__global__ void __launch_bounds__(kThreads, 1)
-    mv_tc_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ CUtensorMap tm_vh,
-                 const __grid_constant__ CUtensorMap tm_vl, const TcArgs a) {
-    constexpr int DP = D <= 4 ? 4 : 8;
-    using L = TcLayout<T, DP>;
-    extern __shared__ uint8_t smem_raw[];
-    if (a.skip && *a.skip) return;
-
-    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L::kBar);
-    // bars: full[4], ready[4], empty[4], acc
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + L::kBar + 128);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + L::kBar + 136);
-
-    const int warp = threadIdx.x >> 5;
-    const int lane = threadIdx.x & 31;
-    const int64_t row0 = (int64_t)blockIdx.x * kBM;
-    const int c_begin = blockIdx.y * a.chunks_per_split;
-    const int c_end = min(a.total_chunks, c_begin + a.chunks_per_split);
-    const int n_it = c_end - c_begin;
-
-    auto bar_full = [&](int s) { return smem_u32(&bars[s]); };
-    auto bar_ready = [&](int s) { return smem_u32(&bars[kStages + s]); };
-    auto bar_empty = [&](int s) { return smem_u32(&bars[2 * kStages + s]); };
-    const uint32_t bar_acc = smem_u32(&bars[3 * kStages]);
-
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s) {
-            mbar_init(bar_full(s), 1);
-            mbar_init(bar_ready(s), kGenWarps);
-            mbar_init(bar_empty(s), 1);
-        }
-        mbar_init(bar_acc, 1);
-        *abort_flag = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        fence_async_smem();
-    }
-    if (warp == 9) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_u32(tmem_slot))
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem_acc = *tmem_slot;
-
-    if (warp == 8) {
-        // ------------------------------------------------------------ producer (TMA)
-        int last_it[kStages];
-        for (int s = 0; s < kStages; ++s) last_it[s] = -1;
-        if (lane == 0) {
-            for (int it = 0; it < n_it; ++it) {
-                const int s = it % kStages;
-                if (it >= kStages &&
-                    !mbar_wait(bar_empty(s), ((it / kStages) - 1) & 1, a.budget, abort_flag, a.err, kErrWaitEmpty))
-                    break;
-                uint8_t *st = smem + s * L::kStage;
-                const int q = c_begin + it;
-                mbar_arrive_expect_tx(bar_full(s), (uint32_t)(2 * L::kB + L::kX));
-                tma_load_2d(smem_u32(st + 2 * L::kA + 2 * L::kB), &tm_x, 0, q * kBK, bar_full(s));
-                tma_load_2d(smem_u32(st + 2 * L::kA), &tm_vh, 0, q * T, bar_full(s));
-                tma_load_2d(smem_u32(st + 2 * L::kA + L::kB), &tm_vl, 0, q * T, bar_full(s));
-                last_it[s] = it;
-            }
-            if (*abort_flag) {
-                // drain the copies this thread issued
-                for (int s = 0; s < kStages; ++s) {
-                    if (last_it[s] < 0) continue;
-                    volatile int no_abort = 0;
-                    mbar_wait(bar_full(s), (last_it[s] / kStages) & 1, kDrainBudget, &no_abort, a.err, 0);
-                }
-            }
-        }
-    } else if (warp == 9) {
-        // ------------------------------------------------------------ MMA issuer
-        if (lane == 0) {
-            const uint32_t idesc = instr_desc<T>();
-            bool issued = false;
-            for (int it = 0; it < n_it; ++it) {
-                const int s = it % kStages;
-                if (!mbar_wait(bar_ready(s), (it / kStages) & 1, a.budget, abort_flag, a.err, kErrWaitReady)) break;
-                tc_fence_after();
-                const uint32_t st = smem_u32(smem + s * L::kStage);
-                const uint32_t a_hi = st, a_lo = st + L::kA, b_hi = st + 2 * L::kA, b_lo = b_hi + L::kB;
-#pragma unroll
-                for (int ks = 0; ks < kBK / 16; ++ks) {
-                    // A: core matrix (row group rg, k group kg) at (kg * 16 + rg) * 128 bytes
-                    const uint64_t dah = smem_desc(a_hi + ks * 4096, 2048, 128);
-                    const uint64_t dal = smem_desc(a_lo + ks * 4096, 2048, 128);
-                    // B: core matrix (column group cg, k group kg) at (kg * T/8 + cg) * 128 bytes
-                    const uint64_t dbh = smem_desc(b_hi + ks * 2 * T * 16, T * 16, 128);
-                    const uint64_t dbl = smem_desc(b_lo + ks * 2 * T * 16, T * 16, 128);
-                    mma_bf16(tmem_acc, dah, dbh, idesc, (it > 0 || ks > 0) ? 1u : 0u);
-                    mma_bf16(tmem_acc, dah, dbl, idesc, 1u);
-                    mma_bf16(tmem_acc, dal, dbh, idesc, 1u);
-                }
-                mma_commit(bar_empty(s));
-                issued = true;
-            }
-            if (issued) mma_commit(bar_acc);
-            if (*abort_flag && issued) {
-                volatile int no_abort = 0;
-                mbar_wait(bar_acc, 0, kDrainBudget, &no_abort, a.err, 0);
-            }
-        }
-    } else {
-        // ------------------------------------------------------------ generation (warps 0-7)
-        const int kg = warp;  // this warp's 8-column group of every chunk
-        // this thread's 4 rows of the prescaled x (row0 + 127 < Np because Np % 256 == 0)
-        float xi[4][D];
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const float *xr = a.Xs + (row0 + 32 * r + lane) * DP;
-#pragma unroll
-            for (int d = 0; d < D; ++d) xi[r][d] = xr[d];
-        }
-        bool ok = true;
-        for (int it = 0; it < n_it; ++it) {
-            const int s = it % kStages;
-            const bool got = mbar_wait(bar_full(s), (it / kStages) & 1, a.budget, abort_flag, a.err, kErrWaitFull);
-            if (!__all_sync(0xffffffffu, got)) {
-                ok = false;
-                break;
-            }
-            uint8_t *st = smem + s * L::kStage;
-            const float *xs = reinterpret_cast<const float *>(st + 2 * L::kA + 2 * L::kB);
-            float xj[8][D];
-#pragma unroll
-            for (int jj = 0; jj < 8; ++jj) {
-                const float *p = xs + (8 * kg + jj) * DP;
-                const float4 q0 = *reinterpret_cast<const float4 *>(p);
-                xj[jj][0] = q0.x;
-                if (D > 1) xj[jj][1 < D ? 1 : 0] = q0.y;
-                if (D > 2) xj[jj][2 < D ? 2 : 0] = q0.z;
-                if (D > 3) xj[jj][3 < D ? 3 : 0] = q0.w;
-                if (DP == 8) {
-                    const float4 q1 = *reinterpret_cast<const float4 *>(p + 4);
-                    if (D > 4) xj[jj][4 < D ? 4 : 0] = q1.x;
-                    if (D > 5) xj[jj][5 < D ? 5 : 0] = q1.y;
-                    if (D > 6) xj[jj][6 < D ? 6 : 0] = q1.z;
-                    if (D > 7) xj[jj][7 < D ? 7 : 0] = q1.w;
-                }
-            }
-            uint8_t *ahi = st;
-            uint8_t *alo = st + L::kA;
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                float k[8];
-#pragma unroll
-                for (int jj = 0; jj < 8; ++jj) {
-                    float d0 = xi[r][0] - xj[jj][0];
-                    float r2 = d0 * d0;
-#pragma unroll
-                    for (int d = 1; d < D; ++d) {
-                        const float dd = xi[r][d] - xj[jj][d];
-                        r2 = fmaf(dd, dd, r2);
-                    }
-                    k[jj] = Entry<KIND>::k(r2, a.log2s2);
-                }
-                uint32_t h[4], l[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    h[u] = pack_bf16x2(k[2 * u], k[2 * u + 1]);
-                    float h0, h1;
-                    unpack_bf16x2(h[u], h0, h1);
-                    l[u] = pack_bf16x2(k[2 * u] - h0, k[2 * u + 1] - h1);
-                }
-                const int rg = 4 * r + (lane >> 3);
-                const int off = (kg * 16 + rg) * 128 + (lane & 7) * 16;
-                *reinterpret_cast<uint4 *>(ahi + off) = make_uint4(h[0], h[1], h[2], h[3]);
-                *reinterpret_cast<uint4 *>(alo + off) = make_uint4(l[0], l[1], l[2], l[3]);
-            }
-            fence_async_smem();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(bar_ready(s));
-        }
-        // ------------------------------------------------------------ epilogue (warps 0-3)
-        if (warp < 4 && ok && !*abort_flag) {
-            const bool got = mbar_wait(bar_acc, 0, a.budget, abort_flag, a.err, kErrWaitAcc);
-            if (__all_sync(0xffffffffu, got)) {
-                tc_fence_after();
-                uint32_t v[T];
-                tmem_ld<T>(tmem_acc + ((uint32_t)(32 * warp) << 16), v);
-                tmem_wait_ld();
-                const int64_t i = row0 + 32 * warp + lane;
-                if (i < a.N) {
-                    if (a.partial) {
-                        float4 *dst = reinterpret_cast<float4 *>(a.partial + ((int64_t)blockIdx.y * a.Np + i) * T);
-#pragma unroll
-                        for (int c = 0; c < T; c += 4)
-                            dst[c / 4] = make_float4(__uint_as_float(v[c]), __uint_as_float(v[c + 1]),
-                                                     __uint_as_float(v[c + 2]), __uint_as_float(v[c + 3]));
-                    } else {
-                        const float *vi = a.V + i * a.ldv;
-                        float *oi = a.out + i * a.ldo;
-#pragma unroll
-                        for (int c = 0; c < T; ++c) oi[c] = fmaf(a.noise, vi[c], __uint_as_float(v[c]));
-                    }
-                }
-            }
-        }
-    }
-    tc_fence_before();
-    __syncthreads();
-    if (warp == 9) {
-        tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem_acc) : "memory");
-    }
-}
-
 
 // V -> (V_hi, V_lo) in the tile order the MMA reads: element (j, c) of chunk q = j / 64 sits at
 // q*64*T + ((j%64)/8 * T/8 + c/8) * 64 + (c%8) * 8 + j%8; rows j >= N are zero.
-template <int T>
+// FMT f16: V is first scaled per column by 2^e_c and col_scale[c] = s^2 2^-15 2^-e_c is written.
+template <int T, int FMT>
 __global__ void split_v_kernel(const float *__restrict__ V, int64_t ldv, int64_t N, int64_t Np,
-                               __nv_bfloat16 *__restrict__ vh, __nv_bfloat16 *__restrict__ vl, const int *skip) {
+                               uint16_t *__restrict__ vh, uint16_t *__restrict__ vl,
+                               const unsigned int *__restrict__ vmax, float *__restrict__ col_scale, float s2,
+                               const int *skip) {
     if (skip && *skip) return;
     const int64_t total = Np * T;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t j = e / T;
         const int c = (int)(e - j * T);
-        const float v = j < N ? V[j * ldv + c] : 0.0f;
-        const __nv_bfloat16 h = __float2bfloat16_rn(v);
-        const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
+        float v = j < N ? V[j * ldv + c] : 0.0f;
+        uint16_t h, l;
+        if (FMT == kFmtBF16) {
+            const __nv_bfloat16 hb = __float2bfloat16_rn(v);
+            const __nv_bfloat16 lb = __float2bfloat16_rn(v - __bfloat162float(hb));
+            h = *reinterpret_cast<const uint16_t *>(&hb);
+            l = *reinterpret_cast<const uint16_t *>(&lb);
+        } else {
+            const int ec = col_exponent(vmax[c]);
+            v = ldexpf(v, ec);
+            const __half hh = __float2half_rn(v);
+            const __half lh = __float2half_rn(v - __half2float(hh));
+            h = *reinterpret_cast<const uint16_t *>(&hh);
+            l = *reinterpret_cast<const uint16_t *>(&lh);
+            if (j == 0) col_scale[c] = ldexpf(s2, -15 - ec);
+        }
         const int64_t q = j / kBK;
         const int jj = (int)(j - q * kBK);
         const int64_t off = q * kBK * T + (int64_t)((jj >> 3) * (T / 8) + (c >> 3)) * 64 + (c & 7) * 8 + (jj & 7);
@@ -480,38 +117,6 @@ bool make_map(CUtensorMap *m, CUtensorMapDataType dt, int elem_bytes, const void
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int KIND, int D, int T>
-cudaError_t launch_tc_inst(dim3 grid, const CUtensorMap &mx, const CUtensorMap &mh, const CUtensorMap &ml,
-                           const TcArgs &a, cudaStream_t st) {
-    constexpr int DP = D <= 4 ? 4 : 8;
-    constexpr int bytes = TcLayout<T, DP>::kBytes;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(mv_tc_kernel<KIND, D, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             bytes);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
-    mv_tc_kernel<KIND, D, T><<<grid, kThreads, bytes, st>>>(mx, mh, ml, a);
-    return cudaGetLastError();
-}
-
-template <int KIND, int T>
-cudaError_t dispatch_d(int D, dim3 grid, const CUtensorMap &mx, const CUtensorMap &mh, const CUtensorMap &ml,
-                       const TcArgs &a, cudaStream_t st) {
-    switch (D) {
-        case 1: return launch_tc_inst<KIND, 1, T>(grid, mx, mh, ml, a, st);
-        case 2: return launch_tc_inst<KIND, 2, T>(grid, mx, mh, ml, a, st);
-        case 3: return launch_tc_inst<KIND, 3, T>(grid, mx, mh, ml, a, st);
-        case 4: return launch_tc_inst<KIND, 4, T>(grid, mx, mh, ml, a, st);
-        case 5: return launch_tc_inst<KIND, 5, T>(grid, mx, mh, ml, a, st);
-        case 6: return launch_tc_inst<KIND, 6, T>(grid, mx, mh, ml, a, st);
-        case 7: return launch_tc_inst<KIND, 7, T>(grid, mx, mh, ml, a, st);
-        case 8: return launch_tc_inst<KIND, 8, T>(grid, mx, mh, ml, a, st);
-    }
-    return cudaErrorInvalidValue;
-}
-
 struct TcGrid {
     int rb, S, cps, total;
 };
@@ -545,36 +150,56 @@ TcGrid tc_grid(int64_t Np, int num_sms) {
 
 bool tc_supported(int t) { return (t == 16 || t == 32) && encode_fn() != nullptr; }
 
-int64_t tc_vsplit_bytes(int64_t Np, int t) { return 2 * Np * t * (int64_t)sizeof(__nv_bfloat16); }
+// V_hi, V_lo [Np, t] 16-bit each, then per-column max bits [64] and epilogue scales [64].
+int64_t tc_vsplit_bytes(int64_t Np, int t) { return 2 * Np * t * 2 + 2 * 64 * 4; }
 
 int64_t mv_tc_partial_floats(int64_t Np, int t, int num_sms) {
     const TcGrid g = tc_grid(Np, num_sms);
     return g.S > 1 ? (int64_t)g.S * Np * t : 0;
 }
 
+int mv_tc_launches(int64_t Np, int t, int num_sms, int fmt) {
+    return (mv_tc_partial_floats(Np, t, num_sms) > 0 ? 3 : 2) + (fmt == kFmtF16 ? 1 : 0);
+}
+
 cudaError_t launch_mv_tc(const KernelParams &kp, const float *Xs, int64_t N, int64_t Np, const float *V, int64_t ldv,
-                         float *out, int64_t ldo, int t, void *vsplit, float *partial, int64_t partial_cap,
+                         float *out, int64_t ldo, int t, int fmt, void *vsplit, float *partial, int64_t partial_cap,
                          const int *skip, int *err_flag, long long wait_budget, int num_sms, cudaStream_t st) {
     if (!(t == 16 || t == 32) || Np % 256 != 0) return cudaErrorInvalidValue;
-    __nv_bfloat16 *vh = (__nv_bfloat16 *)vsplit;
-    __nv_bfloat16 *vl = vh + Np * t;
+    uint16_t *vh = (uint16_t *)vsplit;
+    uint16_t *vl = vh + Np * t;
+    unsigned int *vmax = (unsigned int *)(vl + Np * t);
+    float *col_scale = (float *)(vmax + 64);
     const int blocks = (int)std::min<int64_t>((Np * t + 255) / 256, 8192);
-    if (t == 16)
-        split_v_kernel<16><<<blocks, 256, 0, st>>>(V, ldv, N, Np, vh, vl, skip);
-    else
-        split_v_kernel<32><<<blocks, 256, 0, st>>>(V, ldv, N, Np, vh, vl, skip);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e;
+    if (fmt == kFmtF16) {
+        e = cudaMemsetAsync(vmax, 0, 64 * sizeof(unsigned int), st);
+        if (e != cudaSuccess) return e;
+        const int mb = (int)std::min<int64_t>((N * t + 255) / 256, 1024);
+        col_absmax_kernel<<<mb, (256 / t) * t, 0, st>>>(V, ldv, N, t, vmax, skip);
+        if (t == 16)
+            split_v_kernel<16, kFmtF16><<<blocks, 256, 0, st>>>(V, ldv, N, Np, vh, vl, vmax, col_scale, kp.s2, skip);
+        else
+            split_v_kernel<32, kFmtF16><<<blocks, 256, 0, st>>>(V, ldv, N, Np, vh, vl, vmax, col_scale, kp.s2, skip);
+    } else {
+        if (t == 16)
+            split_v_kernel<16, kFmtBF16><<<blocks, 256, 0, st>>>(V, ldv, N, Np, vh, vl, vmax, col_scale, kp.s2, skip);
+        else
+            split_v_kernel<32, kFmtBF16><<<blocks, 256, 0, st>>>(V, ldv, N, Np, vh, vl, vmax, col_scale, kp.s2, skip);
+    }
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
 
     const TcGrid g = tc_grid(Np, num_sms);
     if (g.S > 1 && (partial == nullptr || (int64_t)g.S * Np * t > partial_cap)) return cudaErrorInvalidValue;
+    const CUtensorMapDataType vt = fmt == kFmtF16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     CUtensorMap mx, mh, ml;
     if (!make_map(&mx, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, Xs, (uint64_t)kp.dpad, (uint64_t)Np, (uint32_t)kp.dpad,
                   (uint32_t)kBK) ||
-        !make_map(&mh, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, vh, 64, (uint64_t)(Np * t / 64), 64, (uint32_t)t) ||
-        !make_map(&ml, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, vl, 64, (uint64_t)(Np * t / 64), 64, (uint32_t)t))
+        !make_map(&mh, vt, 2, vh, 64, (uint64_t)(Np * t / 64), 64, (uint32_t)t) ||
+        !make_map(&ml, vt, 2, vl, 64, (uint64_t)(Np * t / 64), 64, (uint32_t)t))
         return cudaErrorInvalidValue;
-    TcArgs a;
+    tc::TcArgs a;
     a.Xs = Xs;
     a.V = V;
     a.out = g.S > 1 ? nullptr : out;
@@ -587,16 +212,13 @@ cudaError_t launch_mv_tc(const KernelParams &kp, const float *Xs, int64_t N, int
     a.ldo = ldo;
     a.chunks_per_split = g.cps;
     a.total_chunks = g.total;
-    a.log2s2 = kp.log2_s2;
+    a.log2s2 = fmt == kFmtF16 ? 15.0f : kp.log2_s2;
     a.noise = kp.noise;
+    a.col_scale = fmt == kFmtF16 ? col_scale : nullptr;
     a.budget = wait_budget;
     const dim3 grid((unsigned)g.rb, (unsigned)g.S, 1);
-    if (kp.kind == LGP_RBF)
-        e = t == 16 ? dispatch_d<LGP_RBF, 16>(kp.D, grid, mx, mh, ml, a, st)
-                    : dispatch_d<LGP_RBF, 32>(kp.D, grid, mx, mh, ml, a, st);
-    else
-        e = t == 16 ? dispatch_d<LGP_MATERN52, 16>(kp.D, grid, mx, mh, ml, a, st)
-                    : dispatch_d<LGP_MATERN52, 32>(kp.D, grid, mx, mh, ml, a, st);
+    e = fmt == kFmtF16 ? tc::dispatch_f16(kp.kind, kp.D, t, grid, mx, mh, ml, a, st)
+                       : tc::dispatch_bf16(kp.kind, kp.D, t, grid, mx, mh, ml, a, st);
     if (e != cudaSuccess || g.S == 1) return e;
     const int rblocks = (int)std::min<int64_t>((N * t + 255) / 256, 4096);
     tc_reduce_kernel<<<rblocks, 256, 0, st>>>(partial, g.S, Np, N, t, V, ldv, out, ldo, kp.noise, skip);

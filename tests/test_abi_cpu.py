@@ -73,7 +73,7 @@ def test_struct_layouts_are_packed_as_in_c():
     import paper_2605_17898_gb300 as pkg
     assert ctypes.sizeof(pkg.lgp_hyper) == 24
     assert ctypes.sizeof(pkg.lgp_options) == 32
-    assert ctypes.sizeof(pkg.lgp_lml_info) == 48
+    assert ctypes.sizeof(pkg.lgp_lml_info) == 56
 
 
 def test_workloads_shapes_and_dtypes():
