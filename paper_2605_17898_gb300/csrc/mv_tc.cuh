@@ -13,15 +13,22 @@
 //             s^2 2^-15 2^-e_c. Entries below 2^-18 s^2 lose relative precision in their
 //             lo half but keep an absolute error below 2^-40 s^2.
 //
-// CTA structure (one CTA per SM: 10 warps, ~170 KB shared memory):
-//   warps 0-7  generate the 128 x 64 entry tile of each column chunk in registers and
-//              write its hi/lo halves to shared memory in the K-major no-swizzle layout the
-//              MMA reads; warps 0-3 also run the epilogue (TMEM -> registers -> HBM);
-//   warp 8     producer: TMA (cp.async.bulk.tensor) of the prescaled x_j tile and of the
-//              pre-split V_hi / V_lo tiles into a 4-stage ring;
-//   warp 9     allocates the tensor-memory accumulator (128 lanes x t float32 columns) and
-//              one elected thread issues the tcgen05.mma instructions (M=128, N=t, K=16,
-//              three per K step) and commits them to the ring's "empty" barriers.
+// CTA structure (one CTA per SM: 14 warps, ~200 KB shared memory):
+//   warps 0-7   generate the 128 x 64 entry tile of each column chunk in registers and
+//               write its hi/lo halves to shared memory in the K-major no-swizzle layout the
+//               MMA reads;
+//   warp 8      producer: TMA (cp.async.bulk.tensor) of the prescaled x_j tile and of the
+//               pre-split V_hi / V_lo tiles into a 4-stage ring;
+//   warp 9      allocates two tensor-memory accumulators (128 lanes x 32 float32 columns
+//               each) and one elected thread issues the tcgen05.mma instructions (M=128,
+//               N=t, K=16, three per K step) and commits them to the ring's "empty" barriers;
+//   warps 10-13 drain: every kGroup chunks the MMA switches accumulator and these warps move
+//               the finished one into float32 registers (round-to-nearest adds), so no
+//               tensor-core accumulation chain is longer than kGroup * 12 MMAs; they also run
+//               the epilogue (registers -> HBM).
+// Accumulation chains are kept short because the tensor pipe's float32 accumulation rounds
+// less carefully than an IEEE add: measured, its error grew linearly with the chain length
+// (1.8e-5 at N=4099, 6.6e-4 at N=500000 for one chain per CTA), and ~1e-6 with drains.
 // A CTA owns 128 output rows and a range of 64-column chunks; when the grid splits the
 // column range, each CTA writes float32 partial sums that a second kernel reduces in a
 // fixed order.
@@ -52,7 +59,9 @@ constexpr int kStages = 4;
 constexpr int kBM = 128;          // rows per CTA (MMA M)
 constexpr int kBK = 64;           // columns j per chunk (4 MMA K steps)
 constexpr int kGenWarps = 8;
-constexpr int kThreads = 320;     // 8 generation warps + producer warp + MMA warp
+constexpr int kThreads = 448;     // 8 generation warps + producer + MMA + 4 drain warps
+constexpr int kGroup = 2;         // chunks accumulated in tensor memory between drains
+constexpr int kAccCols = 32;      // tensor-memory columns per accumulator buffer
 constexpr long long kDrainBudget = 2000000000LL;
 
 // error codes written to the device error word on a timeout
@@ -65,9 +74,9 @@ struct TcLayout {
     static constexpr int kX = kBK * DP * 4;     // prescaled x_j tile
     static constexpr int kStage = 2 * kA + 2 * kB + kX;
     static constexpr int kBar = kStages * kStage;      // barriers after the ring
-    // + barriers/flags, alignment slack, and a 32 KB guard band after the ring so that no
+    // + barriers/flags, alignment slack, and a guard band after the ring so that no
     // descriptor-addressed read of the last stage can leave the CTA's allocation
-    static constexpr int kBytes = kBar + 256 + 1024 + 32768;
+    static constexpr int kBytes = kBar + 256 + 1024 + 16384;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -236,9 +245,9 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L::kBar);
-    // bars: full[4], ready[4], empty[4], acc
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + L::kBar + 128);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + L::kBar + 136);
+    // bars: full[4], ready[4], empty[4], acc_full[2], acc_empty[2], fin
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + L::kBar + 192);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + L::kBar + 200);
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -250,7 +259,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     auto bar_full = [&](int s) { return smem_u32(&bars[s]); };
     auto bar_ready = [&](int s) { return smem_u32(&bars[kStages + s]); };
     auto bar_empty = [&](int s) { return smem_u32(&bars[2 * kStages + s]); };
-    const uint32_t bar_acc = smem_u32(&bars[3 * kStages]);
+    auto bar_acc_full = [&](int b) { return smem_u32(&bars[3 * kStages + b]); };
+    auto bar_acc_empty = [&](int b) { return smem_u32(&bars[3 * kStages + 2 + b]); };
+    const uint32_t bar_fin = smem_u32(&bars[3 * kStages + 4]);
+    const int n_groups = (n_it + kGroup - 1) / kGroup;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -258,13 +270,17 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_init(bar_ready(s), kGenWarps);
             mbar_init(bar_empty(s), 1);
         }
-        mbar_init(bar_acc, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(bar_acc_full(b), 1);
+            mbar_init(bar_acc_empty(b), 4);
+        }
+        mbar_init(bar_fin, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_async_smem();
     }
     if (warp == 9) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_u32(tmem_slot))
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(smem_u32(tmem_slot))
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -307,8 +323,17 @@ __global__ void __launch_bounds__(kThreads, 1)
             bool issued = false;
             for (int it = 0; it < n_it; ++it) {
                 const int s = it % kStages;
+                const int g = it / kGroup;
+                const int buf = g & 1;
+                const bool group_start = (it % kGroup) == 0;
+                const bool group_end = (it % kGroup) == kGroup - 1 || it == n_it - 1;
+                // the drain warps must have read this buffer's previous group (g - 2)
+                if (group_start && g >= 2 &&
+                    !mbar_wait(bar_acc_empty(buf), ((g >> 1) - 1) & 1, a.budget, abort_flag, a.err, kErrWaitAcc))
+                    break;
                 if (!mbar_wait(bar_ready(s), (it / kStages) & 1, a.budget, abort_flag, a.err, kErrWaitReady)) break;
                 tc_fence_after();
+                const uint32_t acc = tmem_acc + (uint32_t)(buf * kAccCols);
                 const uint32_t st = smem_u32(smem + s * L::kStage);
                 const uint32_t a_hi = st, a_lo = st + L::kA, b_hi = st + 2 * L::kA, b_lo = b_hi + L::kB;
 #pragma unroll
@@ -319,20 +344,22 @@ __global__ void __launch_bounds__(kThreads, 1)
                     // B: core matrix (column group cg, k group kg) at (kg * T/8 + cg) * 128 bytes
                     const uint64_t dbh = smem_desc(b_hi + ks * 2 * T * 16, T * 16, 128);
                     const uint64_t dbl = smem_desc(b_lo + ks * 2 * T * 16, T * 16, 128);
-                    mma_bf16(tmem_acc, dah, dbh, idesc, (it > 0 || ks > 0) ? 1u : 0u);
-                    mma_bf16(tmem_acc, dah, dbl, idesc, 1u);
-                    mma_bf16(tmem_acc, dal, dbh, idesc, 1u);
+                    mma_bf16(acc, dah, dbh, idesc, (group_start && ks == 0) ? 0u : 1u);
+                    mma_bf16(acc, dah, dbl, idesc, 1u);
+                    mma_bf16(acc, dal, dbh, idesc, 1u);
                 }
                 mma_commit(bar_empty(s));
+                if (group_end) mma_commit(bar_acc_full(buf));
                 issued = true;
             }
-            if (issued) mma_commit(bar_acc);
-            if (*abort_flag && issued) {
+            if (issued) {
+                // every MMA this thread issued has completed before the CTA frees tensor memory
+                mma_commit(bar_fin);
                 volatile int no_abort = 0;
-                mbar_wait(bar_acc, 0, kDrainBudget, &no_abort, a.err, 0);
+                mbar_wait(bar_fin, 0, kDrainBudget, &no_abort, a.err, 0);
             }
         }
-    } else {
+    } else if (warp < 8) {
         // ------------------------------------------------------------ generation (warps 0-7)
         const int kg = warp;  // this warp's 8-column group of every chunk
         // this thread's 4 rows of the prescaled x (row0 + 127 < Np because Np % 256 == 0)
@@ -403,32 +430,47 @@ __global__ void __launch_bounds__(kThreads, 1)
             __syncwarp();
             if (lane == 0) mbar_arrive(bar_ready(s));
         }
-        // ------------------------------------------------------------ epilogue (warps 0-3)
-        if (warp < 4 && ok && !*abort_flag) {
-            const bool got = mbar_wait(bar_acc, 0, a.budget, abort_flag, a.err, kErrWaitAcc);
-            if (__all_sync(0xffffffffu, got)) {
-                tc_fence_after();
-                uint32_t v[T];
-                tmem_ld<T>(tmem_acc + ((uint32_t)(32 * warp) << 16), v);
-                tmem_wait_ld();
-                const int64_t i = row0 + 32 * warp + lane;
-                if (a.col_scale) {
+        (void)ok;
+    } else if (warp >= 10) {
+        // ------------------------------------------------------------ drain + epilogue (warps 10-13)
+        const int quarter = warp & 3;  // tensor-memory lanes 32*quarter .. +31
+        float sum[T];
 #pragma unroll
-                    for (int c = 0; c < T; ++c) v[c] = __float_as_uint(__uint_as_float(v[c]) * a.col_scale[c]);
-                }
-                if (i < a.N) {
-                    if (a.partial) {
-                        float4 *dst = reinterpret_cast<float4 *>(a.partial + ((int64_t)blockIdx.y * a.Np + i) * T);
+        for (int c = 0; c < T; ++c) sum[c] = 0.0f;
+        bool ok = true;
+        for (int g = 0; g < n_groups; ++g) {
+            const int buf = g & 1;
+            const bool got = mbar_wait(bar_acc_full(buf), (g >> 1) & 1, a.budget, abort_flag, a.err, kErrWaitAcc);
+            if (!__all_sync(0xffffffffu, got)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            uint32_t v[T];
+            tmem_ld<T>(tmem_acc + (uint32_t)(buf * kAccCols) + ((uint32_t)(32 * quarter) << 16), v);
+            tmem_wait_ld();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar_acc_empty(buf));
 #pragma unroll
-                        for (int c = 0; c < T; c += 4)
-                            dst[c / 4] = make_float4(__uint_as_float(v[c]), __uint_as_float(v[c + 1]),
-                                                     __uint_as_float(v[c + 2]), __uint_as_float(v[c + 3]));
-                    } else {
-                        const float *vi = a.V + i * a.ldv;
-                        float *oi = a.out + i * a.ldo;
+            for (int c = 0; c < T; ++c) sum[c] += __uint_as_float(v[c]);
+        }
+        if (ok && !*abort_flag) {
+            const int64_t i = row0 + 32 * quarter + lane;
+            if (a.col_scale) {
 #pragma unroll
-                        for (int c = 0; c < T; ++c) oi[c] = fmaf(a.noise, vi[c], __uint_as_float(v[c]));
-                    }
+                for (int c = 0; c < T; ++c) sum[c] *= a.col_scale[c];
+            }
+            if (i < a.N) {
+                if (a.partial) {
+                    float4 *dst = reinterpret_cast<float4 *>(a.partial + ((int64_t)blockIdx.y * a.Np + i) * T);
+#pragma unroll
+                    for (int c = 0; c < T; c += 4) dst[c / 4] = make_float4(sum[c], sum[c + 1], sum[c + 2], sum[c + 3]);
+                } else {
+                    const float *vi = a.V + i * a.ldv;
+                    float *oi = a.out + i * a.ldo;
+#pragma unroll
+                    for (int c = 0; c < T; ++c) oi[c] = fmaf(a.noise, vi[c], sum[c]);
                 }
             }
         }
@@ -437,7 +479,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     if (warp == 9) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem_acc) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem_acc) : "memory");
     }
 }
 

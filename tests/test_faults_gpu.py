@@ -21,7 +21,7 @@ def test_wait_budget_exhaustion_is_reported_and_context_survives(lgp):
     lgp.lgp_kernel_matvec(X, p, V, prec=lgp.LGP_PREC_SPLIT_BF16, ctx=ctx)
     assert ctx.check_device_status() == lgp.LGP_ERR_TIMEOUT
     ctx.set_wait_budget(0)  # default budget
-    out = lgp.lgp_kernel_matvec(X, p, V, prec=lgp.LGP_PREC_SPLIT_BF16, ctx=ctx)
+    out = lgp.lgp_kernel_matvec(X, p, V, prec=lgp.LGP_PREC_SPLIT_F16, ctx=ctx)
     assert ctx.check_device_status() == lgp.LGP_OK
     ref = lgp.lgp_kernel_matvec(X, p, V, prec=lgp.LGP_PREC_FP32, ctx=ctx)
     torch.cuda.synchronize()
