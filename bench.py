@@ -297,7 +297,7 @@ def main():
         kev.append((a, b))
     torch.cuda.synchronize()
     mv_ms = statistics.mean(a.elapsed_time(b) for a, b in kev)
-    split = kprec == lgp.LGP_PREC_SPLIT_BF16
+    split = kprec in (lgp.LGP_PREC_SPLIT_BF16, lgp.LGP_PREC_SPLIT_F16)
     ops_pair, mufu_pair = per_pair_ops(p.kind, p.D, split, args.t)
     pairs = float(p.N) ** 2
     achieved_tops = pairs * ops_pair / (mv_ms / 1e3) / 1e12
@@ -350,10 +350,12 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32+bf16x3" if split else "f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": ("f32+f16x3" if kprec == lgp.LGP_PREC_SPLIT_F16 else "f32+bf16x3") if split else "f32",
+            "data": "synthetic",
             "config": {"workload": p.name, "N": p.N, "D": p.D, "t": args.t, "kernel": "matern52",
                        "lanczos_steps": args.lanczos, "tol": args.tol, "max_iter": args.max_iter,
-                       "cg_iterations": iters, "precision": "split_bf16" if split else "fp32",
+                       "cg_iterations": iters,
+                       "precision": {1: "fp32", 2: "split_bf16", 3: "split_f16"}.get(kprec, str(kprec)),
                        "l2": "flushed between steps (256 MB write outside the step events)",
                        "parallelism": f"replicas{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
