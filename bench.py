@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--plain", action="store_true", help="also time the plain FP32 single-RHS path")
+    ap.add_argument("--mode", choices=["lml", "matvec"], default="lml",
+                    help="lml: the LML+grad step (default); matvec: only the product, for kernel profiling")
     return ap.parse_args()
 
 
@@ -236,6 +238,9 @@ def main():
 
     p = wl.cfg3(N=args.N, t=args.t)
     m = args.t - 1
+    if args.mode == "matvec":
+        bench_matvec_only(lgp, ctx, p, args, dev, prec, rank)
+        return
     X = torch.as_tensor(p.X, device=dev)
     y = torch.as_tensor(p.y, device=dev)
     flush_buf = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
@@ -367,6 +372,32 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def bench_matvec_only(lgp, ctx, p, args, dev, prec, rank):
+    """Only the product K_y V on the workload (a small, fast command for kernel profiling)."""
+    import torch
+    import workloads as wl
+    X = torch.as_tensor(p.X, device=dev)
+    V = torch.as_tensor(wl.rhs_block(p.N, args.t, seed=3, kind="sign"), device=dev)
+    out = torch.empty_like(V)
+    kprec = ctx.matvec_precision(args.t, prec)
+    for _ in range(args.warmup):
+        lgp.lgp_kernel_matvec(X, p, V, prec=kprec, out=out, ctx=ctx)
+    torch.cuda.synchronize()
+    evs = []
+    for _ in range(args.steps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        lgp.lgp_kernel_matvec(X, p, V, prec=kprec, out=out, ctx=ctx)
+        b.record()
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
+    if rank == 0:
+        print(json.dumps({"mode": "matvec", "workload": p.name, "precision": kprec, "ms": ms,
+                          "pair_rhs_per_s": float(p.N) ** 2 * args.t / (ms / 1e3)}), flush=True)
 
 
 def bench_plain(lgp, ctx, p, X, y, args, dev):
