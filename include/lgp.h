@@ -223,6 +223,33 @@ lgp_status lgp_batch_cg_solve(lgp_ctx *ctx, int32_t n_gp, const lgp_hyper *hyp, 
                               const float *const *B, float *const *Xsol, const int64_t *N, int32_t t,
                               const lgp_options *opt, int32_t *iters, double *rel_resid, lgp_stream stream);
 
+/*
+ * Allocation-free K_y V for callers that cannot allocate device memory: code
+ * running while a stream is captured into a CUDA graph (allocation calls are not
+ * allowed there), programs whose device memory belongs to another allocator, and
+ * latency-critical loops where cudaMalloc/cudaFree could synchronise the device.
+ * The paper has no counterpart of this entry point; it is a deployment variant of
+ * lgp_kernel_matvec's tensor-core path.
+ *
+ * Same arguments and result as lgp_kernel_matvec with prec in {AUTO, SPLIT_F16,
+ * SPLIT_BF16} (AUTO = SPLIT_F16), but no context: it works on the current CUDA
+ * device and calls no cudaMalloc, cudaFree or other allocating routine. Its
+ * scratch is one fixed device array of about 17.3 MiB inside the library, held by
+ * every GPU that loads the library until the process exits.
+ *   - Limits: 1 <= N <= 8192, t in {16, 32}, 1 <= D <= 8; larger sizes return
+ *     LGP_ERR_UNSUPPORTED before anything is launched.
+ *   - Set-up: the first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - Every call shares the one array: calls whose work overlaps on the GPU (on
+ *     different streams, or from several threads) race and corrupt each other.
+ *     Order them on one stream.
+ *   - Asynchronous on `stream`; no error word is read back (a NaN/Inf in X or V
+ *     propagates to out). Returns LGP_ERR_INVALID_ARG for bad pointers or values,
+ *     LGP_ERR_CUDA if a launch fails.
+ */
+lgp_status lgp_kernel_matvec_noalloc(const lgp_hyper *hyp, const float *X, const float *V, float *out,
+                                     int64_t N, int32_t t, int32_t prec, lgp_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -43,7 +43,7 @@ EXPORTED = [
     "lgp_version", "lgp_status_string", "lgp_create", "lgp_destroy", "lgp_last_error_message",
     "lgp_workspace_bytes", "lgp_matvec_precision", "lgp_set_wait_budget", "lgp_check_device_status",
     "lgp_kernel_matvec", "lgp_kernel_matvec_grad", "lgp_cg_solve", "lgp_lml_and_grad",
-    "lgp_rademacher_probes", "lgp_batch_cg_solve",
+    "lgp_rademacher_probes", "lgp_batch_cg_solve", "lgp_kernel_matvec_noalloc",
 ]
 
 
@@ -103,6 +103,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "lgp_rademacher_probes": (c.c_int32, [vp, c.c_uint64, c.c_int64, c.c_int32, vp, c.c_int64, vp]),
         "lgp_batch_cg_solve": (c.c_int32, [vp, c.c_int32, c.POINTER(lgp_hyper), vp, vp, vp, vp, c.c_int32,
                                            c.POINTER(lgp_options), vp, vp, vp]),
+        "lgp_kernel_matvec_noalloc": (c.c_int32, [c.POINTER(lgp_hyper), vp, vp, vp, c.c_int64, c.c_int32, c.c_int32,
+                                                  vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -229,6 +231,21 @@ def lgp_kernel_matvec(X, hyp, V, prec: int = LGP_PREC_AUTO, out=None, ctx: Conte
         ctx._check(s)
     del keep
     return out.reshape(-1) if squeeze else out
+
+
+def lgp_kernel_matvec_noalloc(X, hyp, V, out, prec: int = LGP_PREC_AUTO, stream=None) -> int:
+    """K_y V into a caller-provided `out` with no device allocation (N <= 8192, t in {16, 32}).
+
+    For callers that cannot allocate device memory (stream capture, foreign allocators,
+    latency-critical loops). Returns the lgp_status; the scratch is a fixed array inside
+    the library, so overlapping calls on different streams race.
+    """
+    N, t = V.shape
+    h, keep = Hyper.of(hyp).to_c()
+    s = load().lgp_kernel_matvec_noalloc(ctypes.byref(h), _ptr(X), _ptr(V), _ptr(out), int(N), int(t), int(prec),
+                                         _stream_ptr(stream))
+    del keep
+    return int(s)
 
 
 def lgp_kernel_matvec_grad(X, hyp, W, ctx: Context | None = None, stream=None):
