@@ -13,16 +13,16 @@
 //             s^2 2^-15 2^-e_c. Entries below 2^-18 s^2 lose relative precision in their
 //             lo half but keep an absolute error below 2^-40 s^2.
 //
-// CTA structure (one CTA per SM: 14 warps, ~200 KB shared memory):
-//   warps 0-7   generate the 128 x 64 entry tile of each column chunk in registers and
-//               write its hi/lo halves to shared memory in the K-major no-swizzle layout the
-//               MMA reads;
-//   warp 8      producer: TMA (cp.async.bulk.tensor) of the prescaled x_j tile and of the
+// CTA structure (one CTA per SM: 22 warps, ~190 KB shared memory):
+//   warps 0-15  generate the 128 x 64 entry tile of each column chunk in registers (each
+//               thread: 2 rows x 8 columns) and write its hi/lo halves to shared memory in the
+//               K-major no-swizzle layout the MMA reads;
+//   warp 16     producer: TMA (cp.async.bulk.tensor) of the prescaled x_j tile and of the
 //               pre-split V_hi / V_lo tiles into a 4-stage ring;
-//   warp 9      allocates two tensor-memory accumulators (128 lanes x 32 float32 columns
+//   warp 17     allocates two tensor-memory accumulators (128 lanes x 32 float32 columns
 //               each) and one elected thread issues the tcgen05.mma instructions (M=128,
 //               N=t, K=16, three per K step) and commits them to the ring's "empty" barriers;
-//   warps 10-13 drain: every kGroup chunks the MMA switches accumulator and these warps move
+//   warps 18-21 drain: every kGroup chunks the MMA switches accumulator and these warps move
 //               the finished one into float32 registers (round-to-nearest adds), so no
 //               tensor-core accumulation chain is longer than kGroup * 12 MMAs; they also run
 //               the epilogue (registers -> HBM).
@@ -33,7 +33,8 @@
 // column range, each CTA writes float32 partial sums that a second kernel reduces in a
 // fixed order.
 //
-// Every wait on an mbarrier is bounded by a cycle budget: a wait that runs out records
+// The service warps (producer, MMA, drain) back off with nanosleep while they poll, so the
+// generation warps keep the issue slots. Every wait on an mbarrier is bounded by a cycle budget: a wait that runs out records
 // an error code in a device word, raises a CTA-wide abort flag, and all roles leave their
 // loops; the producer then waits (bounded) for its own copies in flight, the MMA thread
 // for its own MMAs, and the TMEM accumulator is freed before the CTA exits.
@@ -58,8 +59,11 @@ namespace tc {
 constexpr int kStages = 4;
 constexpr int kBM = 128;          // rows per CTA (MMA M)
 constexpr int kBK = 64;           // columns j per chunk (4 MMA K steps)
-constexpr int kGenWarps = 8;
-constexpr int kThreads = 448;     // 8 generation warps + producer + MMA + 4 drain warps
+constexpr int kGenWarps = 16;
+constexpr int kProducerWarp = 16;
+constexpr int kMmaWarp = 17;
+constexpr int kDrainWarp0 = 18;
+constexpr int kThreads = 704;     // 16 generation warps + producer + MMA + 4 drain warps
 constexpr int kGroup = 2;         // chunks accumulated in tensor memory between drains
 constexpr int kAccCols = 32;      // tensor-memory columns per accumulator buffer
 constexpr long long kDrainBudget = 2000000000LL;
@@ -111,12 +115,13 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
 
 // Bounded wait for the phase with the given parity. Returns false on timeout or abort.
 static __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long budget, volatile int *abort_flag,
-                                       int *err, int code) {
+                                              int *err, int code, int sleep_ns = 0) {
     if (mbar_try(bar, parity)) return true;
     const long long t0 = clock64();
     while (true) {
         if (mbar_try(bar, parity)) return true;
         if (*abort_flag) return false;
+        if (sleep_ns) __nanosleep(sleep_ns);
         if (clock64() - t0 > budget) {
             *abort_flag = 1;
             atomicOr(err, code);
@@ -279,7 +284,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_async_smem();
     }
-    if (warp == 9) {
+    if (warp == kMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(smem_u32(tmem_slot))
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -289,7 +294,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_fence_after();
     const uint32_t tmem_acc = *tmem_slot;
 
-    if (warp == 8) {
+    if (warp == kProducerWarp) {
         // ------------------------------------------------------------ producer (TMA)
         int last_it[kStages];
         for (int s = 0; s < kStages; ++s) last_it[s] = -1;
@@ -297,7 +302,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int it = 0; it < n_it; ++it) {
                 const int s = it % kStages;
                 if (it >= kStages &&
-                    !mbar_wait(bar_empty(s), ((it / kStages) - 1) & 1, a.budget, abort_flag, a.err, kErrWaitEmpty))
+                    !mbar_wait(bar_empty(s), ((it / kStages) - 1) & 1, a.budget, abort_flag, a.err, kErrWaitEmpty, 64))
                     break;
                 uint8_t *st = smem + s * L::kStage;
                 const int q = c_begin + it;
@@ -316,7 +321,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
         }
-    } else if (warp == 9) {
+    } else if (warp == kMmaWarp) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
             const uint32_t idesc = instr_desc<T, FMT>();
@@ -329,9 +334,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const bool group_end = (it % kGroup) == kGroup - 1 || it == n_it - 1;
                 // the drain warps must have read this buffer's previous group (g - 2)
                 if (group_start && g >= 2 &&
-                    !mbar_wait(bar_acc_empty(buf), ((g >> 1) - 1) & 1, a.budget, abort_flag, a.err, kErrWaitAcc))
+                    !mbar_wait(bar_acc_empty(buf), ((g >> 1) - 1) & 1, a.budget, abort_flag, a.err, kErrWaitAcc, 32))
                     break;
-                if (!mbar_wait(bar_ready(s), (it / kStages) & 1, a.budget, abort_flag, a.err, kErrWaitReady)) break;
+                if (!mbar_wait(bar_ready(s), (it / kStages) & 1, a.budget, abort_flag, a.err, kErrWaitReady, 32)) break;
                 tc_fence_after();
                 const uint32_t acc = tmem_acc + (uint32_t)(buf * kAccCols);
                 const uint32_t st = smem_u32(smem + s * L::kStage);
@@ -359,69 +364,72 @@ __global__ void __launch_bounds__(kThreads, 1)
                 mbar_wait(bar_fin, 0, kDrainBudget, &no_abort, a.err, 0);
             }
         }
-    } else if (warp < 8) {
-        // ------------------------------------------------------------ generation (warps 0-7)
-        const int kg = warp;  // this warp's 8-column group of every chunk
-        // this thread's 4 rows of the prescaled x (row0 + 127 < Np because Np % 256 == 0)
-        float xi[4][D];
+    } else if (warp < kGenWarps) {
+        // ------------------------------------------------------------ generation (warps 0-15)
+        const int kg = warp & 7;    // this warp's 8-column group of every chunk
+        const int half = warp >> 3; // rows 64*half .. 64*half + 63
+        // this thread's 2 rows of the prescaled x (row0 + 127 < Np because Np % 256 == 0)
+        float xi[2][D];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const float *xr = a.Xs + (row0 + 32 * r + lane) * DP;
+        for (int r = 0; r < 2; ++r) {
+            const float *xr = a.Xs + (row0 + 64 * half + 32 * r + lane) * DP;
 #pragma unroll
             for (int d = 0; d < D; ++d) xi[r][d] = xr[d];
         }
-        bool ok = true;
         for (int it = 0; it < n_it; ++it) {
             const int s = it % kStages;
             const bool got = mbar_wait(bar_full(s), (it / kStages) & 1, a.budget, abort_flag, a.err, kErrWaitFull);
-            if (!__all_sync(0xffffffffu, got)) {
-                ok = false;
-                break;
-            }
+            if (!__all_sync(0xffffffffu, got)) break;
             uint8_t *st = smem + s * L::kStage;
             const float *xs = reinterpret_cast<const float *>(st + 2 * L::kA + 2 * L::kB);
-            float xj[8][D];
+            float k[2][8];
 #pragma unroll
-            for (int jj = 0; jj < 8; ++jj) {
-                const float *p = xs + (8 * kg + jj) * DP;
-                const float4 q0 = *reinterpret_cast<const float4 *>(p);
-                xj[jj][0] = q0.x;
-                if (D > 1) xj[jj][1 < D ? 1 : 0] = q0.y;
-                if (D > 2) xj[jj][2 < D ? 2 : 0] = q0.z;
-                if (D > 3) xj[jj][3 < D ? 3 : 0] = q0.w;
-                if (DP == 8) {
-                    const float4 q1 = *reinterpret_cast<const float4 *>(p + 4);
-                    if (D > 4) xj[jj][4 < D ? 4 : 0] = q1.x;
-                    if (D > 5) xj[jj][5 < D ? 5 : 0] = q1.y;
-                    if (D > 6) xj[jj][6 < D ? 6 : 0] = q1.z;
-                    if (D > 7) xj[jj][7 < D ? 7 : 0] = q1.w;
+            for (int jh = 0; jh < 2; ++jh) {
+                float xj[4][D];
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) {
+                    const float *p = xs + (8 * kg + 4 * jh + jj) * DP;
+                    const float4 q0 = *reinterpret_cast<const float4 *>(p);
+                    xj[jj][0] = q0.x;
+                    if (D > 1) xj[jj][1 < D ? 1 : 0] = q0.y;
+                    if (D > 2) xj[jj][2 < D ? 2 : 0] = q0.z;
+                    if (D > 3) xj[jj][3 < D ? 3 : 0] = q0.w;
+                    if (DP == 8) {
+                        const float4 q1 = *reinterpret_cast<const float4 *>(p + 4);
+                        if (D > 4) xj[jj][4 < D ? 4 : 0] = q1.x;
+                        if (D > 5) xj[jj][5 < D ? 5 : 0] = q1.y;
+                        if (D > 6) xj[jj][6 < D ? 6 : 0] = q1.z;
+                        if (D > 7) xj[jj][7 < D ? 7 : 0] = q1.w;
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj) {
+                        float d0 = xi[r][0] - xj[jj][0];
+                        float r2 = d0 * d0;
+#pragma unroll
+                        for (int d = 1; d < D; ++d) {
+                            const float dd = xi[r][d] - xj[jj][d];
+                            r2 = fmaf(dd, dd, r2);
+                        }
+                        k[r][4 * jh + jj] = Entry<KIND>::k(r2, a.log2s2);
+                    }
                 }
             }
             uint8_t *ahi = st;
             uint8_t *alo = st + L::kA;
 #pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                float k[8];
-#pragma unroll
-                for (int jj = 0; jj < 8; ++jj) {
-                    float d0 = xi[r][0] - xj[jj][0];
-                    float r2 = d0 * d0;
-#pragma unroll
-                    for (int d = 1; d < D; ++d) {
-                        const float dd = xi[r][d] - xj[jj][d];
-                        r2 = fmaf(dd, dd, r2);
-                    }
-                    k[jj] = Entry<KIND>::k(r2, a.log2s2);
-                }
+            for (int r = 0; r < 2; ++r) {
                 uint32_t h[4], l[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    h[u] = pack2<FMT>(k[2 * u], k[2 * u + 1]);
+                    h[u] = pack2<FMT>(k[r][2 * u], k[r][2 * u + 1]);
                     float h0, h1;
                     unpack2<FMT>(h[u], h0, h1);
-                    l[u] = pack2<FMT>(k[2 * u] - h0, k[2 * u + 1] - h1);
+                    l[u] = pack2<FMT>(k[r][2 * u] - h0, k[r][2 * u + 1] - h1);
                 }
-                const int rg = 4 * r + (lane >> 3);
+                const int rg = 8 * half + 4 * r + (lane >> 3);
                 const int off = (kg * 16 + rg) * 128 + (lane & 7) * 16;
                 *reinterpret_cast<uint4 *>(ahi + off) = make_uint4(h[0], h[1], h[2], h[3]);
                 *reinterpret_cast<uint4 *>(alo + off) = make_uint4(l[0], l[1], l[2], l[3]);
@@ -430,9 +438,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             __syncwarp();
             if (lane == 0) mbar_arrive(bar_ready(s));
         }
-        (void)ok;
-    } else if (warp >= 10) {
-        // ------------------------------------------------------------ drain + epilogue (warps 10-13)
+    } else if (warp >= kDrainWarp0) {
+        // ------------------------------------------------------------ drain + epilogue (warps 18-21)
         const int quarter = warp & 3;  // tensor-memory lanes 32*quarter .. +31
         float sum[T];
 #pragma unroll
@@ -440,7 +447,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         bool ok = true;
         for (int g = 0; g < n_groups; ++g) {
             const int buf = g & 1;
-            const bool got = mbar_wait(bar_acc_full(buf), (g >> 1) & 1, a.budget, abort_flag, a.err, kErrWaitAcc);
+            const bool got = mbar_wait(bar_acc_full(buf), (g >> 1) & 1, a.budget, abort_flag, a.err, kErrWaitAcc, 128);
             if (!__all_sync(0xffffffffu, got)) {
                 ok = false;
                 break;
@@ -477,7 +484,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 9) {
+    if (warp == kMmaWarp) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem_acc) : "memory");
     }
