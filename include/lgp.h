@@ -224,6 +224,14 @@ lgp_status lgp_batch_cg_solve(lgp_ctx *ctx, int32_t n_gp, const lgp_hyper *hyp, 
                               const lgp_options *opt, int32_t *iters, double *rel_resid, lgp_stream stream);
 
 /*
+ * Measurement support (no counterpart in the paper): throughput of one GPU pipe on the
+ * current device, timed with CUDA events on `stream` at the clock the GPU runs.
+ * which: 0 float32 FMA results/s, 1 packed float32x2 FMA results/s (two per lane),
+ * 2 MUFU ex2.approx results/s, 3 MUFU sqrt.approx results/s. Synchronises `stream`.
+ */
+lgp_status lgp_measure_pipe_peak(int32_t which, double *ops_per_s, lgp_stream stream);
+
+/*
  * Allocation-free K_y V for callers that cannot allocate device memory: code
  * running while a stream is captured into a CUDA graph (allocation calls are not
  * allowed there), programs whose device memory belongs to another allocator, and

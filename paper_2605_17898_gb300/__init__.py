@@ -44,6 +44,7 @@ EXPORTED = [
     "lgp_workspace_bytes", "lgp_matvec_precision", "lgp_set_wait_budget", "lgp_check_device_status",
     "lgp_kernel_matvec", "lgp_kernel_matvec_grad", "lgp_cg_solve", "lgp_lml_and_grad",
     "lgp_rademacher_probes", "lgp_batch_cg_solve", "lgp_kernel_matvec_noalloc",
+    "lgp_measure_pipe_peak",
 ]
 
 
@@ -103,6 +104,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "lgp_rademacher_probes": (c.c_int32, [vp, c.c_uint64, c.c_int64, c.c_int32, vp, c.c_int64, vp]),
         "lgp_batch_cg_solve": (c.c_int32, [vp, c.c_int32, c.POINTER(lgp_hyper), vp, vp, vp, vp, c.c_int32,
                                            c.POINTER(lgp_options), vp, vp, vp]),
+        "lgp_measure_pipe_peak": (c.c_int32, [c.c_int32, c.POINTER(c.c_double), vp]),
         "lgp_kernel_matvec_noalloc": (c.c_int32, [c.POINTER(lgp_hyper), vp, vp, vp, c.c_int64, c.c_int32, c.c_int32,
                                                   vp]),
     }
@@ -246,6 +248,18 @@ def lgp_kernel_matvec_noalloc(X, hyp, V, out, prec: int = LGP_PREC_AUTO, stream=
                                          _stream_ptr(stream))
     del keep
     return int(s)
+
+
+PIPE_FFMA, PIPE_FFMA2, PIPE_MUFU_EX2, PIPE_MUFU_SQRT = 0, 1, 2, 3
+
+
+def lgp_measure_pipe_peak(which: int, stream=None) -> float:
+    """Measured results/s of one pipe on the current device (see include/lgp.h)."""
+    v = ctypes.c_double(0.0)
+    s = load().lgp_measure_pipe_peak(int(which), ctypes.byref(v), _stream_ptr(stream))
+    if s != LGP_OK:
+        raise LGPError(s, "lgp_measure_pipe_peak failed")
+    return v.value
 
 
 def lgp_kernel_matvec_grad(X, hyp, W, ctx: Context | None = None, stream=None):

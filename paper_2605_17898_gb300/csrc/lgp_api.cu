@@ -10,6 +10,7 @@
 #include <string>
 #include <vector>
 
+#include "batch.cuh"
 #include "lgp_internal.cuh"
 
 using namespace lgp;
@@ -650,10 +651,168 @@ lgp_status lgp_lml_and_grad(lgp_ctx *ctx, const lgp_hyper *hyp, const float *X, 
 lgp_status lgp_batch_cg_solve(lgp_ctx *ctx, int32_t n_gp, const lgp_hyper *hyp, const float *const *X,
                               const float *const *B, float *const *Xsol, const int64_t *N, int32_t t,
                               const lgp_options *opt, int32_t *iters, double *rel_resid, lgp_stream stream) {
-    (void)n_gp; (void)hyp; (void)X; (void)B; (void)Xsol; (void)N; (void)t; (void)opt; (void)iters; (void)rel_resid;
-    (void)stream;
     if (!ctx) return LGP_ERR_INVALID_ARG;
-    return fail(ctx, LGP_ERR_UNSUPPORTED, "lgp_batch_cg_solve is not built yet");
+    if (n_gp < 1 || n_gp > 4096) return fail(ctx, LGP_ERR_UNSUPPORTED, "n_gp=%d outside 1..4096", n_gp);
+    if (t < 1 || t > 16) return fail(ctx, LGP_ERR_UNSUPPORTED, "batched solve supports 1 <= t <= 16 (got %d)", t);
+    if (!hyp || !X || !B || !Xsol || !N) return fail(ctx, LGP_ERR_INVALID_ARG, "NULL problem array");
+    lgp_status s;
+    if ((s = check_opts(ctx, opt, false)) != LGP_OK) return s;
+    LGP_CUDA(cudaSetDevice(ctx->device));
+    std::vector<BatchGp> gps(n_gp);
+    std::vector<KernelParams> kps(n_gp);
+    std::vector<BatchItem> items;
+    std::vector<BatchVecBlock> vblocks;
+    const int rows_per_vblock = std::max(1, 4096 / t);
+    const int bm = batch_item_rows();
+    int64_t xs_total = 0, rows_total = 0;
+    for (int g = 0; g < n_gp; ++g) {
+        if (N[g] < 1) return fail(ctx, LGP_ERR_INVALID_ARG, "N[%d]=%lld must be >= 1", g, (long long)N[g]);
+        if ((s = make_params(ctx, &hyp[g], &kps[g])) != LGP_OK) return s;
+        char nm[32];
+        snprintf(nm, sizeof nm, "X[%d]", g);
+        if ((s = check_dev_ptr(ctx, X[g], nm))) return s;
+        snprintf(nm, sizeof nm, "B[%d]", g);
+        if ((s = check_dev_ptr(ctx, B[g], nm))) return s;
+        snprintf(nm, sizeof nm, "Xsol[%d]", g);
+        if ((s = check_dev_ptr(ctx, Xsol[g], nm))) return s;
+        if ((const float *)Xsol[g] == B[g]) return fail(ctx, LGP_ERR_INVALID_ARG, "Xsol[%d] aliases B[%d]", g, g);
+        BatchGp &G = gps[g];
+        G.N = N[g];
+        G.Np = pad_rows(N[g]);
+        G.xs_off = xs_total;
+        G.vec_off = rows_total;
+        G.kind = kps[g].kind;
+        G.dpad = kps[g].dpad;
+        G.log2s2 = kps[g].log2_s2;
+        G.noise = kps[g].noise;
+        G.B = B[g];
+        G.Xsol = Xsol[g];
+        G.blk0 = (int)vblocks.size();
+        for (int64_t r0 = 0; r0 < G.N; r0 += rows_per_vblock)
+            vblocks.push_back({g, r0, std::min<int64_t>(G.N, r0 + rows_per_vblock)});
+        G.blk1 = (int)vblocks.size();
+        for (int64_t rb = 0; rb * bm < G.N; ++rb) items.push_back({g, (int)rb});
+        xs_total += G.Np * G.dpad;
+        rows_total += G.Np;
+    }
+    // longest items first: every item of problem g costs ~N_g
+    std::stable_sort(items.begin(), items.end(),
+                     [&](const BatchItem &a, const BatchItem &b) { return gps[a.gp].N > gps[b.gp].N; });
+    const int ng_t = n_gp * t;
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    size_t off = 0;
+    const size_t o_gps = off; off = al(off + gps.size() * sizeof(BatchGp));
+    const size_t o_items = off; off = al(off + items.size() * sizeof(BatchItem));
+    const size_t o_vb = off; off = al(off + vblocks.size() * sizeof(BatchVecBlock));
+    const size_t o_rr = off; off = al(off + 4 * (size_t)ng_t * sizeof(double));
+    const size_t o_act = off; off = al(off + 2 * (size_t)ng_t * sizeof(int));
+    const size_t o_gpd = off; off = al(off + (size_t)n_gp * sizeof(int));
+    const size_t o_misc = off; off = al(off + 256);
+    if ((s = ensure(ctx, ctx->batch_meta, off)) != LGP_OK) return s;
+    if ((s = ensure(ctx, ctx->xs, (size_t)xs_total * sizeof(float))) != LGP_OK) return s;
+    if ((s = ensure(ctx, ctx->cg_vec, (size_t)4 * rows_total * t * sizeof(float))) != LGP_OK) return s;
+    if ((s = ensure(ctx, ctx->cg_partial, vblocks.size() * (size_t)t * sizeof(double))) != LGP_OK) return s;
+    if ((s = ensure(ctx, ctx->flags, 64)) != LGP_OK) return s;
+    unsigned char *meta = (unsigned char *)ctx->batch_meta.p;
+    BatchArgs A;
+    A.gps = (const BatchGp *)(meta + o_gps);
+    A.items = (const BatchItem *)(meta + o_items);
+    A.vblocks = (const BatchVecBlock *)(meta + o_vb);
+    A.n_gp = n_gp;
+    A.n_items = (int)items.size();
+    A.n_vblocks = (int)vblocks.size();
+    A.t = t;
+    A.tt = 1;
+    while (A.tt < t) A.tt *= 2;
+    A.Xs = (const float *)ctx->xs.p;
+    float *v = (float *)ctx->cg_vec.p;
+    A.x = v;
+    A.r = v + rows_total * t;
+    A.p = v + 2 * rows_total * t;
+    A.kp = v + 3 * rows_total * t;
+    A.partial = (double *)ctx->cg_partial.p;
+    double *dd = (double *)(meta + o_rr);
+    A.rr = dd;
+    A.bnorm2 = dd + ng_t;
+    A.alpha = dd + 2 * ng_t;
+    A.beta = dd + 3 * ng_t;
+    int *ii = (int *)(meta + o_act);
+    A.active = ii;
+    A.iters = ii + ng_t;
+    A.gp_done = (int *)(meta + o_gpd);
+    A.done = (int *)(meta + o_misc);
+    A.item_counter = (int *)(meta + o_misc + 4);
+    A.st = (BatchState *)(meta + o_misc + 64);
+
+    cudaStream_t user = (cudaStream_t)stream;
+    if ((s = enter(ctx, user)) != LGP_OK) return s;
+    cudaStream_t st = ctx->work;
+    LGP_CUDA(cudaMemsetAsync(ctx->flags.p, 0, 4 * sizeof(int), st));
+    LGP_CUDA(cudaMemcpyAsync(meta + o_gps, gps.data(), gps.size() * sizeof(BatchGp), cudaMemcpyHostToDevice, st));
+    LGP_CUDA(cudaMemcpyAsync(meta + o_items, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice,
+                             st));
+    LGP_CUDA(cudaMemcpyAsync(meta + o_vb, vblocks.data(), vblocks.size() * sizeof(BatchVecBlock),
+                             cudaMemcpyHostToDevice, st));
+    for (int g = 0; g < n_gp; ++g)
+        launch_prep_x(X[g], gps[g].N, kps[g].D, kps[g].dpad, kps[g].scale, (float *)ctx->xs.p + gps[g].xs_off,
+                      gps[g].Np, (int *)ctx->flags.p, st);
+    LGP_CUDA(launch_batch_init(A, opt->tol, opt->max_iter, st));
+
+    // capture a chunk of iterations once, replay until every column of every problem has stopped
+    LGP_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    cudaError_t ce = cudaSuccess;
+    for (int k = 0; k < kChunk && ce == cudaSuccess; ++k) ce = launch_batch_iteration(A, ctx->num_sms, st);
+    cudaGraph_t graph = nullptr;
+    cudaError_t ce2 = cudaStreamEndCapture(st, &graph);
+    if (ce != cudaSuccess || ce2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return fail(ctx, LGP_ERR_CUDA, "batch graph capture failed: %s",
+                    cudaGetErrorString(ce != cudaSuccess ? ce : ce2));
+    }
+    cudaGraphExec_t exec = nullptr;
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) return fail(ctx, LGP_ERR_CUDA, "batch graph instantiate failed: %s", cudaGetErrorString(ce));
+    const int max_chunks = (opt->max_iter + kChunk - 1) / kChunk + 1;
+    int prev = -1;
+    for (int k = 0; k < max_chunks && ce == cudaSuccess; ++k) {
+        ce = cudaGraphLaunch(exec, st);
+        const int slot = k & 1;
+        if (ce == cudaSuccess) ce = cudaMemcpyAsync(ctx->h_done + slot, A.done, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (ce == cudaSuccess) ce = cudaEventRecord(ctx->ev_chunk[slot], st);
+        if (ce == cudaSuccess && prev >= 0) {
+            ce = cudaEventSynchronize(ctx->ev_chunk[prev]);
+            if (ce == cudaSuccess && ctx->h_done[prev]) break;
+        }
+        prev = slot;
+    }
+    cudaGraphExecDestroy(exec);
+    if (ce != cudaSuccess) return fail(ctx, LGP_ERR_CUDA, "batch replay failed: %s", cudaGetErrorString(ce));
+    LGP_CUDA(launch_batch_copy_out(A, st));
+    std::vector<int> h_it(ng_t), h_act(ng_t);
+    std::vector<double> h_rr(ng_t), h_b2(ng_t);
+    BatchState h_st;
+    LGP_CUDA(cudaMemcpyAsync(h_it.data(), A.iters, ng_t * sizeof(int), cudaMemcpyDeviceToHost, st));
+    LGP_CUDA(cudaMemcpyAsync(h_act.data(), A.active, ng_t * sizeof(int), cudaMemcpyDeviceToHost, st));
+    LGP_CUDA(cudaMemcpyAsync(h_rr.data(), A.rr, ng_t * sizeof(double), cudaMemcpyDeviceToHost, st));
+    LGP_CUDA(cudaMemcpyAsync(h_b2.data(), A.bnorm2, ng_t * sizeof(double), cudaMemcpyDeviceToHost, st));
+    LGP_CUDA(cudaMemcpyAsync(&h_st, A.st, sizeof(BatchState), cudaMemcpyDeviceToHost, st));
+    LGP_CUDA(cudaMemcpyAsync(ctx->h_flags, ctx->flags.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    if ((s = leave_sync(ctx, user)) != LGP_OK) return s;
+    if (ctx->h_flags[0]) return fail(ctx, LGP_ERR_NONFINITE, "some X[g] contains NaN or Inf");
+    bool unconverged = false;
+    for (int k = 0; k < ng_t; ++k) {
+        if (iters) iters[k] = h_it[k];
+        if (rel_resid) rel_resid[k] = h_b2[k] > 0.0 ? std::sqrt(h_rr[k] / h_b2[k]) : 0.0;
+        if (h_act[k]) unconverged = true;
+    }
+    if (h_st.status & 1) return fail(ctx, LGP_ERR_NONFINITE, "non-finite value in some B[g] or a CG scalar");
+    if (h_st.status & 2) return fail(ctx, LGP_ERR_BREAKDOWN, "CG breakdown in a batched problem");
+    if (unconverged) {
+        fail(ctx, LGP_WARN_NOT_CONVERGED, "some batched column reached max_iter before tol");
+        return LGP_WARN_NOT_CONVERGED;
+    }
+    return LGP_OK;
 }
 
 }  // extern "C"

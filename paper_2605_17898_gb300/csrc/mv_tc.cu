@@ -68,6 +68,18 @@ __global__ void split_v_kernel(const float *__restrict__ V, int64_t ldv, int64_t
     }
 }
 
+// XsT[d, j] = Xs[j, d]: the transposed prescaled X the tensor-core product stages by TMA.
+__global__ void transpose_x_kernel(const float *__restrict__ Xs, int64_t Np, int dpad, float *__restrict__ XsT,
+                                   const int *skip) {
+    if (skip && *skip) return;
+    const int64_t total = Np * dpad;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int d = (int)(e / Np);
+        const int64_t j = e - (int64_t)d * Np;
+        XsT[e] = Xs[j * dpad + d];
+    }
+}
+
 __global__ void tc_reduce_kernel(const float *__restrict__ partial, int S, int64_t Np, int64_t N, int t,
                                  const float *__restrict__ V, int64_t ldv, float *__restrict__ out, int64_t ldo,
                                  float noise, const int *skip) {
@@ -150,8 +162,9 @@ TcGrid tc_grid(int64_t Np, int num_sms) {
 
 bool tc_supported(int t) { return (t == 16 || t == 32) && encode_fn() != nullptr; }
 
-// V_hi, V_lo [Np, t] 16-bit each, then per-column max bits [64] and epilogue scales [64].
-int64_t tc_vsplit_bytes(int64_t Np, int t) { return 2 * Np * t * 2 + 2 * 64 * 4; }
+// V_hi, V_lo [Np, t] 16-bit each, per-column max bits [64] and epilogue scales [64], then the
+// transposed prescaled X [8, Np] float32.
+int64_t tc_vsplit_bytes(int64_t Np, int t) { return 2 * Np * t * 2 + 2 * 64 * 4 + 8 * Np * 4; }
 
 int64_t mv_tc_partial_floats(int64_t Np, int t, int num_sms) {
     const TcGrid g = tc_grid(Np, num_sms);
@@ -159,7 +172,7 @@ int64_t mv_tc_partial_floats(int64_t Np, int t, int num_sms) {
 }
 
 int mv_tc_launches(int64_t Np, int t, int num_sms, int fmt) {
-    return (mv_tc_partial_floats(Np, t, num_sms) > 0 ? 3 : 2) + (fmt == kFmtF16 ? 1 : 0);
+    return (mv_tc_partial_floats(Np, t, num_sms) > 0 ? 4 : 3) + (fmt == kFmtF16 ? 1 : 0);
 }
 
 cudaError_t launch_mv_tc(const KernelParams &kp, const float *Xs, int64_t N, int64_t Np, const float *V, int64_t ldv,
@@ -170,6 +183,7 @@ cudaError_t launch_mv_tc(const KernelParams &kp, const float *Xs, int64_t N, int
     uint16_t *vl = vh + Np * t;
     unsigned int *vmax = (unsigned int *)(vl + Np * t);
     float *col_scale = (float *)(vmax + 64);
+    float *XsT = col_scale + 64;
     const int blocks = (int)std::min<int64_t>((Np * t + 255) / 256, 8192);
     cudaError_t e;
     if (fmt == kFmtF16) {
@@ -187,6 +201,8 @@ cudaError_t launch_mv_tc(const KernelParams &kp, const float *Xs, int64_t N, int
         else
             split_v_kernel<32, kFmtBF16><<<blocks, 256, 0, st>>>(V, ldv, N, Np, vh, vl, vmax, col_scale, kp.s2, skip);
     }
+    transpose_x_kernel<<<(int)std::min<int64_t>((Np * kp.dpad + 255) / 256, 4096), 256, 0, st>>>(Xs, Np, kp.dpad,
+                                                                                              XsT, skip);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
 
@@ -194,8 +210,8 @@ cudaError_t launch_mv_tc(const KernelParams &kp, const float *Xs, int64_t N, int
     if (g.S > 1 && (partial == nullptr || (int64_t)g.S * Np * t > partial_cap)) return cudaErrorInvalidValue;
     const CUtensorMapDataType vt = fmt == kFmtF16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     CUtensorMap mx, mh, ml;
-    if (!make_map(&mx, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, Xs, (uint64_t)kp.dpad, (uint64_t)Np, (uint32_t)kp.dpad,
-                  (uint32_t)kBK) ||
+    if (!make_map(&mx, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, XsT, (uint64_t)Np, (uint64_t)kp.dpad, (uint32_t)kBK,
+                  (uint32_t)kp.dpad) ||
         !make_map(&mh, vt, 2, vh, 64, (uint64_t)(Np * t / 64), 64, (uint32_t)t) ||
         !make_map(&ml, vt, 2, vl, 64, (uint64_t)(Np * t / 64), 64, (uint32_t)t))
         return cudaErrorInvalidValue;

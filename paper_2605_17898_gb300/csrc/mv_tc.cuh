@@ -75,7 +75,7 @@ template <int T, int DP>
 struct TcLayout {
     static constexpr int kA = kBM * kBK * 2;    // one bf16 half of the entry tile
     static constexpr int kB = T * kBK * 2;      // one bf16 half of the V tile
-    static constexpr int kX = kBK * DP * 4;     // prescaled x_j tile
+    static constexpr int kX = kBK * DP * 4;     // prescaled x_j tile, transposed: [DP][64] floats
     static constexpr int kStage = 2 * kA + 2 * kB + kX;
     static constexpr int kBar = kStages * kStage;      // barriers after the ring
     // + barriers/flags, alignment slack, and a guard band after the ring so that no
@@ -114,7 +114,7 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
 }
 
 // Bounded wait for the phase with the given parity. Returns false on timeout or abort.
-static __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long budget, volatile int *abort_flag,
+static __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long budget, volatile int *abort_flag,
                                               int *err, int code, int sleep_ns = 0) {
     if (mbar_try(bar, parity)) return true;
     const long long t0 = clock64();
@@ -223,8 +223,30 @@ __device__ __forceinline__ void unpack2(uint32_t u, float &a, float &b) {
     }
 }
 
+// Two kernel entries at once on packed float32x2 arithmetic (same roundings as the scalar
+// form in lgp_internal.cuh: FFMA2 performs two independent FFMAs).
+template <int KIND> struct Entry2;
+
+template <> struct Entry2<LGP_RBF> {
+    static __device__ __forceinline__ float2 k(float2 rh2, float2 ls2) {
+        const float2 arg = __ffma2_rn(rh2, make_float2(-1.0f, -1.0f), ls2);
+        return make_float2(ex2_approx(arg.x), ex2_approx(arg.y));
+    }
+};
+
+template <> struct Entry2<LGP_MATERN52> {
+    static __device__ __forceinline__ float2 k(float2 rh2, float2 ls2) {
+        const float2 rh = make_float2(sqrt_approx(rh2.x), sqrt_approx(rh2.y));
+        const float2 arg = __ffma2_rn(rh, make_float2(-kLog2e, -kLog2e), ls2);
+        const float2 e = make_float2(ex2_approx(arg.x), ex2_approx(arg.y));
+        float2 poly = __ffma2_rn(rh2, make_float2(1.0f / 3.0f, 1.0f / 3.0f), rh);
+        poly = __fadd2_rn(poly, make_float2(1.0f, 1.0f));
+        return __fmul2_rn(poly, e);
+    }
+};
+
 struct TcArgs {
-    const float *Xs;     // prescaled x [Np, DP] (the rows of this CTA)
+    const float *Xs;     // prescaled x [Np, DP] (row-major; each generation thread reads its own rows)
     const float *V;      // user V [N, ldv] (for the sigma^2 V term)
     float *out;          // [N, ldo] or nullptr in split mode
     float *partial;      // [S, Np, T] in split mode
@@ -307,7 +329,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 uint8_t *st = smem + s * L::kStage;
                 const int q = c_begin + it;
                 mbar_arrive_expect_tx(bar_full(s), (uint32_t)(2 * L::kB + L::kX));
-                tma_load_2d(smem_u32(st + 2 * L::kA + 2 * L::kB), &tm_x, 0, q * kBK, bar_full(s));
+                tma_load_2d(smem_u32(st + 2 * L::kA + 2 * L::kB), &tm_x, q * kBK, 0, bar_full(s));
                 tma_load_2d(smem_u32(st + 2 * L::kA), &tm_vh, 0, q * T, bar_full(s));
                 tma_load_2d(smem_u32(st + 2 * L::kA + L::kB), &tm_vl, 0, q * T, bar_full(s));
                 last_it[s] = it;
@@ -368,52 +390,48 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ------------------------------------------------------------ generation (warps 0-15)
         const int kg = warp & 7;    // this warp's 8-column group of every chunk
         const int half = warp >> 3; // rows 64*half .. 64*half + 63
-        // this thread's 2 rows of the prescaled x (row0 + 127 < Np because Np % 256 == 0)
-        float xi[2][D];
+        const float2 m1 = make_float2(-1.0f, -1.0f);
+        const float2 ls2 = make_float2(a.log2s2, a.log2s2);
+        // this thread's 2 rows of the prescaled x, each coordinate duplicated into both halves
+        // of a float2 (row0 + 127 < Np because Np % 256 == 0)
+        float2 xi2[2][D];
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
             const float *xr = a.Xs + (row0 + 64 * half + 32 * r + lane) * DP;
 #pragma unroll
-            for (int d = 0; d < D; ++d) xi[r][d] = xr[d];
+            for (int d = 0; d < D; ++d) xi2[r][d] = make_float2(xr[d], xr[d]);
         }
         for (int it = 0; it < n_it; ++it) {
             const int s = it % kStages;
             const bool got = mbar_wait(bar_full(s), (it / kStages) & 1, a.budget, abort_flag, a.err, kErrWaitFull);
             if (!__all_sync(0xffffffffu, got)) break;
             uint8_t *st = smem + s * L::kStage;
-            const float *xs = reinterpret_cast<const float *>(st + 2 * L::kA + 2 * L::kB);
+            const float *xs = reinterpret_cast<const float *>(st + 2 * L::kA + 2 * L::kB);  // [DP][64]
             float k[2][8];
 #pragma unroll
             for (int jh = 0; jh < 2; ++jh) {
-                float xj[4][D];
+                // columns j = 8*kg + 4*jh + {0,1} (pair 0) and {2,3} (pair 1), every coordinate
+                float2 xj2[D][2];
 #pragma unroll
-                for (int jj = 0; jj < 4; ++jj) {
-                    const float *p = xs + (8 * kg + 4 * jh + jj) * DP;
-                    const float4 q0 = *reinterpret_cast<const float4 *>(p);
-                    xj[jj][0] = q0.x;
-                    if (D > 1) xj[jj][1 < D ? 1 : 0] = q0.y;
-                    if (D > 2) xj[jj][2 < D ? 2 : 0] = q0.z;
-                    if (D > 3) xj[jj][3 < D ? 3 : 0] = q0.w;
-                    if (DP == 8) {
-                        const float4 q1 = *reinterpret_cast<const float4 *>(p + 4);
-                        if (D > 4) xj[jj][4 < D ? 4 : 0] = q1.x;
-                        if (D > 5) xj[jj][5 < D ? 5 : 0] = q1.y;
-                        if (D > 6) xj[jj][6 < D ? 6 : 0] = q1.z;
-                        if (D > 7) xj[jj][7 < D ? 7 : 0] = q1.w;
-                    }
+                for (int d = 0; d < D; ++d) {
+                    const float4 q = *reinterpret_cast<const float4 *>(xs + d * kBK + 8 * kg + 4 * jh);
+                    xj2[d][0] = make_float2(q.x, q.y);
+                    xj2[d][1] = make_float2(q.z, q.w);
                 }
 #pragma unroll
                 for (int r = 0; r < 2; ++r) {
 #pragma unroll
-                    for (int jj = 0; jj < 4; ++jj) {
-                        float d0 = xi[r][0] - xj[jj][0];
-                        float r2 = d0 * d0;
+                    for (int jp = 0; jp < 2; ++jp) {
+                        float2 dd = __ffma2_rn(xj2[0][jp], m1, xi2[r][0]);
+                        float2 r2 = __fmul2_rn(dd, dd);
 #pragma unroll
                         for (int d = 1; d < D; ++d) {
-                            const float dd = xi[r][d] - xj[jj][d];
-                            r2 = fmaf(dd, dd, r2);
+                            dd = __ffma2_rn(xj2[d][jp], m1, xi2[r][d]);
+                            r2 = __ffma2_rn(dd, dd, r2);
                         }
-                        k[r][4 * jh + jj] = Entry<KIND>::k(r2, a.log2s2);
+                        const float2 kv = Entry2<KIND>::k(r2, ls2);
+                        k[r][4 * jh + 2 * jp] = kv.x;
+                        k[r][4 * jh + 2 * jp + 1] = kv.y;
                     }
                 }
             }
@@ -427,7 +445,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     h[u] = pack2<FMT>(k[r][2 * u], k[r][2 * u + 1]);
                     float h0, h1;
                     unpack2<FMT>(h[u], h0, h1);
-                    l[u] = pack2<FMT>(k[r][2 * u] - h0, k[r][2 * u + 1] - h1);
+                    const float2 lo = __ffma2_rn(make_float2(h0, h1), m1, make_float2(k[r][2 * u], k[r][2 * u + 1]));
+                    l[u] = pack2<FMT>(lo.x, lo.y);
                 }
                 const int rg = 8 * half + 4 * r + (lane >> 3);
                 const int off = (kg * 16 + rg) * 128 + (lane & 7) * 16;

@@ -30,7 +30,7 @@ constexpr int kNoallocMaxT = 32;
 constexpr int kNoallocMaxSplits = 16;    // the product's grid splits the columns at most 16 ways at Np = 8192
 
 constexpr size_t kXsBytes = (size_t)kNoallocNp * 8 * sizeof(float);
-constexpr size_t kVsplitBytes = (size_t)2 * kNoallocNp * kNoallocMaxT * 2 + 2 * 64 * 4;
+constexpr size_t kVsplitBytes = (size_t)2 * kNoallocNp * kNoallocMaxT * 2 + 2 * 64 * 4 + (size_t)8 * kNoallocNp * 4;
 constexpr size_t kPartialBytes = (size_t)kNoallocMaxSplits * kNoallocNp * kNoallocMaxT * sizeof(float);
 constexpr size_t kFlagBytes = 256;
 

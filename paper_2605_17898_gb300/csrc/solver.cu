@@ -38,6 +38,16 @@ __device__ void block_col_reduce(double v, int t, double *red, double *out_row) 
     if (tid < t) out_row[tid] = red[tid];
 }
 
+// Sum of partial[b * stride + c] over b < G by one warp: lane l adds b = l, l + 32, ... in order,
+// then a fixed shuffle tree combines the lanes (same order every call).
+__device__ __forceinline__ double warp_sum_partials(const double *__restrict__ partial, int G, int stride, int c) {
+    const int lane = threadIdx.x & 31;
+    double s = 0.0;
+    for (int b = lane; b < G; b += 32) s += partial[(int64_t)b * stride + c];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    return __shfl_sync(0xffffffffu, s, 0);
+}
+
 // Row range of block b when G blocks share N rows.
 __device__ __forceinline__ void block_rows(int64_t N, int64_t *r0, int64_t *r1) {
     const int64_t per = (N + gridDim.x - 1) / gridDim.x;
@@ -62,27 +72,29 @@ __global__ void cg_init_kernel(const float *__restrict__ B, int64_t ldb, int64_t
     block_col_reduce(s, t, red, partial + (int64_t)blockIdx.x * t);
 }
 
+// Scalar kernels run as one block of 32 * min(t, 32) threads: warp w owns columns w, w + 32.
 __global__ void cg_init_scalars_kernel(CgState *st, const double *__restrict__ partial, int G, int t, double tol,
                                        int max_iter, int hist_len) {
-    const int c = threadIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     int any = 0;
     int bad = 0;
-    if (c < t) {
-        double s = 0.0;
-        for (int b = 0; b < G; ++b) s += partial[(int64_t)b * t + c];
+    for (int c = warp; c < t; c += nw) {
+        const double s = warp_sum_partials(partial, G, t, c);
+        if (lane != 0) continue;
         st->bnorm2[c] = s;
         st->rr[c] = s;
         st->alpha[c] = 0.0;
         st->beta[c] = 0.0;
         st->iters[c] = 0;
-        bad = !isfinite(s);
-        const int act = (s > 0.0) && !bad;
+        const int b_ = !isfinite(s);
+        bad |= b_;
+        const int act = (s > 0.0) && !b_;
         st->active[c] = act;
-        any = act;
+        any |= act;
     }
     any = __syncthreads_or(any);
     bad = __syncthreads_or(bad);
-    if (c == 0) {
+    if (threadIdx.x == 0) {
         st->iter = 0;
         st->t = t;
         st->tol = tol;
@@ -108,14 +120,14 @@ __global__ void cg_pkp_kernel(const float *__restrict__ p, const float *__restri
 
 __global__ void cg_alpha_kernel(CgState *st, const double *__restrict__ partial, int G, double *hist_alpha) {
     if (st->done) return;
-    const int c = threadIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const int t = st->t;
     int bad = 0, nonfinite = 0;
-    if (c < t) {
+    for (int c = warp; c < t; c += nw) {
         double alpha = 0.0;
         if (st->active[c]) {
-            double pkp = 0.0;
-            for (int b = 0; b < G; ++b) pkp += partial[(int64_t)b * t + c];
+            const double pkp = warp_sum_partials(partial, G, t, c);
+            if (lane != 0) continue;
             if (!isfinite(pkp)) {
                 nonfinite = 1;
                 st->active[c] = 0;
@@ -126,12 +138,13 @@ __global__ void cg_alpha_kernel(CgState *st, const double *__restrict__ partial,
                 alpha = st->rr[c] / pkp;
             }
         }
+        if (lane != 0) continue;
         st->alpha[c] = alpha;
         if (st->iter < st->hist_len) hist_alpha[(int64_t)st->iter * t + c] = alpha;
     }
     bad = __syncthreads_or(bad);
     nonfinite = __syncthreads_or(nonfinite);
-    if (c == 0 && (bad || nonfinite) && st->status == 0)
+    if (threadIdx.x == 0 && (bad || nonfinite) && st->status == 0)
         st->status = nonfinite ? (int)LGP_ERR_NONFINITE : (int)LGP_ERR_BREAKDOWN;
 }
 
@@ -160,25 +173,26 @@ __global__ void cg_xr_kernel(float *__restrict__ x, float *__restrict__ r, const
 
 __global__ void cg_beta_kernel(CgState *st, const double *__restrict__ partial, int G, double *hist_beta) {
     if (st->done) return;
-    const int c = threadIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const int t = st->t;
     int any = 0;
-    if (c < t) {
+    for (int c = warp; c < t; c += nw) {
         double beta = 0.0;
         if (st->active[c]) {
-            double rr = 0.0;
-            for (int b = 0; b < G; ++b) rr += partial[(int64_t)b * t + c];
+            const double rr = warp_sum_partials(partial, G, t, c);
+            if (lane != 0) continue;
             beta = rr / st->rr[c];
             st->rr[c] = rr;
             st->iters[c] += 1;
             if (!(sqrt(rr) > st->tol * sqrt(st->bnorm2[c]))) st->active[c] = 0;
         }
+        if (lane != 0) continue;
         st->beta[c] = beta;
         if (st->iter < st->hist_len) hist_beta[(int64_t)st->iter * t + c] = beta;
-        any = st->active[c];
+        any |= st->active[c];
     }
     any = __syncthreads_or(any);
-    if (c == 0) {
+    if (threadIdx.x == 0) {
         st->iter += 1;
         if (!any || st->iter >= st->max_iter) st->done = 1;
     }
@@ -378,16 +392,17 @@ void launch_cg_init(const float *B, int64_t ldb, int64_t N, int64_t Np, int t, c
                     int max_iter, int hist_len, cudaStream_t st) {
     (void)Np;
     cg_init_kernel<<<b.G, vec_block(t), 0, st>>>(B, ldb, N, t, b.x, b.r, b.p, b.partial);
-    cg_init_scalars_kernel<<<1, kMaxT, 0, st>>>(b.state, b.partial, b.G, t, tol, max_iter, hist_len);
+    cg_init_scalars_kernel<<<1, 32 * (t < 32 ? t : 32), 0, st>>>(b.state, b.partial, b.G, t, tol, max_iter, hist_len);
 }
 
 void launch_cg_after_matvec(int64_t N, int64_t Np, int t, const CgBuffers &b, cudaStream_t st) {
     (void)Np;
     const int bd = vec_block(t);
     cg_pkp_kernel<<<b.G, bd, 0, st>>>(b.p, b.Kp, N, t, b.state, b.partial);
-    cg_alpha_kernel<<<1, kMaxT, 0, st>>>(b.state, b.partial, b.G, b.hist_alpha);
+    const int sb = 32 * (t < 32 ? t : 32);
+    cg_alpha_kernel<<<1, sb, 0, st>>>(b.state, b.partial, b.G, b.hist_alpha);
     cg_xr_kernel<<<b.G, bd, 0, st>>>(b.x, b.r, b.p, b.Kp, N, t, b.state, b.partial);
-    cg_beta_kernel<<<1, kMaxT, 0, st>>>(b.state, b.partial, b.G, b.hist_beta);
+    cg_beta_kernel<<<1, sb, 0, st>>>(b.state, b.partial, b.G, b.hist_beta);
     cg_p_kernel<<<b.G, bd, 0, st>>>(b.p, b.r, N, t, b.state);
 }
 
