@@ -305,19 +305,48 @@ lgp_status run_cg(lgp_ctx *ctx, const Prepared &pp, const float *B, int64_t ldb,
             cudaGraphExecDestroy(ctx->cg_exec);
             ctx->cg_exec = nullptr;
         }
-        LGP_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        // One graph for the whole solve: a conditional WHILE node whose body is a chunk of
+        // kChunk iterations followed by a kernel that sets the condition to "not done and under
+        // the chunk cap", so the iteration loop runs on the device with no host round trip.
+        cudaGraph_t g = nullptr;
+        LGP_CUDA(cudaGraphCreate(&g, 0));
+        cudaGraphConditionalHandle h;
+        cudaError_t ce = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+        // the parameter struct holds a union with no default constructor: zero raw storage instead
+        alignas(cudaGraphNodeParams) unsigned char np_storage[sizeof(cudaGraphNodeParams)] = {};
+        cudaGraphNodeParams &np = *reinterpret_cast<cudaGraphNodeParams *>(np_storage);
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t node;
+        if (ce == cudaSuccess) ce = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+        if (ce != cudaSuccess) {
+            cudaGraphDestroy(g);
+            return fail(ctx, LGP_ERR_CUDA, "conditional graph node: %s", cudaGetErrorString(ce));
+        }
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        ce = cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (ce != cudaSuccess) {
+            cudaGraphDestroy(g);
+            return fail(ctx, LGP_ERR_CUDA, "capture to graph: %s", cudaGetErrorString(ce));
+        }
         lgp_status cs = LGP_OK;
         for (int k = 0; k < kChunk && cs == LGP_OK; ++k) {
             cs = matvec_prepared(ctx, pp, b.p, t, b.Kp, t, t, prec, &b.state->done, st);
             if (cs == LGP_OK) launch_cg_after_matvec(pp.N, pp.Np, t, b, st);
         }
-        cudaGraph_t g = nullptr;
-        cudaError_t ce = cudaStreamEndCapture(st, &g);
+        if (cs == LGP_OK) launch_cg_loop_condition(h, b.state, st);
+        cudaGraph_t captured = nullptr;
+        ce = cudaStreamEndCapture(st, &captured);
         if (cs != LGP_OK) {
-            if (g) cudaGraphDestroy(g);
+            cudaGraphDestroy(g);
             return cs;
         }
-        if (ce != cudaSuccess) return fail(ctx, LGP_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ce));
+        if (ce != cudaSuccess) {
+            cudaGraphDestroy(g);
+            return fail(ctx, LGP_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ce));
+        }
         ce = cudaGraphInstantiate(&ctx->cg_exec, g, 0);
         cudaGraphDestroy(g);
         if (ce != cudaSuccess) {
@@ -326,22 +355,8 @@ lgp_status run_cg(lgp_ctx *ctx, const Prepared &pp, const float *B, int64_t ldb,
         }
         ctx->cg_key = key;
     }
-    // Replay chunks; the host checks the done flag of chunk k while chunk k+1 runs.
-    const int max_chunks = (opt->max_iter + kChunk - 1) / kChunk + 1;
-    int prev = -1;
-    int launched = 0;
-    for (int k = 0; k < max_chunks; ++k) {
-        LGP_CUDA(cudaGraphLaunch(ctx->cg_exec, st));
-        ++launched;
-        const int slot = k & 1;
-        LGP_CUDA(cudaMemcpyAsync(ctx->h_done + slot, &b.state->done, sizeof(int), cudaMemcpyDeviceToHost, st));
-        LGP_CUDA(cudaEventRecord(ctx->ev_chunk[slot], st));
-        if (prev >= 0) {
-            LGP_CUDA(cudaEventSynchronize(ctx->ev_chunk[prev]));
-            if (ctx->h_done[prev]) break;
-        }
-        prev = slot;
-    }
+    LGP_CUDA(cudaGraphLaunch(ctx->cg_exec, st));
+    const int launched = 1;
     LGP_CUDA(cudaMemcpyAsync(ctx->h_state, b.state, sizeof(CgState), cudaMemcpyDeviceToHost, st));
     *bout = b;
     if (chunks_run) *chunks_run = launched;
@@ -641,9 +656,12 @@ lgp_status lgp_lml_and_grad(lgp_ctx *ctx, const lgp_hyper *hyp, const float *X, 
         info->iters_max = *std::max_element(it.begin(), it.end());
         info->iters_min = *std::min_element(it.begin(), it.end());
         info->max_rel_resid = *std::max_element(rel.begin(), rel.end());
-        info->cg_chunks = chunks;
-        // prep_x, y copy, probes, CG init (2), the replayed chunks, column dots (2), SLQ, adjoint (3)
-        info->launches = 3 + 2 + chunks * kChunk * cg_iteration_launches(ctx, pp, t, prec) + 2 + 1 + (grad ? 3 : 0);
+        // chunks the device loop ran (each: kChunk iterations + the condition kernel)
+        const int ran = ctx->h_state->loop_chunks;
+        info->cg_chunks = ran;
+        (void)chunks;
+        // prep_x, y copy, probes, CG init (2), the loop's chunks, column dots (2), SLQ, adjoint (3)
+        info->launches = 3 + 2 + ran * (kChunk * cg_iteration_launches(ctx, pp, t, prec) + 1) + 2 + 1 + (grad ? 3 : 0);
     }
     return cs;
 }

@@ -89,6 +89,8 @@ struct CgState {
     int max_iter;
     int hist_len;      // Lanczos steps kept per column
     int t;
+    int loop_chunks;   // chunks run by the device-side while loop
+    int max_chunks;    // hard cap on loop_chunks (the loop ends even if `done` were never set)
     double tol;
     int active[kMaxT];
     int iters[kMaxT];
@@ -160,6 +162,8 @@ void launch_cg_init(const float *B, int64_t ldb, int64_t N, int64_t Np, int t, c
                     int max_iter, int hist_len, cudaStream_t st);
 void launch_cg_after_matvec(int64_t N, int64_t Np, int t, const CgBuffers &b, cudaStream_t st);
 void launch_cg_copy_out(const CgBuffers &b, int64_t N, int t, float *Xsol, int64_t ldx, cudaStream_t st);
+// Body tail of the device-side CG loop: sets the while-node condition to "not done and under the chunk cap".
+void launch_cg_loop_condition(cudaGraphConditionalHandle h, CgState *state, cudaStream_t st);
 int cg_num_blocks(int64_t N, int t, int num_sms);
 
 // Column dot products sum_i A[i,c] B[i,c] and sum_i A[i,c]^2 (float64), c < t: out[2t].

@@ -102,6 +102,8 @@ __global__ void cg_init_scalars_kernel(CgState *st, const double *__restrict__ p
         st->hist_len = hist_len;
         st->status = bad ? (int)LGP_ERR_NONFINITE : 0;
         st->done = (!any || bad) ? 1 : 0;
+        st->loop_chunks = 0;
+        st->max_chunks = max_iter / 8 + 2;
     }
 }
 
@@ -210,6 +212,12 @@ __global__ void cg_p_kernel(float *__restrict__ p, const float *__restrict__ r, 
         const int64_t e = i * t + c;
         p[e] = fmaf(beta, p[e], r[e]);
     }
+}
+
+__global__ void cg_loop_condition_kernel(cudaGraphConditionalHandle h, CgState *st) {
+    st->loop_chunks += 1;
+    const bool more = !st->done && st->loop_chunks < st->max_chunks;
+    cudaGraphSetConditional(h, more ? 1u : 0u);
 }
 
 __global__ void copy_out_kernel(const float *__restrict__ x, int64_t N, int t, float *__restrict__ out, int64_t ldo) {
@@ -404,6 +412,10 @@ void launch_cg_after_matvec(int64_t N, int64_t Np, int t, const CgBuffers &b, cu
     cg_xr_kernel<<<b.G, bd, 0, st>>>(b.x, b.r, b.p, b.Kp, N, t, b.state, b.partial);
     cg_beta_kernel<<<1, sb, 0, st>>>(b.state, b.partial, b.G, b.hist_beta);
     cg_p_kernel<<<b.G, bd, 0, st>>>(b.p, b.r, N, t, b.state);
+}
+
+void launch_cg_loop_condition(cudaGraphConditionalHandle h, CgState *state, cudaStream_t st) {
+    cg_loop_condition_kernel<<<1, 1, 0, st>>>(h, state);
 }
 
 void launch_cg_copy_out(const CgBuffers &b, int64_t N, int t, float *Xsol, int64_t ldx, cudaStream_t st) {
