@@ -163,6 +163,8 @@ __global__ void bscal_init_kernel(BatchArgs a, double tol, int max_iter) {
         a.st->max_iter = max_iter;
         a.st->tol = tol;
         a.st->status = 0;
+        a.st->loop_chunks = 0;
+        a.st->max_chunks = max_iter / 8 + 2;
     }
     if (k >= a.n_gp * a.t) return;
     const int gi = k / a.t, c = k % a.t;
@@ -299,6 +301,12 @@ __global__ void bcopy_out_kernel(BatchArgs a) {
         g.Xsol[i * t + c] = a.x[(g.vec_off + i) * t + c];
 }
 
+__global__ void batch_loop_condition_kernel(cudaGraphConditionalHandle h, BatchArgs a) {
+    a.st->loop_chunks += 1;
+    const bool more = !*a.done && a.st->loop_chunks < a.st->max_chunks;
+    cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
 inline int vec_threads(int t) { return (kVec / t) * t; }
 
 }  // namespace
@@ -334,6 +342,11 @@ cudaError_t launch_batch_iteration(const BatchArgs &a, int num_sms, cudaStream_t
     bbeta_kernel<<<sb, 256, 0, st>>>(a);
     bdone_kernel<<<1, 256, 0, st>>>(a, 0);
     bp_kernel<<<a.n_vblocks, vt, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_loop_condition(cudaGraphConditionalHandle h, const BatchArgs &a, cudaStream_t st) {
+    batch_loop_condition_kernel<<<1, 1, 0, st>>>(h, a);
     return cudaGetLastError();
 }
 

@@ -30,6 +30,7 @@ struct BatchVecBlock {
 
 struct BatchState {
     int iter, max_iter, status;
+    int loop_chunks, max_chunks;  // device-side loop count and its hard cap
     double tol;
 };
 
@@ -53,5 +54,7 @@ int batch_item_rows();
 cudaError_t launch_batch_init(const BatchArgs &a, double tol, int max_iter, cudaStream_t st);
 cudaError_t launch_batch_iteration(const BatchArgs &a, int num_sms, cudaStream_t st);
 cudaError_t launch_batch_copy_out(const BatchArgs &a, cudaStream_t st);
+// Body tail of the device-side batch loop: condition = not done and under the chunk cap.
+cudaError_t launch_batch_loop_condition(cudaGraphConditionalHandle h, const BatchArgs &a, cudaStream_t st);
 
 }  // namespace lgp

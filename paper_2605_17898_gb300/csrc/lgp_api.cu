@@ -776,14 +776,33 @@ lgp_status lgp_batch_cg_solve(lgp_ctx *ctx, int32_t n_gp, const lgp_hyper *hyp, 
                       gps[g].Np, (int *)ctx->flags.p, st);
     LGP_CUDA(launch_batch_init(A, opt->tol, opt->max_iter, st));
 
-    // capture a chunk of iterations once, replay until every column of every problem has stopped
-    LGP_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    cudaError_t ce = cudaSuccess;
-    for (int k = 0; k < kChunk && ce == cudaSuccess; ++k) ce = launch_batch_iteration(A, ctx->num_sms, st);
+    // one graph: a conditional WHILE node whose body is a chunk of iterations plus the condition kernel,
+    // so every iteration of every problem runs without a host round trip
     cudaGraph_t graph = nullptr;
-    cudaError_t ce2 = cudaStreamEndCapture(st, &graph);
+    LGP_CUDA(cudaGraphCreate(&graph, 0));
+    cudaGraphConditionalHandle h;
+    cudaError_t ce = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
+    alignas(cudaGraphNodeParams) unsigned char np_storage[sizeof(cudaGraphNodeParams)] = {};
+    cudaGraphNodeParams &np = *reinterpret_cast<cudaGraphNodeParams *>(np_storage);
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (ce == cudaSuccess) ce = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np);
+    if (ce == cudaSuccess)
+        ce = cudaStreamBeginCaptureToGraph(st, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal);
+    if (ce != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return fail(ctx, LGP_ERR_CUDA, "batch conditional graph: %s", cudaGetErrorString(ce));
+    }
+    for (int k = 0; k < kChunk && ce == cudaSuccess; ++k) ce = launch_batch_iteration(A, ctx->num_sms, st);
+    if (ce == cudaSuccess) ce = launch_batch_loop_condition(h, A, st);
+    cudaGraph_t captured = nullptr;
+    cudaError_t ce2 = cudaStreamEndCapture(st, &captured);
     if (ce != cudaSuccess || ce2 != cudaSuccess) {
-        if (graph) cudaGraphDestroy(graph);
+        cudaGraphDestroy(graph);
         return fail(ctx, LGP_ERR_CUDA, "batch graph capture failed: %s",
                     cudaGetErrorString(ce != cudaSuccess ? ce : ce2));
     }
@@ -791,21 +810,10 @@ lgp_status lgp_batch_cg_solve(lgp_ctx *ctx, int32_t n_gp, const lgp_hyper *hyp, 
     ce = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     if (ce != cudaSuccess) return fail(ctx, LGP_ERR_CUDA, "batch graph instantiate failed: %s", cudaGetErrorString(ce));
-    const int max_chunks = (opt->max_iter + kChunk - 1) / kChunk + 1;
-    int prev = -1;
-    for (int k = 0; k < max_chunks && ce == cudaSuccess; ++k) {
-        ce = cudaGraphLaunch(exec, st);
-        const int slot = k & 1;
-        if (ce == cudaSuccess) ce = cudaMemcpyAsync(ctx->h_done + slot, A.done, sizeof(int), cudaMemcpyDeviceToHost, st);
-        if (ce == cudaSuccess) ce = cudaEventRecord(ctx->ev_chunk[slot], st);
-        if (ce == cudaSuccess && prev >= 0) {
-            ce = cudaEventSynchronize(ctx->ev_chunk[prev]);
-            if (ce == cudaSuccess && ctx->h_done[prev]) break;
-        }
-        prev = slot;
-    }
+    ce = cudaGraphLaunch(exec, st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
     cudaGraphExecDestroy(exec);
-    if (ce != cudaSuccess) return fail(ctx, LGP_ERR_CUDA, "batch replay failed: %s", cudaGetErrorString(ce));
+    if (ce != cudaSuccess) return fail(ctx, LGP_ERR_CUDA, "batch loop failed: %s", cudaGetErrorString(ce));
     LGP_CUDA(launch_batch_copy_out(A, st));
     std::vector<int> h_it(ng_t), h_act(ng_t);
     std::vector<double> h_rr(ng_t), h_b2(ng_t);

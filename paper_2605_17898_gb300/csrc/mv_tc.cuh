@@ -14,14 +14,19 @@
 //             lo half but keep an absolute error below 2^-40 s^2.
 //
 // CTA structure (one CTA per SM: 22 warps, ~190 KB shared memory):
-//   warps 0-15  generate the 128 x 64 entry tile of each column chunk in registers (each
-//               thread: 2 rows x 8 columns) and write its hi/lo halves to shared memory in the
-//               K-major no-swizzle layout the MMA reads;
-//   warp 16     producer: TMA (cp.async.bulk.tensor) of the prescaled x_j tile and of the
-//               pre-split V_hi / V_lo tiles into a 4-stage ring;
-//   warp 17     allocates two tensor-memory accumulators (128 lanes x 32 float32 columns
-//               each) and one elected thread issues the tcgen05.mma instructions (M=128,
-//               N=t, K=16, three per K step) and commits them to the ring's "empty" barriers;
+//   warps 0-15  generate the 128 x 64 entry tile of each column chunk in registers. Two ways
+//               to hand it to the MMA, chosen by D at compile time:
+//               - A in tensor memory (D <= 4): each thread computes one row x 16 columns and
+//                 stores the hi/lo halves with tcgen05.st (lane = row, two 16-bit entries per
+//                 32-bit column); the entry tile never touches shared memory;
+//               - A in shared memory (D > 4): each thread computes 2 rows x 8 columns, which
+//                 halves its x_j loads, and stores the halves in the K-major no-swizzle layout;
+//   warp 16     producer: TMA (cp.async.bulk.tensor) of the transposed prescaled x_j tile and
+//               of the pre-split V_hi / V_lo tiles into a shared-memory ring;
+//   warp 17     allocates tensor memory (two float32 accumulators of 128 lanes x 32 columns,
+//               plus the entry stages when A lives there) and one elected thread issues the
+//               tcgen05.mma instructions (M=128, N=t, K=16, three per K step) and commits them
+//               to the ring's "empty" barriers;
 //   warps 18-21 drain: every kGroup chunks the MMA switches accumulator and these warps move
 //               the finished one into float32 registers (round-to-nearest adds), so no
 //               tensor-core accumulation chain is longer than kGroup * 12 MMAs; they also run
@@ -56,7 +61,10 @@ constexpr int kFmtF16 = 1;
 
 namespace tc {
 
-constexpr int kStages = 4;
+// pipeline depth: 6 stages with A in tensor memory (10 KB of shared memory each), 4 with A in
+// shared memory (43 KB each)
+template <bool ATMEM> struct Depth { static constexpr int value = ATMEM ? 6 : 4; };
+constexpr int kMaxStages = 6;
 constexpr int kBM = 128;          // rows per CTA (MMA M)
 constexpr int kBK = 64;           // columns j per chunk (4 MMA K steps)
 constexpr int kGenWarps = 16;
@@ -66,22 +74,37 @@ constexpr int kDrainWarp0 = 18;
 constexpr int kThreads = 704;     // 16 generation warps + producer + MMA + 4 drain warps
 constexpr int kGroup = 2;         // chunks accumulated in tensor memory between drains
 constexpr int kAccCols = 32;      // tensor-memory columns per accumulator buffer
+constexpr int kAStageCols = 64;   // tensor-memory columns per entry stage (hi 32 + lo 32)
+constexpr int kACol0 = 2 * kAccCols;
+template <bool ATMEM> struct TmemCols { static constexpr int value = ATMEM ? 512 : 64; };
 constexpr long long kDrainBudget = 2000000000LL;
 
 // error codes written to the device error word on a timeout
 constexpr int kErrWaitFull = 0x10, kErrWaitEmpty = 0x20, kErrWaitReady = 0x40, kErrWaitAcc = 0x80;
 
-template <int T, int DP>
+// Shared-memory stage: [A hi | A lo] (only when A lives in shared memory) [V hi | V lo] [x tile].
+template <int T, int DP, bool ATMEM>
 struct TcLayout {
-    static constexpr int kA = kBM * kBK * 2;    // one bf16 half of the entry tile
-    static constexpr int kB = T * kBK * 2;      // one bf16 half of the V tile
-    static constexpr int kX = kBK * DP * 4;     // prescaled x_j tile, transposed: [DP][64] floats
+    static constexpr int kStages = Depth<ATMEM>::value;
+    static constexpr int kA = ATMEM ? 0 : kBM * kBK * 2;  // one 16-bit half of the entry tile
+    static constexpr int kB = T * kBK * 2;                // one 16-bit half of the V tile
+    static constexpr int kX = kBK * DP * 4;               // prescaled x_j tile, transposed: [DP][64] floats
     static constexpr int kStage = 2 * kA + 2 * kB + kX;
     static constexpr int kBar = kStages * kStage;      // barriers after the ring
     // + barriers/flags, alignment slack, and a guard band after the ring so that no
     // descriptor-addressed read of the last stage can leave the CTA's allocation
-    static constexpr int kBytes = kBar + 256 + 1024 + 16384;
+    static constexpr int kBytes = kBar + 256 + 1024 + 4096;
 };
+
+// A from shared memory (descriptor) instead of tensor memory.
+__device__ __forceinline__ void mma_ss(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -160,14 +183,24 @@ __device__ __forceinline__ uint32_t instr_desc() {
     return (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(T >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+// D (tensor memory) += A (tensor memory) x B (shared-memory descriptor); acc = 0 overwrites D.
+__device__ __forceinline__ void mma_ts(uint32_t tmem_d, uint32_t tmem_a, uint64_t b, uint32_t idesc, uint32_t acc) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "r"(tmem_a), "l"(b), "r"(idesc), "r"(acc)
         : "memory");
 }
+
+// Eight 32-bit columns of this thread's tensor-memory lane.
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&v)[8]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(v[0]),
+                 "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
@@ -266,7 +299,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     mv_tc_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ CUtensorMap tm_vh,
                  const __grid_constant__ CUtensorMap tm_vl, const TcArgs a) {
     constexpr int DP = D <= 4 ? 4 : 8;
-    using L = TcLayout<T, DP>;
+    constexpr bool ATMEM = D <= 4;
+    using L = TcLayout<T, DP, ATMEM>;
+    constexpr int kStages = L::kStages;
+    constexpr int kTmemCols = TmemCols<ATMEM>::value;
     extern __shared__ uint8_t smem_raw[];
     if (a.skip && *a.skip) return;
 
@@ -307,7 +343,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         fence_async_smem();
     }
     if (warp == kMmaWarp) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(smem_u32(tmem_slot))
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "n"(kTmemCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -362,18 +399,29 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tc_fence_after();
                 const uint32_t acc = tmem_acc + (uint32_t)(buf * kAccCols);
                 const uint32_t st = smem_u32(smem + s * L::kStage);
-                const uint32_t a_hi = st, a_lo = st + L::kA, b_hi = st + 2 * L::kA, b_lo = b_hi + L::kB;
+                const uint32_t b_hi = st + 2 * L::kA, b_lo = b_hi + L::kB;
+                // A in tensor memory: hi at columns [a_col, a_col + 32), lo at +32, K step ks reads 8
+                // columns (16 entries) of each. A in shared memory: core matrix (row group rg, k group
+                // kg) at (kg * 16 + rg) * 128 bytes.
+                const uint32_t a_col = tmem_acc + (uint32_t)(kACol0 + s * kAStageCols);
 #pragma unroll
                 for (int ks = 0; ks < kBK / 16; ++ks) {
-                    // A: core matrix (row group rg, k group kg) at (kg * 16 + rg) * 128 bytes
-                    const uint64_t dah = smem_desc(a_hi + ks * 4096, 2048, 128);
-                    const uint64_t dal = smem_desc(a_lo + ks * 4096, 2048, 128);
                     // B: core matrix (column group cg, k group kg) at (kg * T/8 + cg) * 128 bytes
                     const uint64_t dbh = smem_desc(b_hi + ks * 2 * T * 16, T * 16, 128);
                     const uint64_t dbl = smem_desc(b_lo + ks * 2 * T * 16, T * 16, 128);
-                    mma_bf16(acc, dah, dbh, idesc, (group_start && ks == 0) ? 0u : 1u);
-                    mma_bf16(acc, dah, dbl, idesc, 1u);
-                    mma_bf16(acc, dal, dbh, idesc, 1u);
+                    const uint32_t first = (group_start && ks == 0) ? 0u : 1u;
+                    if constexpr (ATMEM) {
+                        const uint32_t ah = a_col + 8 * ks, al = a_col + 32 + 8 * ks;
+                        mma_ts(acc, ah, dbh, idesc, first);
+                        mma_ts(acc, ah, dbl, idesc, 1u);
+                        mma_ts(acc, al, dbh, idesc, 1u);
+                    } else {
+                        const uint64_t dah = smem_desc(st + ks * 4096, 2048, 128);
+                        const uint64_t dal = smem_desc(st + L::kA + ks * 4096, 2048, 128);
+                        mma_ss(acc, dah, dbh, idesc, first);
+                        mma_ss(acc, dah, dbl, idesc, 1u);
+                        mma_ss(acc, dal, dbh, idesc, 1u);
+                    }
                 }
                 mma_commit(bar_empty(s));
                 if (group_end) mma_commit(bar_acc_full(buf));
@@ -387,6 +435,65 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         }
     } else if (warp < kGenWarps) {
+        if constexpr (ATMEM) {
+        // ------------------------------------------------------------ generation (warps 0-15)
+        const int quarter = warp & 3;  // tensor-memory lanes (= rows) 32*quarter .. +31
+        const int cgrp = warp >> 2;    // columns 16*cgrp .. 16*cgrp + 15 of every chunk
+        const float2 m1 = make_float2(-1.0f, -1.0f);
+        const float2 ls2 = make_float2(a.log2s2, a.log2s2);
+        // this thread's row of the prescaled x, each coordinate duplicated into both halves of a
+        // float2 (row0 + 127 < Np because Np % 256 == 0)
+        float2 xi2[D];
+        {
+            const float *xr = a.Xs + (row0 + 32 * quarter + lane) * DP;
+#pragma unroll
+            for (int d = 0; d < D; ++d) xi2[d] = make_float2(xr[d], xr[d]);
+        }
+        const uint32_t lane_addr = tmem_acc + ((uint32_t)(32 * quarter) << 16);
+        for (int it = 0; it < n_it; ++it) {
+            const int s = it % kStages;
+            const bool got = mbar_wait(bar_full(s), (it / kStages) & 1, a.budget, abort_flag, a.err, kErrWaitFull);
+            if (!__all_sync(0xffffffffu, got)) break;
+            const float *xs = reinterpret_cast<const float *>(smem + s * L::kStage + 2 * L::kA + 2 * L::kB);  // [DP][64]
+            uint32_t h[8], l[8];
+#pragma unroll
+            for (int jq = 0; jq < 4; ++jq) {
+                // columns j = 16*cgrp + 4*jq + {0,1} (pair 0) and {2,3} (pair 1), every coordinate
+                float2 xj2[D][2];
+#pragma unroll
+                for (int d = 0; d < D; ++d) {
+                    const float4 q = *reinterpret_cast<const float4 *>(xs + d * kBK + 16 * cgrp + 4 * jq);
+                    xj2[d][0] = make_float2(q.x, q.y);
+                    xj2[d][1] = make_float2(q.z, q.w);
+                }
+#pragma unroll
+                for (int jp = 0; jp < 2; ++jp) {
+                    float2 dd = __ffma2_rn(xj2[0][jp], m1, xi2[0]);
+                    float2 r2 = __fmul2_rn(dd, dd);
+#pragma unroll
+                    for (int d = 1; d < D; ++d) {
+                        dd = __ffma2_rn(xj2[d][jp], m1, xi2[d]);
+                        r2 = __ffma2_rn(dd, dd, r2);
+                    }
+                    const float2 kv = Entry2<KIND>::k(r2, ls2);
+                    const uint32_t hw = pack2<FMT>(kv.x, kv.y);
+                    float h0, h1;
+                    unpack2<FMT>(hw, h0, h1);
+                    const float2 lo = __ffma2_rn(make_float2(h0, h1), m1, kv);
+                    h[2 * jq + jp] = hw;
+                    l[2 * jq + jp] = pack2<FMT>(lo.x, lo.y);
+                }
+            }
+            // 16 entries = 8 columns of this row's lane in the stage's hi and lo regions
+            const uint32_t col = (uint32_t)(kACol0 + s * kAStageCols + 8 * cgrp);
+            tmem_st8(lane_addr + col, h);
+            tmem_st8(lane_addr + col + 32, l);
+            tmem_wait_st();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar_ready(s));
+        }
+        } else {
         // ------------------------------------------------------------ generation (warps 0-15)
         const int kg = warp & 7;    // this warp's 8-column group of every chunk
         const int half = warp >> 3; // rows 64*half .. 64*half + 63
@@ -457,6 +564,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             __syncwarp();
             if (lane == 0) mbar_arrive(bar_ready(s));
         }
+        }
     } else if (warp >= kDrainWarp0) {
         // ------------------------------------------------------------ drain + epilogue (warps 18-21)
         const int quarter = warp & 3;  // tensor-memory lanes 32*quarter .. +31
@@ -505,7 +613,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     if (warp == kMmaWarp) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem_acc) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_acc), "n"(kTmemCols)
+                     : "memory");
     }
 }
 

@@ -10,7 +10,7 @@ template <int KIND, int D, int T, int FMT>
 cudaError_t launch_tc_inst(dim3 grid, const CUtensorMap &mx, const CUtensorMap &mh, const CUtensorMap &ml,
                            const TcArgs &a, cudaStream_t st) {
     constexpr int DP = D <= 4 ? 4 : 8;
-    constexpr int bytes = TcLayout<T, DP>::kBytes;
+    constexpr int bytes = TcLayout<T, DP, (D <= 4)>::kBytes;
     static bool configured = false;
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(mv_tc_kernel<KIND, D, T, FMT>,
