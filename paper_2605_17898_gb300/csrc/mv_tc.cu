@@ -31,12 +31,13 @@ __device__ __forceinline__ int col_exponent(unsigned int maxbits) {
     return min(60, max(-60, 15 - ex));
 }
 
-// V -> (V_hi, V_lo) in the tile order the MMA reads: element (j, c) of chunk q = j / 64 sits at
-// q*64*T + ((j%64)/8 * T/8 + c/8) * 64 + (c%8) * 8 + j%8; rows j >= N are zero.
+// V -> stacked [V_hi; V_lo] in the tile order the MMA reads: B row c' = c (hi) or t + c (lo);
+// element (j, c') of chunk q = j / 64 sits at q*64*2t + ((j%64)/8 * 2t/8 + c'/8) * 64 + (c'%8) * 8 + j%8;
+// rows j >= N are zero.
 // FMT f16: V is first scaled per column by 2^e_c and col_scale[c] = s^2 2^-15 2^-e_c is written.
 template <int T, int FMT>
 __global__ void split_v_kernel(const float *__restrict__ V, int64_t ldv, int64_t N, int64_t Np,
-                               uint16_t *__restrict__ vh, uint16_t *__restrict__ vl,
+                               uint16_t *__restrict__ vs,
                                const unsigned int *__restrict__ vmax, float *__restrict__ col_scale, float s2,
                                const int *skip) {
     if (skip && *skip) return;
@@ -62,9 +63,9 @@ __global__ void split_v_kernel(const float *__restrict__ V, int64_t ldv, int64_t
         }
         const int64_t q = j / kBK;
         const int jj = (int)(j - q * kBK);
-        const int64_t off = q * kBK * T + (int64_t)((jj >> 3) * (T / 8) + (c >> 3)) * 64 + (c & 7) * 8 + (jj & 7);
-        vh[off] = h;
-        vl[off] = l;
+        const int64_t chunk = q * kBK * 2 * T + (int64_t)(jj >> 3) * (2 * T / 8) * 64 + (c & 7) * 8 + (jj & 7);
+        vs[chunk + (int64_t)(c >> 3) * 64] = h;
+        vs[chunk + (int64_t)((T + c) >> 3) * 64] = l;
     }
 }
 
@@ -179,9 +180,8 @@ cudaError_t launch_mv_tc(const KernelParams &kp, const float *Xs, int64_t N, int
                          float *out, int64_t ldo, int t, int fmt, void *vsplit, float *partial, int64_t partial_cap,
                          const int *skip, int *err_flag, long long wait_budget, int num_sms, cudaStream_t st) {
     if (!(t == 16 || t == 32) || Np % 256 != 0) return cudaErrorInvalidValue;
-    uint16_t *vh = (uint16_t *)vsplit;
-    uint16_t *vl = vh + Np * t;
-    unsigned int *vmax = (unsigned int *)(vl + Np * t);
+    uint16_t *vs = (uint16_t *)vsplit;  // stacked [V_hi; V_lo], 2 * Np * t entries
+    unsigned int *vmax = (unsigned int *)(vs + 2 * Np * t);
     float *col_scale = (float *)(vmax + 64);
     float *XsT = col_scale + 64;
     const int blocks = (int)std::min<int64_t>((Np * t + 255) / 256, 8192);
@@ -192,14 +192,14 @@ cudaError_t launch_mv_tc(const KernelParams &kp, const float *Xs, int64_t N, int
         const int mb = (int)std::min<int64_t>((N * t + 255) / 256, 1024);
         col_absmax_kernel<<<mb, (256 / t) * t, 0, st>>>(V, ldv, N, t, vmax, skip);
         if (t == 16)
-            split_v_kernel<16, kFmtF16><<<blocks, 256, 0, st>>>(V, ldv, N, Np, vh, vl, vmax, col_scale, kp.s2, skip);
+            split_v_kernel<16, kFmtF16><<<blocks, 256, 0, st>>>(V, ldv, N, Np, vs, vmax, col_scale, kp.s2, skip);
         else
-            split_v_kernel<32, kFmtF16><<<blocks, 256, 0, st>>>(V, ldv, N, Np, vh, vl, vmax, col_scale, kp.s2, skip);
+            split_v_kernel<32, kFmtF16><<<blocks, 256, 0, st>>>(V, ldv, N, Np, vs, vmax, col_scale, kp.s2, skip);
     } else {
         if (t == 16)
-            split_v_kernel<16, kFmtBF16><<<blocks, 256, 0, st>>>(V, ldv, N, Np, vh, vl, vmax, col_scale, kp.s2, skip);
+            split_v_kernel<16, kFmtBF16><<<blocks, 256, 0, st>>>(V, ldv, N, Np, vs, vmax, col_scale, kp.s2, skip);
         else
-            split_v_kernel<32, kFmtBF16><<<blocks, 256, 0, st>>>(V, ldv, N, Np, vh, vl, vmax, col_scale, kp.s2, skip);
+            split_v_kernel<32, kFmtBF16><<<blocks, 256, 0, st>>>(V, ldv, N, Np, vs, vmax, col_scale, kp.s2, skip);
     }
     transpose_x_kernel<<<(int)std::min<int64_t>((Np * kp.dpad + 255) / 256, 4096), 256, 0, st>>>(Xs, Np, kp.dpad,
                                                                                               XsT, skip);
@@ -209,11 +209,10 @@ cudaError_t launch_mv_tc(const KernelParams &kp, const float *Xs, int64_t N, int
     const TcGrid g = tc_grid(Np, num_sms);
     if (g.S > 1 && (partial == nullptr || (int64_t)g.S * Np * t > partial_cap)) return cudaErrorInvalidValue;
     const CUtensorMapDataType vt = fmt == kFmtF16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-    CUtensorMap mx, mh, ml;
+    CUtensorMap mx, mv;
     if (!make_map(&mx, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, XsT, (uint64_t)Np, (uint64_t)kp.dpad, (uint32_t)kBK,
                   (uint32_t)kp.dpad) ||
-        !make_map(&mh, vt, 2, vh, 64, (uint64_t)(Np * t / 64), 64, (uint32_t)t) ||
-        !make_map(&ml, vt, 2, vl, 64, (uint64_t)(Np * t / 64), 64, (uint32_t)t))
+        !make_map(&mv, vt, 2, vs, 64, (uint64_t)(Np * 2 * t / 64), 64, (uint32_t)(2 * t)))
         return cudaErrorInvalidValue;
     tc::TcArgs a;
     a.Xs = Xs;
@@ -233,8 +232,8 @@ cudaError_t launch_mv_tc(const KernelParams &kp, const float *Xs, int64_t N, int
     a.col_scale = fmt == kFmtF16 ? col_scale : nullptr;
     a.budget = wait_budget;
     const dim3 grid((unsigned)g.rb, (unsigned)g.S, 1);
-    e = fmt == kFmtF16 ? tc::dispatch_f16(kp.kind, kp.D, t, grid, mx, mh, ml, a, st)
-                       : tc::dispatch_bf16(kp.kind, kp.D, t, grid, mx, mh, ml, a, st);
+    e = fmt == kFmtF16 ? tc::dispatch_f16(kp.kind, kp.D, t, grid, mx, mv, a, st)
+                       : tc::dispatch_bf16(kp.kind, kp.D, t, grid, mx, mv, a, st);
     if (e != cudaSuccess || g.S == 1) return e;
     const int rblocks = (int)std::min<int64_t>((N * t + 255) / 256, 4096);
     tc_reduce_kernel<<<rblocks, 256, 0, st>>>(partial, g.S, Np, N, t, V, ldv, out, ldo, kp.noise, skip);

@@ -4,6 +4,9 @@
 // global memory) is split as k = hi + lo with hi = rn(k), lo = rn(k - hi) in a 16-bit
 // format; the block V is split the same way once per call. The contraction is
 //   out = K_hi V_hi + K_hi V_lo + K_lo V_hi   (float32 accumulation in tensor memory).
+// V_hi and V_lo are stacked as one B operand of 2t columns, so K_hi [V_hi V_lo] is a single
+// MMA of N = 2t (A read once) and K_lo V_hi a second MMA of N = t over the first half of the
+// same B tile; their three t-column results are summed in float32 when the accumulators drain.
 // Two formats:
 //   kFmtBF16: bfloat16 halves (8 significant bits each, about 16 bits per factor);
 //   kFmtF16:  float16 halves (11 bits each, about 22 bits per factor) on values scaled
@@ -63,7 +66,7 @@ namespace tc {
 
 // pipeline depth: 6 stages with A in tensor memory (10 KB of shared memory each), 4 with A in
 // shared memory (43 KB each)
-template <bool ATMEM> struct Depth { static constexpr int value = ATMEM ? 6 : 4; };
+template <bool ATMEM> struct Depth { static constexpr int value = 4; };
 constexpr int kMaxStages = 6;
 constexpr int kBM = 128;          // rows per CTA (MMA M)
 constexpr int kBK = 64;           // columns j per chunk (4 MMA K steps)
@@ -73,10 +76,10 @@ constexpr int kMmaWarp = 17;
 constexpr int kDrainWarp0 = 18;
 constexpr int kThreads = 704;     // 16 generation warps + producer + MMA + 4 drain warps
 constexpr int kGroup = 2;         // chunks accumulated in tensor memory between drains
-constexpr int kAccCols = 32;      // tensor-memory columns per accumulator buffer
+constexpr int kAccCols = 128;     // tensor-memory columns per accumulator buffer: [hi*[Vh Vl] (2t) | lo*Vh (t)]
 constexpr int kAStageCols = 64;   // tensor-memory columns per entry stage (hi 32 + lo 32)
 constexpr int kACol0 = 2 * kAccCols;
-template <bool ATMEM> struct TmemCols { static constexpr int value = ATMEM ? 512 : 64; };
+template <bool ATMEM> struct TmemCols { static constexpr int value = ATMEM ? 512 : 256; };
 constexpr long long kDrainBudget = 2000000000LL;
 
 // error codes written to the device error word on a timeout
@@ -87,7 +90,7 @@ template <int T, int DP, bool ATMEM>
 struct TcLayout {
     static constexpr int kStages = Depth<ATMEM>::value;
     static constexpr int kA = ATMEM ? 0 : kBM * kBK * 2;  // one 16-bit half of the entry tile
-    static constexpr int kB = T * kBK * 2;                // one 16-bit half of the V tile
+    static constexpr int kB = T * kBK * 2;                // one 16-bit half of the V tile (stacked: 2 kB)
     static constexpr int kX = kBK * DP * 4;               // prescaled x_j tile, transposed: [DP][64] floats
     static constexpr int kStage = 2 * kA + 2 * kB + kX;
     static constexpr int kBar = kStages * kStage;      // barriers after the ring
@@ -177,10 +180,10 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
 }
 
 // Instruction descriptor: kind::f16, A = B = bf16 or f16 (K-major), D = f32, M = 128, N = T.
-template <int T, int FMT>
+template <int NCOLS, int FMT>
 __device__ __forceinline__ uint32_t instr_desc() {
     constexpr uint32_t ab = FMT == kFmtBF16 ? 1u : 0u;
-    return (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(T >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
+    return (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(NCOLS >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
 }
 
 // D (tensor memory) += A (tensor memory) x B (shared-memory descriptor); acc = 0 overwrites D.
@@ -296,8 +299,8 @@ struct TcArgs {
 
 template <int KIND, int D, int T, int FMT>
 __global__ void __launch_bounds__(kThreads, 1)
-    mv_tc_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ CUtensorMap tm_vh,
-                 const __grid_constant__ CUtensorMap tm_vl, const TcArgs a) {
+    mv_tc_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ CUtensorMap tm_v,
+                 const TcArgs a) {
     constexpr int DP = D <= 4 ? 4 : 8;
     constexpr bool ATMEM = D <= 4;
     using L = TcLayout<T, DP, ATMEM>;
@@ -367,8 +370,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int q = c_begin + it;
                 mbar_arrive_expect_tx(bar_full(s), (uint32_t)(2 * L::kB + L::kX));
                 tma_load_2d(smem_u32(st + 2 * L::kA + 2 * L::kB), &tm_x, q * kBK, 0, bar_full(s));
-                tma_load_2d(smem_u32(st + 2 * L::kA), &tm_vh, 0, q * T, bar_full(s));
-                tma_load_2d(smem_u32(st + 2 * L::kA + L::kB), &tm_vl, 0, q * T, bar_full(s));
+                tma_load_2d(smem_u32(st + 2 * L::kA), &tm_v, 0, q * 2 * T, bar_full(s));
                 last_it[s] = it;
             }
             if (*abort_flag) {
@@ -383,7 +385,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else if (warp == kMmaWarp) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
-            const uint32_t idesc = instr_desc<T, FMT>();
+            const uint32_t idesc2 = instr_desc<2 * T, FMT>();  // K_hi x [V_hi V_lo]
+            const uint32_t idesc1 = instr_desc<T, FMT>();      // K_lo x V_hi
             bool issued = false;
             for (int it = 0; it < n_it; ++it) {
                 const int s = it % kStages;
@@ -399,28 +402,27 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tc_fence_after();
                 const uint32_t acc = tmem_acc + (uint32_t)(buf * kAccCols);
                 const uint32_t st = smem_u32(smem + s * L::kStage);
-                const uint32_t b_hi = st + 2 * L::kA, b_lo = b_hi + L::kB;
+                const uint32_t b_v = st + 2 * L::kA;  // stacked [V_hi; V_lo]: 2t B rows
                 // A in tensor memory: hi at columns [a_col, a_col + 32), lo at +32, K step ks reads 8
                 // columns (16 entries) of each. A in shared memory: core matrix (row group rg, k group
                 // kg) at (kg * 16 + rg) * 128 bytes.
                 const uint32_t a_col = tmem_acc + (uint32_t)(kACol0 + s * kAStageCols);
 #pragma unroll
                 for (int ks = 0; ks < kBK / 16; ++ks) {
-                    // B: core matrix (column group cg, k group kg) at (kg * T/8 + cg) * 128 bytes
-                    const uint64_t dbh = smem_desc(b_hi + ks * 2 * T * 16, T * 16, 128);
-                    const uint64_t dbl = smem_desc(b_lo + ks * 2 * T * 16, T * 16, 128);
+                    // B: core matrix (stacked column group cg in 0..2t/8, k group kg) at
+                    // (kg * 2t/8 + cg) * 128 bytes; the first t/8 groups are V_hi
+                    const uint64_t dbv = smem_desc(b_v + ks * 2 * (2 * T) * 16, 2 * T * 16, 128);
+                    const uint32_t acc_lo = acc + 2 * T;
                     const uint32_t first = (group_start && ks == 0) ? 0u : 1u;
                     if constexpr (ATMEM) {
                         const uint32_t ah = a_col + 8 * ks, al = a_col + 32 + 8 * ks;
-                        mma_ts(acc, ah, dbh, idesc, first);
-                        mma_ts(acc, ah, dbl, idesc, 1u);
-                        mma_ts(acc, al, dbh, idesc, 1u);
+                        mma_ts(acc, ah, dbv, idesc2, first);
+                        mma_ts(acc_lo, al, dbv, idesc1, first);
                     } else {
                         const uint64_t dah = smem_desc(st + ks * 4096, 2048, 128);
                         const uint64_t dal = smem_desc(st + L::kA + ks * 4096, 2048, 128);
-                        mma_ss(acc, dah, dbh, idesc, first);
-                        mma_ss(acc, dah, dbl, idesc, 1u);
-                        mma_ss(acc, dal, dbh, idesc, 1u);
+                        mma_ss(acc, dah, dbv, idesc2, first);
+                        mma_ss(acc_lo, dal, dbv, idesc1, first);
                     }
                 }
                 mma_commit(bar_empty(s));
@@ -580,14 +582,19 @@ __global__ void __launch_bounds__(kThreads, 1)
                 break;
             }
             tc_fence_after();
-            uint32_t v[T];
-            tmem_ld<T>(tmem_acc + (uint32_t)(buf * kAccCols) + ((uint32_t)(32 * quarter) << 16), v);
-            tmem_wait_ld();
+            const uint32_t base = tmem_acc + (uint32_t)(buf * kAccCols) + ((uint32_t)(32 * quarter) << 16);
+            // blocks: K_hi V_hi at +0, K_hi V_lo at +t, K_lo V_hi at +2t (one at a time: registers)
+#pragma unroll
+            for (int blk = 0; blk < 3; ++blk) {
+                uint32_t v[T];
+                tmem_ld<T>(base + (uint32_t)(blk * T), v);
+                tmem_wait_ld();
+#pragma unroll
+                for (int c = 0; c < T; ++c) sum[c] += __uint_as_float(v[c]);
+            }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(bar_acc_empty(buf));
-#pragma unroll
-            for (int c = 0; c < T; ++c) sum[c] += __uint_as_float(v[c]);
         }
         if (ok && !*abort_flag) {
             const int64_t i = row0 + 32 * quarter + lane;
