@@ -6,7 +6,9 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -49,6 +51,8 @@ struct lgp_ctx {
     // cached CG graph
     cudaGraphExec_t cg_exec = nullptr;
     std::vector<unsigned char> cg_key;
+    // autotuned column-split counts of the tensor-core product, keyed by (Np, t, fmt, D, kind)
+    std::map<std::vector<int64_t>, int> tc_splits;
 };
 
 namespace {
@@ -183,19 +187,82 @@ lgp_status prepare_x(lgp_ctx *ctx, const lgp_hyper *hyp, const float *X, int64_t
     return LGP_OK;
 }
 
+std::vector<int64_t> tc_key(const Prepared &pp, int t, int prec) {
+    return {pp.Np, (int64_t)t, (int64_t)tc_fmt(prec), (int64_t)pp.kp.D, (int64_t)pp.kp.kind};
+}
+
+int tc_splits_for(const lgp_ctx *ctx, const Prepared &pp, int t, int prec) {
+    auto it = ctx->tc_splits.find(tc_key(pp, t, prec));
+    return it == ctx->tc_splits.end() ? 0 : it->second;
+}
+
+// Autotuner of the tensor-core product's column-split count (set LGP_AUTOTUNE=0 to keep the
+// wave-efficiency heuristic): on the first product of a shape, time the three most
+// wave-efficient split counts on the caller's own inputs (one warm-up and two timed launches
+// each, CUDA events on the stream) and keep the fastest for that shape. Never runs during a
+// stream capture.
+lgp_status autotune_tc(lgp_ctx *ctx, const Prepared &pp, const float *V, int64_t ldv, float *out, int64_t ldo, int t,
+                       int prec, cudaStream_t st) {
+    const std::vector<int64_t> key = tc_key(pp, t, prec);
+    if (ctx->tc_splits.count(key)) return LGP_OK;
+    const char *env = std::getenv("LGP_AUTOTUNE");
+    int cand[3], n = 0;
+    tc_split_candidates(pp.Np, ctx->num_sms, cand, &n);
+    if ((env && env[0] == '0') || n <= 1) {
+        ctx->tc_splits[key] = 0;
+        return LGP_OK;
+    }
+    int64_t need = 1;
+    for (int k = 0; k < n; ++k) need = std::max(need, mv_tc_partial_floats(pp.Np, t, ctx->num_sms, cand[k]));
+    lgp_status s;
+    if ((s = ensure(ctx, ctx->mv_partial, (size_t)need * sizeof(float))) != LGP_OK) return s;
+    if ((s = ensure(ctx, ctx->vsplit, (size_t)tc_vsplit_bytes(pp.Np, t))) != LGP_OK) return s;
+    cudaEvent_t e0, e1;
+    LGP_CUDA(cudaEventCreate(&e0));
+    LGP_CUDA(cudaEventCreate(&e1));
+    int best = 0;
+    float best_ms = 1e30f;
+    cudaError_t ce = cudaSuccess;
+    for (int k = 0; k < n && ce == cudaSuccess; ++k) {
+        float total = 0.0f;
+        for (int rep = 0; rep < 3 && ce == cudaSuccess; ++rep) {
+            ce = cudaEventRecord(e0, st);
+            if (ce == cudaSuccess)
+                ce = launch_mv_tc(pp.kp, pp.xs, pp.N, pp.Np, V, ldv, out, ldo, t, tc_fmt(prec), ctx->vsplit.p,
+                                  (float *)ctx->mv_partial.p, (int64_t)(ctx->mv_partial.bytes / sizeof(float)), nullptr,
+                                  (int *)ctx->flags.p + 1, ctx->wait_budget, ctx->num_sms, st, cand[k]);
+            if (ce == cudaSuccess) ce = cudaEventRecord(e1, st);
+            if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) total += ms;
+        }
+        if (ce == cudaSuccess && total < best_ms) {
+            best_ms = total;
+            best = cand[k];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (ce != cudaSuccess) return fail(ctx, LGP_ERR_CUDA, "autotune launch failed: %s", cudaGetErrorString(ce));
+    ctx->tc_splits[key] = best;
+    return LGP_OK;
+}
+
 // K_y V for prepared X. V has row stride ldv; out has row stride ldo.
 lgp_status matvec_prepared(lgp_ctx *ctx, const Prepared &pp, const float *V, int64_t ldv, float *out, int64_t ldo,
                            int t, int prec, const int *skip, cudaStream_t st) {
     if (is_tc(prec)) {
         lgp_status s = ensure(ctx, ctx->vsplit, (size_t)tc_vsplit_bytes(pp.Np, t));
         if (s != LGP_OK) return s;
-        const int64_t pf = mv_tc_partial_floats(pp.Np, t, ctx->num_sms);
+        const int forced = tc_splits_for(ctx, pp, t, prec);
+        const int64_t pf = mv_tc_partial_floats(pp.Np, t, ctx->num_sms, forced);
         s = ensure(ctx, ctx->mv_partial, (size_t)std::max<int64_t>(pf, 1) * sizeof(float));
         if (s != LGP_OK) return s;
         LGP_CUDA(launch_mv_tc(pp.kp, pp.xs, pp.N, pp.Np, V, ldv, out, ldo, t, tc_fmt(prec), ctx->vsplit.p,
                               (float *)ctx->mv_partial.p,
                               (int64_t)(ctx->mv_partial.bytes / sizeof(float)), skip, (int *)ctx->flags.p + 1,
-                              ctx->wait_budget, ctx->num_sms, st));
+                              ctx->wait_budget, ctx->num_sms, st, forced));
         return LGP_OK;
     }
     const int64_t pf = mv_simt_partial_floats(pp.N, pp.Np, t, ctx->num_sms);
@@ -254,7 +321,7 @@ lgp_status cg_buffers(lgp_ctx *ctx, int64_t N, int64_t Np, int t, int hist_len, 
 
 // Run CG on the internal stream: init, then replay a captured chunk of iterations until done.
 int matvec_launches(const lgp_ctx *ctx, const Prepared &pp, int t, int prec) {
-    return is_tc(prec) ? mv_tc_launches(pp.Np, t, ctx->num_sms, tc_fmt(prec))
+    return is_tc(prec) ? mv_tc_launches(pp.Np, t, ctx->num_sms, tc_fmt(prec), tc_splits_for(ctx, pp, t, prec))
                        : mv_simt_launches(pp.N, pp.Np, t, ctx->num_sms);
 }
 
@@ -271,8 +338,10 @@ lgp_status run_cg(lgp_ctx *ctx, const Prepared &pp, const float *B, int64_t ldb,
     if (s != LGP_OK) return s;
     // the product's own workspace must exist before capture (no allocation inside a capture)
     if (is_tc(prec)) {
+        // tune the product on this solve's right-hand sides (Kp is scratch here) before capture
+        if ((s = autotune_tc(ctx, pp, B, ldb, b.Kp, t, t, prec, st)) != LGP_OK) return s;
         if ((s = ensure(ctx, ctx->vsplit, (size_t)tc_vsplit_bytes(pp.Np, t))) != LGP_OK) return s;
-        const int64_t pf = mv_tc_partial_floats(pp.Np, t, ctx->num_sms);
+        const int64_t pf = mv_tc_partial_floats(pp.Np, t, ctx->num_sms, tc_splits_for(ctx, pp, t, prec));
         if ((s = ensure(ctx, ctx->mv_partial, (size_t)std::max<int64_t>(pf, 1) * sizeof(float))) != LGP_OK) return s;
     } else {
         const int64_t pf = mv_simt_partial_floats(pp.N, pp.Np, t, ctx->num_sms);
@@ -522,6 +591,11 @@ lgp_status lgp_kernel_matvec(lgp_ctx *ctx, const lgp_hyper *hyp, const float *X,
     cudaStream_t st = (cudaStream_t)stream;
     Prepared pp;
     if ((s = prepare_x(ctx, hyp, X, N, st, &pp)) != LGP_OK) return s;
+    if (is_tc(p)) {
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        LGP_CUDA(cudaStreamIsCapturing(st, &cap));
+        if (cap == cudaStreamCaptureStatusNone && (s = autotune_tc(ctx, pp, V, t, out, t, t, p, st)) != LGP_OK) return s;
+    }
     return matvec_prepared(ctx, pp, V, t, out, t, t, p, nullptr, st);
 }
 

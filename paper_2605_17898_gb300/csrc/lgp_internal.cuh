@@ -143,11 +143,16 @@ int64_t adjoint_partial_doubles(int64_t N, int t, int D, int num_sms);
 bool tc_supported(int t);
 int64_t tc_vsplit_bytes(int64_t Np, int t);
 // fmt: 0 = bfloat16 halves, 1 = scaled float16 halves
+// forced_splits > 0 overrides the column-split count (the autotuner's choice); 0 = wave-efficiency heuristic.
 cudaError_t launch_mv_tc(const KernelParams &kp, const float *Xs, int64_t N, int64_t Np, const float *V, int64_t ldv,
                          float *out, int64_t ldo, int t, int fmt, void *vsplit, float *partial, int64_t partial_cap,
-                         const int *skip, int *err_flag, long long wait_budget, int num_sms, cudaStream_t st);
+                         const int *skip, int *err_flag, long long wait_budget, int num_sms, cudaStream_t st,
+                         int forced_splits = 0);
 int64_t mv_tc_partial_floats(int64_t Np, int t, int num_sms);
-int mv_tc_launches(int64_t Np, int t, int num_sms, int fmt);
+int64_t mv_tc_partial_floats(int64_t Np, int t, int num_sms, int forced_splits);
+int mv_tc_launches(int64_t Np, int t, int num_sms, int fmt, int forced_splits = 0);
+// Up to three split counts worth timing, most wave-efficient first.
+void tc_split_candidates(int64_t Np, int num_sms, int *cand, int *n);
 
 // solver.cu
 struct CgBuffers {

@@ -134,29 +134,42 @@ struct TcGrid {
     int rb, S, cps, total;
 };
 
-// Column splits: fill the SMs with whole waves of one-CTA-per-SM work where possible.
-TcGrid tc_grid(int64_t Np, int num_sms) {
+// Wave efficiency of s column splits: work items over whole waves of one-CTA-per-SM, with a
+// mild preference for fewer splits.
+double split_efficiency(int rb, int total, int s, int num_sms) {
+    const int cps = (total + s - 1) / s;
+    const int real_s = (total + cps - 1) / cps;
+    const long long ctas = (long long)rb * real_s;
+    const long long waves = (ctas + num_sms - 1) / num_sms;
+    return (double)ctas / (double)(waves * num_sms) - 0.002 * s;
+}
+
+int max_splits(int total) { return std::max(1, std::min(32, total / 8)); }
+
+TcGrid grid_for_splits(int64_t Np, int s) {
     TcGrid g;
     g.rb = (int)(Np / kBM);
     g.total = (int)(Np / kBK);
+    s = std::max(1, std::min(s, max_splits(g.total)));
+    g.cps = (g.total + s - 1) / s;
+    g.S = (g.total + g.cps - 1) / g.cps;
+    return g;
+}
+
+// Column splits chosen by wave efficiency (the autotuner may override with a measured choice).
+TcGrid tc_grid(int64_t Np, int num_sms, int forced_splits = 0) {
+    if (forced_splits > 0) return grid_for_splits(Np, forced_splits);
+    const int rb = (int)(Np / kBM), total = (int)(Np / kBK);
     int best_s = 1;
     double best_eff = -1.0;
-    const int max_s = std::max(1, std::min(32, g.total / 8));
-    for (int s = 1; s <= max_s; ++s) {
-        const int cps = (g.total + s - 1) / s;
-        const int real_s = (g.total + cps - 1) / cps;
-        const long long ctas = (long long)g.rb * real_s;
-        const long long waves = (ctas + num_sms - 1) / num_sms;
-        // efficiency of the last wave, with a mild preference for fewer splits
-        const double eff = (double)ctas / (double)(waves * num_sms) - 0.002 * s;
+    for (int s = 1; s <= max_splits(total); ++s) {
+        const double eff = split_efficiency(rb, total, s, num_sms);
         if (eff > best_eff + 1e-9) {
             best_eff = eff;
             best_s = s;
         }
     }
-    g.cps = (g.total + best_s - 1) / best_s;
-    g.S = (g.total + g.cps - 1) / g.cps;
-    return g;
+    return grid_for_splits(Np, best_s);
 }
 
 }  // namespace
@@ -167,18 +180,43 @@ bool tc_supported(int t) { return (t == 16 || t == 32) && encode_fn() != nullptr
 // transposed prescaled X [8, Np] float32.
 int64_t tc_vsplit_bytes(int64_t Np, int t) { return 2 * Np * t * 2 + 2 * 64 * 4 + 8 * Np * 4; }
 
-int64_t mv_tc_partial_floats(int64_t Np, int t, int num_sms) {
-    const TcGrid g = tc_grid(Np, num_sms);
+int64_t mv_tc_partial_floats(int64_t Np, int t, int num_sms, int forced_splits) {
+    const TcGrid g = tc_grid(Np, num_sms, forced_splits);
     return g.S > 1 ? (int64_t)g.S * Np * t : 0;
 }
 
-int mv_tc_launches(int64_t Np, int t, int num_sms, int fmt) {
-    return (mv_tc_partial_floats(Np, t, num_sms) > 0 ? 4 : 3) + (fmt == kFmtF16 ? 1 : 0);
+int64_t mv_tc_partial_floats(int64_t Np, int t, int num_sms) { return mv_tc_partial_floats(Np, t, num_sms, 0); }
+
+void tc_split_candidates(int64_t Np, int num_sms, int *cand, int *n) {
+    const int rb = (int)(Np / kBM), total = (int)(Np / kBK);
+    *n = 0;
+    // the three most wave-efficient split counts, best first
+    for (int k = 0; k < 3; ++k) {
+        int best_s = 0;
+        double best_eff = -1e9;
+        for (int s = 1; s <= max_splits(total); ++s) {
+            bool taken = false;
+            for (int q = 0; q < *n; ++q) taken |= cand[q] == grid_for_splits(Np, s).S;
+            if (taken) continue;
+            const double eff = split_efficiency(rb, total, s, num_sms);
+            if (eff > best_eff + 1e-9) {
+                best_eff = eff;
+                best_s = s;
+            }
+        }
+        if (best_s == 0) break;
+        cand[(*n)++] = grid_for_splits(Np, best_s).S;
+    }
+}
+
+int mv_tc_launches(int64_t Np, int t, int num_sms, int fmt, int forced_splits) {
+    return (mv_tc_partial_floats(Np, t, num_sms, forced_splits) > 0 ? 4 : 3) + (fmt == kFmtF16 ? 1 : 0);
 }
 
 cudaError_t launch_mv_tc(const KernelParams &kp, const float *Xs, int64_t N, int64_t Np, const float *V, int64_t ldv,
                          float *out, int64_t ldo, int t, int fmt, void *vsplit, float *partial, int64_t partial_cap,
-                         const int *skip, int *err_flag, long long wait_budget, int num_sms, cudaStream_t st) {
+                         const int *skip, int *err_flag, long long wait_budget, int num_sms, cudaStream_t st,
+                         int forced_splits) {
     if (!(t == 16 || t == 32) || Np % 256 != 0) return cudaErrorInvalidValue;
     uint16_t *vs = (uint16_t *)vsplit;  // stacked [V_hi; V_lo], 2 * Np * t entries
     unsigned int *vmax = (unsigned int *)(vs + 2 * Np * t);
@@ -206,7 +244,7 @@ cudaError_t launch_mv_tc(const KernelParams &kp, const float *Xs, int64_t N, int
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
 
-    const TcGrid g = tc_grid(Np, num_sms);
+    const TcGrid g = tc_grid(Np, num_sms, forced_splits);
     if (g.S > 1 && (partial == nullptr || (int64_t)g.S * Np * t > partial_cap)) return cudaErrorInvalidValue;
     const CUtensorMapDataType vt = fmt == kFmtF16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     CUtensorMap mx, mv;

@@ -220,3 +220,24 @@ def test_tensor_core_agrees_with_fp32_path(lgp):
     a = _run(lgp, p, V, prec=lgp.LGP_PREC_FP32).astype(np.float64)
     b = _run(lgp, p, V, prec=lgp.LGP_PREC_SPLIT_F16).astype(np.float64)
     assert (np.linalg.norm(a - b, axis=0) / np.linalg.norm(a, axis=0)).max() <= TOL
+
+
+def test_autotuned_split_count_gives_the_same_product(lgp):
+    """The autotuner only changes how the column range is split across CTAs: every candidate
+    split must give the product within the tolerance (here: autotuning on vs off, fresh contexts)."""
+    import os
+    import torch
+    p = wl.cfg3(N=9000, t=32)
+    X = torch.as_tensor(p.X, device="cuda")
+    V = torch.as_tensor(wl.rhs_block(p.N, 32, seed=4), device="cuda")
+    outs = []
+    for flag in ["1", "0"]:
+        os.environ["LGP_AUTOTUNE"] = flag
+        ctx = lgp.Context(0)
+        outs.append(lgp.lgp_kernel_matvec(X, p, V, prec=lgp.LGP_PREC_SPLIT_F16, ctx=ctx).cpu().numpy())
+        torch.cuda.synchronize()
+        ctx.close()
+    os.environ.pop("LGP_AUTOTUNE", None)
+    ref = go.matvec(p.X, wl.rhs_block(p.N, 32, seed=4), go.hyper_of(p))
+    for o in outs:
+        assert _colerr(o, ref).max() <= TOL
