@@ -31,6 +31,12 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "matvec pair·RHS evals/s and LML+grad time, N=100k t=32, vs plain FP32 path"
+# DRAM bytes (read + write) of one full-size product launch (N=100000, D=8, M52, t=32), from one
+# `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum` capture (profiles/), valid only for the
+# kernel source it was taken on: the bench reports null once a header of that kernel changes.
+TRAFFIC = {"mv_tc_kernel": {"bytes": None, "source_sha256_16": None},
+           "mv_tcs_kernel": {"bytes": None, "source_sha256_16": None}}
+KERNEL_SOURCES = {"mv_tc_kernel": ["mv_tc.cuh"], "mv_tcs_kernel": ["mv_tcs.cuh", "mv_tc.cuh"]}
 UNIT = "pair*RHS/s"
 SM_COUNT_NOMINAL = 152
 FP32_LANES_PER_SM = 128
@@ -148,21 +154,49 @@ def gpu_uuid(dev_index):
         return None
 
 
+def measured_peaks():
+    """The machine's measured copy bandwidth and bf16 GEMM rates (MEASURED_PEAKS.json), else the
+    earlier single measurement used as fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return {"bf16_tflops": float(d["bf16_tflops"]), "hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    except Exception:
+        return {"bf16_tflops": 1900.0, "hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def kernel_source_hash(name):
+    """First 16 hex digits of the sha256 of the headers that define kernel `name`."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[name]:
+        h.update(open(os.path.join(ROOT, "paper_2605_17898_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def kernel_traffic(name):
+    """Recorded DRAM bytes per launch of `name`, or None if its source changed since the capture."""
+    rec = TRAFFIC.get(name)
+    if not rec or rec["bytes"] is None:
+        return None
+    return rec["bytes"] if kernel_source_hash(name) == rec["source_sha256_16"] else None
+
+
 def flush_l2(buf):
     buf.add_(1.0)
 
 
 def per_pair_ops(kind: int, D: int, split: bool, t: int) -> tuple[float, dict]:
-    """Algorithmic FP32-pipe operations and MUFU operations per (i, j) pair.
+    """Algorithmic FP32-pipe operations and MUFU operations per generated entry k(x_i, x_j).
 
-    Difference form: D subtractions + D multiply-adds for r^2. RBF: one add for the
-    exponent; Matern-5/2: exponent multiply-add, polynomial multiply-add and add,
-    final multiply. Split (tensor-core) path: 2 per entry (the lo subtraction and two
-    half-width roundings counted as half an op each); the contraction runs on the
-    tensor pipe. FP32 SIMT path: t multiply-adds. MUFU: RBF one ex2; Matern-5/2 one
-    sqrt and one ex2.
+    Difference form: D subtractions + D multiply-adds for r^2 (RBF starts the
+    accumulation at -log2 s^2, so its exponent costs nothing more); Matern-5/2:
+    exponent multiply-add, polynomial multiply-add, final multiply-add. Split
+    (tensor-core) path: 2 per entry (the lo subtraction and two half-width roundings
+    counted as half an op each); the contraction runs on the tensor pipe. FP32 SIMT
+    path: t multiply-adds. MUFU: RBF one ex2; Matern-5/2 one sqrt and one ex2.
     """
-    gen = 2 * D + (1 if kind == 0 else 4)
+    gen = 2 * D + (0 if kind == 0 else 3)
     mufu = {"ex2": 1.0, "sqrt": 0.0 if kind == 0 else 1.0}
     return (gen + 2.0, mufu) if split else (gen + t, mufu)
 
@@ -304,27 +338,35 @@ def main():
     torch.cuda.synchronize()
     mv_ms = statistics.mean(a.elapsed_time(b) for a, b in kev)
     split = kprec in (lgp.LGP_PREC_SPLIT_BF16, lgp.LGP_PREC_SPLIT_F16)
+    symmetric = split and ctx.tc_kernel_choice(p.N, p.D, p.kind, args.t, kprec) == lgp.LGP_TC_SYMMETRIC
+    kname = "mv_tcs_kernel" if symmetric else ("mv_tc_kernel" if split else "mv_simt_kernel")
     ops_pair, mufu_pair = per_pair_ops(p.kind, p.D, split, args.t)
     pairs = float(p.N) ** 2
-    achieved_tops = pairs * ops_pair / (mv_ms / 1e3) / 1e12
+    # entries the kernel must generate: the symmetric kernel needs each unordered pair once
+    entries = float(p.N) * (p.N + 1) / 2 if symmetric else pairs
+    achieved_tops = entries * ops_pair / (mv_ms / 1e3) / 1e12
     props = torch.cuda.get_device_properties(local)
     n_sm = props.multi_processor_count
     # peak from unit counts and the maximum SM clock: SMs x 128 FP32 lanes x 2070 MHz
     peak_tops = n_sm * FP32_LANES_PER_SM * MAX_SM_MHZ_NOMINAL * 1e6 / 1e12
+    peaks = measured_peaks()
     meas = {name: lgp.lgp_measure_pipe_peak(i) for i, name in
             enumerate(["ffma", "ffma2_fmas", "mufu_ex2", "mufu_sqrt"])}
-    mufu_time = pairs * (mufu_pair["ex2"] / meas["mufu_ex2"] + mufu_pair["sqrt"] / meas["mufu_sqrt"])
+    mufu_time = entries * (mufu_pair["ex2"] / meas["mufu_ex2"] + mufu_pair["sqrt"] / meas["mufu_sqrt"])
     roofline = {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "Tops/s (FP32 pipe)",
-                "frac": achieved_tops / peak_tops, "traffic": None,
-                "kernel": "mv_tc_kernel" if split else "mv_simt_kernel",
+                "frac": achieved_tops / peak_tops,
+                "traffic": kernel_traffic(kname) if split and p.N == 100000 and args.t == 32 else None,
+                "kernel": kname,
                 "peak_source": "152 SMs x 128 FP32 lanes x 2070 MHz (unit counts and max clock)",
-                "per_pair_ops": ops_pair, "mufu_per_pair": mufu_pair, "matvec_ms": mv_ms,
-                "pairs_per_launch": pairs, "sm_count": n_sm,
+                "per_entry_ops": ops_pair, "mufu_per_entry": mufu_pair, "matvec_ms": mv_ms,
+                "entries_per_launch": entries, "pairs_per_launch": pairs, "sm_count": n_sm,
                 "measured_pipe_peaks_per_s": meas,
                 "frac_of_measured_ffma": achieved_tops * 1e12 / meas["ffma"],
                 "mufu_frac": mufu_time / (mv_ms / 1e3),
                 "tensor_flops_per_launch": pairs * 6 * args.t if split else 0.0,
-                "tensor_frac_of_bf16_burst": (pairs * 6 * args.t / (mv_ms / 1e3)) / 1.89e15 if split else 0.0}
+                "tensor_frac_of_bf16_burst": (pairs * 6 * args.t / (mv_ms / 1e3)) / (peaks["bf16_tflops"] * 1e12)
+                if split else 0.0,
+                "tensor_peak_source": peaks["source"] + " bf16 burst (f16 dense rate = bf16)"}
 
     # ---------------- end to end through the public API with host buffers
     Xh = torch.as_tensor(p.X).pin_memory()
@@ -369,6 +411,7 @@ def main():
             "vs_baseline": None, "dtype": ("f32+f16x3" if kprec == lgp.LGP_PREC_SPLIT_F16 else "f32+bf16x3") if split else "f32",
             "data": "synthetic",
             "config": {"workload": p.name, "N": p.N, "D": p.D, "t": args.t, "kernel": "matern52",
+                       "tc_kernel": kname,
                        "lanczos_steps": args.lanczos, "tol": args.tol, "max_iter": args.max_iter,
                        "cg_iterations": iters,
                        "precision": {1: "fp32", 2: "split_bf16", 3: "split_f16"}.get(kprec, str(kprec)),

@@ -118,6 +118,17 @@ int32_t lgp_version(void);
 /* Human-readable name of a status code (static storage). */
 const char *lgp_status_string(int32_t status);
 
+/* Environment variables read by a context (none changes results beyond float32 rounding order):
+ *   LGP_AUTOTUNE=0      the tensor-core product keeps the row kernel with its wave-efficiency
+ *                       column split instead of timing the candidate kernels on first use of
+ *                       a shape;
+ *   LGP_TC_SYMMETRIC=1  force the symmetric-tile tensor-core kernel (shapes with N > 768);
+ *                       =0 never use it. It adds its tiles' contributions with float32
+ *                       atomic reductions, so its last bits can vary between runs;
+ *   LGP_CG_GRAPH=0      run the CG iteration loop from the host (one launch per kernel, the
+ *                       done flag read back every 8 iterations) instead of one CUDA graph with
+ *                       a device-side while loop; meant for profilers. */
+
 /* Create a context bound to CUDA device `device` (its workspace starts empty).
  * Returns LGP_ERR_INVALID_ARG for a NULL ctx or a device that does not exist,
  * LGP_ERR_UNSUPPORTED if the device is not compute capability 10.3. */
@@ -135,6 +146,14 @@ int64_t lgp_workspace_bytes(const lgp_ctx *ctx);
 /* The lgp_precision lgp_kernel_matvec would use for t columns when asked for `prec`
  * (resolves LGP_PREC_AUTO); a negative lgp_status if that request is unsupported. */
 int32_t lgp_matvec_precision(const lgp_ctx *ctx, int32_t t, int32_t prec);
+
+/* Which tensor-core kernel this context uses for the product of an N-row, D-dimensional
+ * `kind` problem with t columns at precision `prec` (diagnostic; no counterpart in the paper):
+ * LGP_TC_UNTUNED before the first product of that shape, LGP_TC_ROW for the row kernel
+ * (column range split over CTAs), LGP_TC_SYMMETRIC for the symmetric-tile kernel; a negative
+ * lgp_status for invalid arguments or a precision that does not use the tensor cores. */
+enum { LGP_TC_UNTUNED = 0, LGP_TC_ROW = 1, LGP_TC_SYMMETRIC = 2 };
+int32_t lgp_tc_kernel_choice(const lgp_ctx *ctx, int64_t N, int32_t D, int32_t kind, int32_t t, int32_t prec);
 
 /* Bound, in GPU clock cycles, on every device-side wait of the tensor-core product
  * (pipeline barriers between its copy, generation and MMA stages). A wait that

@@ -38,13 +38,16 @@ LGP_PREC_AUTO = 0
 LGP_PREC_FP32 = 1
 LGP_PREC_SPLIT_BF16 = 2
 LGP_PREC_SPLIT_F16 = 3
+LGP_TC_UNTUNED = 0
+LGP_TC_ROW = 1
+LGP_TC_SYMMETRIC = 2
 
 EXPORTED = [
     "lgp_version", "lgp_status_string", "lgp_create", "lgp_destroy", "lgp_last_error_message",
     "lgp_workspace_bytes", "lgp_matvec_precision", "lgp_set_wait_budget", "lgp_check_device_status",
     "lgp_kernel_matvec", "lgp_kernel_matvec_grad", "lgp_cg_solve", "lgp_lml_and_grad",
     "lgp_rademacher_probes", "lgp_batch_cg_solve", "lgp_kernel_matvec_noalloc",
-    "lgp_measure_pipe_peak",
+    "lgp_measure_pipe_peak", "lgp_tc_kernel_choice",
 ]
 
 
@@ -105,6 +108,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "lgp_batch_cg_solve": (c.c_int32, [vp, c.c_int32, c.POINTER(lgp_hyper), vp, vp, vp, vp, c.c_int32,
                                            c.POINTER(lgp_options), vp, vp, vp]),
         "lgp_measure_pipe_peak": (c.c_int32, [c.c_int32, c.POINTER(c.c_double), vp]),
+        "lgp_tc_kernel_choice": (c.c_int32, [vp, c.c_int64, c.c_int32, c.c_int32, c.c_int32, c.c_int32]),
         "lgp_kernel_matvec_noalloc": (c.c_int32, [c.POINTER(lgp_hyper), vp, vp, vp, c.c_int64, c.c_int32, c.c_int32,
                                                   vp]),
     }
@@ -197,6 +201,10 @@ class Context:
 
     def matvec_precision(self, t: int, prec: int = LGP_PREC_AUTO) -> int:
         return int(self.lib.lgp_matvec_precision(self.h, int(t), int(prec)))
+
+    def tc_kernel_choice(self, N: int, D: int, kind: int, t: int, prec: int = LGP_PREC_AUTO) -> int:
+        """LGP_TC_UNTUNED / LGP_TC_ROW / LGP_TC_SYMMETRIC for that product shape (or a negative status)."""
+        return int(self.lib.lgp_tc_kernel_choice(self.h, int(N), int(D), int(kind), int(t), int(prec)))
 
     def set_wait_budget(self, cycles: int):
         self.lib.lgp_set_wait_budget(self.h, int(cycles))

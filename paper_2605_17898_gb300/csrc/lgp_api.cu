@@ -196,18 +196,28 @@ int tc_splits_for(const lgp_ctx *ctx, const Prepared &pp, int t, int prec) {
     return it == ctx->tc_splits.end() ? 0 : it->second;
 }
 
-// Autotuner of the tensor-core product's column-split count (set LGP_AUTOTUNE=0 to keep the
-// wave-efficiency heuristic): on the first product of a shape, time the three most
-// wave-efficient split counts on the caller's own inputs (one warm-up and two timed launches
-// each, CUDA events on the stream) and keep the fastest for that shape. Never runs during a
-// stream capture.
+// Autotuner of the tensor-core product's kernel: on the first product of a shape, time the
+// symmetric-tile kernel and the three most wave-efficient column-split counts of the row kernel
+// on the caller's own inputs (one warm-up and two timed launches each, CUDA events on the
+// stream) and keep the fastest for that shape. Never runs during a stream capture.
+// LGP_AUTOTUNE=0 keeps the row kernel's wave-efficiency heuristic; LGP_TC_SYMMETRIC=1 forces the
+// symmetric kernel (where the shape allows it), LGP_TC_SYMMETRIC=0 leaves it out.
 lgp_status autotune_tc(lgp_ctx *ctx, const Prepared &pp, const float *V, int64_t ldv, float *out, int64_t ldo, int t,
                        int prec, cudaStream_t st) {
     const std::vector<int64_t> key = tc_key(pp, t, prec);
     if (ctx->tc_splits.count(key)) return LGP_OK;
     const char *env = std::getenv("LGP_AUTOTUNE");
-    int cand[3], n = 0;
+    const char *sym = std::getenv("LGP_TC_SYMMETRIC");
+    int cand[4], n = 0;
     tc_split_candidates(pp.Np, ctx->num_sms, cand, &n);
+    if (sym && sym[0] == '1' && tc_symmetric_ok(pp.Np)) {
+        ctx->tc_splits[key] = kTcSymmetric;
+        return LGP_OK;
+    }
+    if (sym && sym[0] == '0' && n > 0 && cand[0] == kTcSymmetric) {
+        for (int k = 1; k < n; ++k) cand[k - 1] = cand[k];
+        --n;
+    }
     if ((env && env[0] == '0') || n <= 1) {
         ctx->tc_splits[key] = 0;
         return LGP_OK;
@@ -353,6 +363,27 @@ lgp_status run_cg(lgp_ctx *ctx, const Prepared &pp, const float *B, int64_t ldb,
 
     launch_cg_init(B, ldb, pp.N, pp.Np, t, b, opt->tol, opt->max_iter, hist_len, st);
     LGP_CUDA(cudaGetLastError());
+
+    const char *graph_env = std::getenv("LGP_CG_GRAPH");
+    if (graph_env && graph_env[0] == '0') {
+        // Host-driven loop: the same kernels launched one by one, the done flag read back after
+        // every chunk (a profiler then sees each launch on its own).
+        int launched = 0;
+        while (true) {
+            for (int k = 0; k < kChunk; ++k) {
+                if ((s = matvec_prepared(ctx, pp, b.p, t, b.Kp, t, t, prec, &b.state->done, st)) != LGP_OK) return s;
+                launch_cg_after_matvec(pp.N, pp.Np, t, b, st);
+            }
+            launch_cg_chunk_tally(b.state, st);
+            ++launched;
+            LGP_CUDA(cudaMemcpyAsync(ctx->h_state, b.state, sizeof(CgState), cudaMemcpyDeviceToHost, st));
+            LGP_CUDA(cudaStreamSynchronize(st));
+            if (ctx->h_state->done || ctx->h_state->loop_chunks >= ctx->h_state->max_chunks) break;
+        }
+        *bout = b;
+        if (chunks_run) *chunks_run = launched;
+        return LGP_OK;
+    }
 
     // Graph key: everything baked into the captured launches.
     std::vector<unsigned char> key;
@@ -558,6 +589,18 @@ int32_t lgp_matvec_precision(const lgp_ctx *ctx, int32_t t, int32_t prec) {
     (void)ctx;
     if (t < 1 || t > kMaxT) return LGP_ERR_UNSUPPORTED;
     return resolve_prec(t, prec);
+}
+
+int32_t lgp_tc_kernel_choice(const lgp_ctx *ctx, int64_t N, int32_t D, int32_t kind, int32_t t, int32_t prec) {
+    if (!ctx || N < 1 || D < 1 || D > kMaxD || (kind != LGP_RBF && kind != LGP_MATERN52)) return LGP_ERR_INVALID_ARG;
+    if (t < 1 || t > kMaxT) return LGP_ERR_UNSUPPORTED;
+    const int p = resolve_prec(t, prec);
+    if (p < 0) return p;
+    if (!is_tc(p)) return LGP_ERR_UNSUPPORTED;
+    const std::vector<int64_t> key = {pad_rows(N), (int64_t)t, (int64_t)tc_fmt(p), (int64_t)D, (int64_t)kind};
+    auto it = ctx->tc_splits.find(key);
+    if (it == ctx->tc_splits.end()) return LGP_TC_UNTUNED;
+    return it->second == kTcSymmetric ? LGP_TC_SYMMETRIC : LGP_TC_ROW;
 }
 
 void lgp_set_wait_budget(lgp_ctx *ctx, int64_t cycles) {

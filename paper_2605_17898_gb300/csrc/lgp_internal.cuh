@@ -143,7 +143,9 @@ int64_t adjoint_partial_doubles(int64_t N, int t, int D, int num_sms);
 bool tc_supported(int t);
 int64_t tc_vsplit_bytes(int64_t Np, int t);
 // fmt: 0 = bfloat16 halves, 1 = scaled float16 halves
-// forced_splits > 0 overrides the column-split count (the autotuner's choice); 0 = wave-efficiency heuristic.
+// forced_splits > 0 overrides the column-split count (the autotuner's choice); 0 = wave-efficiency heuristic;
+// kTcSymmetric = the symmetric-tile kernel (mv_tcs.cuh), which adds onto out instead of writing partials.
+constexpr int kTcSymmetric = -1;
 cudaError_t launch_mv_tc(const KernelParams &kp, const float *Xs, int64_t N, int64_t Np, const float *V, int64_t ldv,
                          float *out, int64_t ldo, int t, int fmt, void *vsplit, float *partial, int64_t partial_cap,
                          const int *skip, int *err_flag, long long wait_budget, int num_sms, cudaStream_t st,
@@ -151,8 +153,10 @@ cudaError_t launch_mv_tc(const KernelParams &kp, const float *Xs, int64_t N, int
 int64_t mv_tc_partial_floats(int64_t Np, int t, int num_sms);
 int64_t mv_tc_partial_floats(int64_t Np, int t, int num_sms, int forced_splits);
 int mv_tc_launches(int64_t Np, int t, int num_sms, int fmt, int forced_splits = 0);
-// Up to three split counts worth timing, most wave-efficient first.
+// Up to four kernel choices worth timing: kTcSymmetric (when tc_symmetric_ok) and the three most
+// wave-efficient split counts.
 void tc_split_candidates(int64_t Np, int num_sms, int *cand, int *n);
+bool tc_symmetric_ok(int64_t Np);
 
 // solver.cu
 struct CgBuffers {
@@ -169,6 +173,8 @@ void launch_cg_after_matvec(int64_t N, int64_t Np, int t, const CgBuffers &b, cu
 void launch_cg_copy_out(const CgBuffers &b, int64_t N, int t, float *Xsol, int64_t ldx, cudaStream_t st);
 // Body tail of the device-side CG loop: sets the while-node condition to "not done and under the chunk cap".
 void launch_cg_loop_condition(cudaGraphConditionalHandle h, CgState *state, cudaStream_t st);
+// Host-driven loop (LGP_CG_GRAPH=0): counts one chunk in state->loop_chunks.
+void launch_cg_chunk_tally(CgState *state, cudaStream_t st);
 int cg_num_blocks(int64_t N, int t, int num_sms);
 
 // Column dot products sum_i A[i,c] B[i,c] and sum_i A[i,c]^2 (float64), c < t: out[2t].

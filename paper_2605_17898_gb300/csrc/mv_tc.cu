@@ -2,6 +2,7 @@
 #include <algorithm>
 
 #include "mv_tc_inst.cuh"
+#include "mv_tcs_inst.cuh"
 
 namespace lgp {
 
@@ -35,17 +36,20 @@ __device__ __forceinline__ int col_exponent(unsigned int maxbits) {
 // element (j, c') of chunk q = j / 64 sits at q*64*2t + ((j%64)/8 * 2t/8 + c'/8) * 64 + (c'%8) * 8 + j%8;
 // rows j >= N are zero.
 // FMT f16: V is first scaled per column by 2^e_c and col_scale[c] = s^2 2^-15 2^-e_c is written.
+// With out_init set, also out_init[j, c] = noise * V[j, c] for j < N (the symmetric product adds
+// onto it).
 template <int T, int FMT>
 __global__ void split_v_kernel(const float *__restrict__ V, int64_t ldv, int64_t N, int64_t Np,
                                uint16_t *__restrict__ vs,
                                const unsigned int *__restrict__ vmax, float *__restrict__ col_scale, float s2,
-                               const int *skip) {
+                               float *__restrict__ out_init, int64_t ldo, float noise, const int *skip) {
     if (skip && *skip) return;
     const int64_t total = Np * T;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t j = e / T;
         const int c = (int)(e - j * T);
         float v = j < N ? V[j * ldv + c] : 0.0f;
+        if (out_init && j < N) out_init[j * ldo + c] = noise * v;
         uint16_t h, l;
         if (FMT == kFmtBF16) {
             const __nv_bfloat16 hb = __float2bfloat16_rn(v);
@@ -181,15 +185,19 @@ bool tc_supported(int t) { return (t == 16 || t == 32) && encode_fn() != nullptr
 int64_t tc_vsplit_bytes(int64_t Np, int t) { return 2 * Np * t * 2 + 2 * 64 * 4 + 8 * Np * 4; }
 
 int64_t mv_tc_partial_floats(int64_t Np, int t, int num_sms, int forced_splits) {
+    if (forced_splits == kTcSymmetric) return 0;
     const TcGrid g = tc_grid(Np, num_sms, forced_splits);
     return g.S > 1 ? (int64_t)g.S * Np * t : 0;
 }
 
 int64_t mv_tc_partial_floats(int64_t Np, int t, int num_sms) { return mv_tc_partial_floats(Np, t, num_sms, 0); }
 
+bool tc_symmetric_ok(int64_t Np) { return Np / tcs::kTile >= 8; }
+
 void tc_split_candidates(int64_t Np, int num_sms, int *cand, int *n) {
     const int rb = (int)(Np / kBM), total = (int)(Np / kBK);
     *n = 0;
+    if (tc_symmetric_ok(Np)) cand[(*n)++] = kTcSymmetric;
     // the three most wave-efficient split counts, best first
     for (int k = 0; k < 3; ++k) {
         int best_s = 0;
@@ -206,6 +214,7 @@ void tc_split_candidates(int64_t Np, int num_sms, int *cand, int *n) {
         }
         if (best_s == 0) break;
         cand[(*n)++] = grid_for_splits(Np, best_s).S;
+        if (*n == 4) break;
     }
 }
 
@@ -223,6 +232,8 @@ cudaError_t launch_mv_tc(const KernelParams &kp, const float *Xs, int64_t N, int
     float *col_scale = (float *)(vmax + 64);
     float *XsT = col_scale + 64;
     const int blocks = (int)std::min<int64_t>((Np * t + 255) / 256, 8192);
+    const bool symmetric = forced_splits == kTcSymmetric;
+    float *out_init = symmetric ? out : nullptr;
     cudaError_t e;
     if (fmt == kFmtF16) {
         e = cudaMemsetAsync(vmax, 0, 64 * sizeof(unsigned int), st);
@@ -230,23 +241,51 @@ cudaError_t launch_mv_tc(const KernelParams &kp, const float *Xs, int64_t N, int
         const int mb = (int)std::min<int64_t>((N * t + 255) / 256, 1024);
         col_absmax_kernel<<<mb, (256 / t) * t, 0, st>>>(V, ldv, N, t, vmax, skip);
         if (t == 16)
-            split_v_kernel<16, kFmtF16><<<blocks, 256, 0, st>>>(V, ldv, N, Np, vs, vmax, col_scale, kp.s2, skip);
+            split_v_kernel<16, kFmtF16><<<blocks, 256, 0, st>>>(V, ldv, N, Np, vs, vmax, col_scale, kp.s2, out_init,
+                                                              ldo, kp.noise, skip);
         else
-            split_v_kernel<32, kFmtF16><<<blocks, 256, 0, st>>>(V, ldv, N, Np, vs, vmax, col_scale, kp.s2, skip);
+            split_v_kernel<32, kFmtF16><<<blocks, 256, 0, st>>>(V, ldv, N, Np, vs, vmax, col_scale, kp.s2, out_init,
+                                                              ldo, kp.noise, skip);
     } else {
         if (t == 16)
-            split_v_kernel<16, kFmtBF16><<<blocks, 256, 0, st>>>(V, ldv, N, Np, vs, vmax, col_scale, kp.s2, skip);
+            split_v_kernel<16, kFmtBF16><<<blocks, 256, 0, st>>>(V, ldv, N, Np, vs, vmax, col_scale, kp.s2, out_init,
+                                                              ldo, kp.noise, skip);
         else
-            split_v_kernel<32, kFmtBF16><<<blocks, 256, 0, st>>>(V, ldv, N, Np, vs, vmax, col_scale, kp.s2, skip);
+            split_v_kernel<32, kFmtBF16><<<blocks, 256, 0, st>>>(V, ldv, N, Np, vs, vmax, col_scale, kp.s2, out_init,
+                                                              ldo, kp.noise, skip);
     }
     transpose_x_kernel<<<(int)std::min<int64_t>((Np * kp.dpad + 255) / 256, 4096), 256, 0, st>>>(Xs, Np, kp.dpad,
                                                                                               XsT, skip);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
 
+    const CUtensorMapDataType vt = fmt == kFmtF16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    if (symmetric) {
+        CUtensorMap mx, mv;
+        if (!make_map(&mx, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, XsT, (uint64_t)Np, (uint64_t)kp.dpad, 64u,
+                      (uint32_t)kp.dpad) ||
+            !make_map(&mv, vt, 2, vs, 64, (uint64_t)(Np * 2 * t / 64), 64, (uint32_t)(2 * t)))
+            return cudaErrorInvalidValue;
+        tcs::TcsArgs a;
+        a.Xs = Xs;
+        a.out = out;
+        a.skip = skip;
+        a.err = err_flag;
+        a.N = N;
+        a.Np = Np;
+        a.ldo = ldo;
+        a.nb = (int)(Np / tcs::kTile);
+        a.tiles = (int64_t)a.nb * (a.nb + 1) / 2;
+        a.log2s2 = fmt == kFmtF16 ? 15.0f : kp.log2_s2;
+        a.col_scale = fmt == kFmtF16 ? col_scale : nullptr;
+        a.vec4 = ((uintptr_t)out % 16 == 0 && ldo % 4 == 0) ? 1 : 0;
+        a.budget = wait_budget;
+        const dim3 grid((unsigned)std::min<int64_t>(num_sms, a.tiles), 1, 1);
+        return fmt == kFmtF16 ? tcs::dispatch_f16(kp.kind, kp.D, t, grid, mx, mv, a, st)
+                              : tcs::dispatch_bf16(kp.kind, kp.D, t, grid, mx, mv, a, st);
+    }
     const TcGrid g = tc_grid(Np, num_sms, forced_splits);
     if (g.S > 1 && (partial == nullptr || (int64_t)g.S * Np * t > partial_cap)) return cudaErrorInvalidValue;
-    const CUtensorMapDataType vt = fmt == kFmtF16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     CUtensorMap mx, mv;
     if (!make_map(&mx, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, XsT, (uint64_t)Np, (uint64_t)kp.dpad, (uint32_t)kBK,
                   (uint32_t)kp.dpad) ||

@@ -213,6 +213,13 @@ template <int N>
 __device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t (&r)[N]);
 
 template <>
+__device__ __forceinline__ void tmem_ld<8>(uint32_t taddr, uint32_t (&r)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+}
+
+template <>
 __device__ __forceinline__ void tmem_ld<16>(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
@@ -263,21 +270,26 @@ __device__ __forceinline__ void unpack2(uint32_t u, float &a, float &b) {
 // form in lgp_internal.cuh: FFMA2 performs two independent FFMAs).
 template <int KIND> struct Entry2;
 
+// acc0(ls2) is where the squared-distance accumulation starts, k(acc, ls2) turns the accumulated
+// value into the entry. RBF folds the outputscale exponent into the accumulation
+// (acc = rh2 - log2 s^2, k = 2^-acc); Matern-5/2 needs rh = sqrt(rh2) and uses
+// k = e + e * (rh + rh2/3), e = 2^(log2 s^2 - rh log2 e).
 template <> struct Entry2<LGP_RBF> {
-    static __device__ __forceinline__ float2 k(float2 rh2, float2 ls2) {
-        const float2 arg = __ffma2_rn(rh2, make_float2(-1.0f, -1.0f), ls2);
-        return make_float2(ex2_approx(arg.x), ex2_approx(arg.y));
+    static __device__ __forceinline__ float2 acc0(float2 ls2) { return make_float2(-ls2.x, -ls2.y); }
+    static __device__ __forceinline__ float2 k(float2 acc, float2 ls2) {
+        (void)ls2;
+        return make_float2(ex2_approx(-acc.x), ex2_approx(-acc.y));
     }
 };
 
 template <> struct Entry2<LGP_MATERN52> {
+    static __device__ __forceinline__ float2 acc0(float2 ls2) { (void)ls2; return make_float2(0.0f, 0.0f); }
     static __device__ __forceinline__ float2 k(float2 rh2, float2 ls2) {
         const float2 rh = make_float2(sqrt_approx(rh2.x), sqrt_approx(rh2.y));
         const float2 arg = __ffma2_rn(rh, make_float2(-kLog2e, -kLog2e), ls2);
         const float2 e = make_float2(ex2_approx(arg.x), ex2_approx(arg.y));
-        float2 poly = __ffma2_rn(rh2, make_float2(1.0f / 3.0f, 1.0f / 3.0f), rh);
-        poly = __fadd2_rn(poly, make_float2(1.0f, 1.0f));
-        return __fmul2_rn(poly, e);
+        const float2 q = __ffma2_rn(rh2, make_float2(1.0f / 3.0f, 1.0f / 3.0f), rh);
+        return __ffma2_rn(e, q, e);
     }
 };
 
@@ -443,6 +455,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int cgrp = warp >> 2;    // columns 16*cgrp .. 16*cgrp + 15 of every chunk
         const float2 m1 = make_float2(-1.0f, -1.0f);
         const float2 ls2 = make_float2(a.log2s2, a.log2s2);
+        const float2 acc_init = Entry2<KIND>::acc0(ls2);
         // this thread's row of the prescaled x, each coordinate duplicated into both halves of a
         // float2 (row0 + 127 < Np because Np % 256 == 0)
         float2 xi2[D];
@@ -471,7 +484,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                 for (int jp = 0; jp < 2; ++jp) {
                     float2 dd = __ffma2_rn(xj2[0][jp], m1, xi2[0]);
-                    float2 r2 = __fmul2_rn(dd, dd);
+                    float2 r2 = __ffma2_rn(dd, dd, acc_init);
 #pragma unroll
                     for (int d = 1; d < D; ++d) {
                         dd = __ffma2_rn(xj2[d][jp], m1, xi2[d]);
@@ -501,6 +514,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int half = warp >> 3; // rows 64*half .. 64*half + 63
         const float2 m1 = make_float2(-1.0f, -1.0f);
         const float2 ls2 = make_float2(a.log2s2, a.log2s2);
+        const float2 acc_init = Entry2<KIND>::acc0(ls2);
         // this thread's 2 rows of the prescaled x, each coordinate duplicated into both halves
         // of a float2 (row0 + 127 < Np because Np % 256 == 0)
         float2 xi2[2][D];
@@ -532,7 +546,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                     for (int jp = 0; jp < 2; ++jp) {
                         float2 dd = __ffma2_rn(xj2[0][jp], m1, xi2[r][0]);
-                        float2 r2 = __fmul2_rn(dd, dd);
+                        float2 r2 = __ffma2_rn(dd, dd, acc_init);
 #pragma unroll
                         for (int d = 1; d < D; ++d) {
                             dd = __ffma2_rn(xj2[d][jp], m1, xi2[r][d]);

@@ -220,6 +220,9 @@ __global__ void cg_loop_condition_kernel(cudaGraphConditionalHandle h, CgState *
     cudaGraphSetConditional(h, more ? 1u : 0u);
 }
 
+// Host-driven form of the loop tail (no graph): only counts the chunk.
+__global__ void cg_chunk_tally_kernel(CgState *st) { st->loop_chunks += 1; }
+
 __global__ void copy_out_kernel(const float *__restrict__ x, int64_t N, int t, float *__restrict__ out, int64_t ldo) {
     const int64_t total = N * t;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
@@ -417,6 +420,8 @@ void launch_cg_after_matvec(int64_t N, int64_t Np, int t, const CgBuffers &b, cu
 void launch_cg_loop_condition(cudaGraphConditionalHandle h, CgState *state, cudaStream_t st) {
     cg_loop_condition_kernel<<<1, 1, 0, st>>>(h, state);
 }
+
+void launch_cg_chunk_tally(CgState *state, cudaStream_t st) { cg_chunk_tally_kernel<<<1, 1, 0, st>>>(state); }
 
 void launch_cg_copy_out(const CgBuffers &b, int64_t N, int t, float *Xsol, int64_t ldx, cudaStream_t st) {
     copy_out_kernel<<<grid_for(N * t), 256, 0, st>>>(b.x, N, t, Xsol, ldx);

@@ -169,6 +169,8 @@ def test_autograd_function(lgp):
                                   seed=5, tol=1e-6)
     (-2.0 * val).backward()
     _, g, _ = lgp.lgp_lml_and_grad(_dev(p.X), _dev(p.y), p, n_probes=15, lanczos_steps=50, seed=5, tol=1e-6)
-    np.testing.assert_allclose(ll.grad.numpy(), -2.0 * g[:p.D], rtol=1e-6)
-    assert float(lo.grad) == pytest.approx(-2.0 * g[p.D], rel=1e-6)
-    assert float(ln.grad) == pytest.approx(-2.0 * g[p.D + 1], rel=1e-6)
+    # a second call: equal up to the float32 summation order of the symmetric product's atomic
+    # reductions (which moves the CG trajectory in the last bits), far inside the 1e-3 gate
+    np.testing.assert_allclose(ll.grad.numpy(), -2.0 * g[:p.D], rtol=1e-4)
+    assert float(lo.grad) == pytest.approx(-2.0 * g[p.D], rel=1e-4)
+    assert float(ln.grad) == pytest.approx(-2.0 * g[p.D + 1], rel=1e-4)
