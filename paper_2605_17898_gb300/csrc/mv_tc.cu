@@ -1,5 +1,6 @@
 // Host side of the split tensor-core product: V splitting, tensor maps, grid shape, launch.
 #include <algorithm>
+#include <cstring>
 
 #include "mv_tc_inst.cuh"
 #include "mv_tcs_inst.cuh"
@@ -131,6 +132,21 @@ bool make_map(CUtensorMap *m, CUtensorMapDataType dt, int elem_bytes, const void
     cuuint32_t es[2] = {1, 1};
     return fn(m, dt, 2, const_cast<void *>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// 2-D map over a row-strided float32 matrix (rows x cols, row stride in bytes), box of
+// box_cols x box_rows, shared-memory side swizzled as given.
+bool make_map_strided(CUtensorMap *m, const void *base, uint64_t cols, uint64_t rows, uint64_t row_stride_bytes,
+                      uint32_t box_cols, uint32_t box_rows, CUtensorMapSwizzle swz) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {cols, rows};
+    cuuint64_t strides[1] = {row_stride_bytes};
+    cuuint32_t box[2] = {box_cols, box_rows};
+    cuuint32_t es[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(base), dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -278,11 +294,19 @@ cudaError_t launch_mv_tc(const KernelParams &kp, const float *Xs, int64_t N, int
         a.tiles = (int64_t)a.nb * (a.nb + 1) / 2;
         a.log2s2 = fmt == kFmtF16 ? 15.0f : kp.log2_s2;
         a.col_scale = fmt == kFmtF16 ? col_scale : nullptr;
-        a.vec4 = ((uintptr_t)out % 16 == 0 && ldo % 4 == 0) ? 1 : 0;
+        // the drain's blocks go to out by TMA reduce when out's rows are 16-byte aligned
+        CUtensorMap mo;
+        memset(&mo, 0, sizeof mo);
+        const bool aligned = (uintptr_t)out % 16 == 0 && ldo % 4 == 0;
+        a.add_mode = aligned ? tcs::kAddTma : tcs::kAddScalar;
+        if (aligned && !make_map_strided(&mo, out, (uint64_t)t, (uint64_t)N, (uint64_t)ldo * 4, (uint32_t)t,
+                                         (uint32_t)tcs::kTile,
+                                         t == 32 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B))
+            a.add_mode = tcs::kAddVec4;
         a.budget = wait_budget;
         const dim3 grid((unsigned)std::min<int64_t>(num_sms, a.tiles), 1, 1);
-        return fmt == kFmtF16 ? tcs::dispatch_f16(kp.kind, kp.D, t, grid, mx, mv, a, st)
-                              : tcs::dispatch_bf16(kp.kind, kp.D, t, grid, mx, mv, a, st);
+        return fmt == kFmtF16 ? tcs::dispatch_f16(kp.kind, kp.D, t, grid, mx, mv, mo, a, st)
+                              : tcs::dispatch_bf16(kp.kind, kp.D, t, grid, mx, mv, mo, a, st);
     }
     const TcGrid g = tc_grid(Np, num_sms, forced_splits);
     if (g.S > 1 && (partial == nullptr || (int64_t)g.S * Np * t > partial_cap)) return cudaErrorInvalidValue;

@@ -14,9 +14,12 @@
 // contiguous range per CTA (persistent grid of min(SMs, tiles) CTAs, equal tile counts to within
 // one). A CTA's range crosses a few tile rows; within one row, out_I accumulates in the drain
 // warps' registers and is added to HBM when the row ends, while out_J is added after every
-// tile. Both additions are float32 red.global.add operations onto out, which the V-splitting
-// kernel initialised to sigma^2 V; their order across CTAs is not fixed, so the result can
-// differ between runs in the last bits.
+// tile. Both additions are float32 adds onto out, which the V-splitting kernel initialised to
+// sigma^2 V: the drain writes the 128 x t block to a swizzled shared-memory tile and one thread
+// hands it to the TMA unit as a bulk tensor reduce-add (cp.reduce.async.bulk.tensor), so the
+// drain warps release the accumulator after their tensor-memory reads alone. (Outputs whose rows
+// are not 16-byte aligned take per-thread red.global.add instead.) The order of the additions
+// across CTAs is not fixed, so the result can differ between runs in the last bits.
 //
 // CTA structure (one CTA per SM: 22 warps, ~205 KB shared memory, all 512 tensor-memory columns):
 //   warps 0-15  generation: each thread computes 2 rows x 16 columns of the tile (two 8-column
@@ -24,7 +27,7 @@
 //   warp 16     producer: TMA of x_J (transposed, two 64-column boxes) and V_J [hi; lo] per
 //               tile into a 2-stage ring, and of V_I once per tile row into a 2-slot buffer;
 //   warp 17     tensor-memory allocation and the MMA issuer (16 or 32 MMAs per tile);
-//   warps 18-21 drain: tensor memory -> registers -> red.global.add.
+//   warps 18-21 drain: tensor memory -> registers -> staging tile -> TMA reduce-add.
 // Accumulators: two buffers of [out_I (128 columns) | out_J (128 columns)].
 // Waits are bounded and abort the CTA as in mv_tc.cuh.
 #pragma once
@@ -71,7 +74,8 @@ struct TcsLayout {
     static constexpr int kX = kTile * DP * 4;     // x_J, transposed: two [DP][64] boxes
     static constexpr int kStage = 2 * kA + 2 * kB + kX;
     static constexpr int kVi = kStages * kStage;  // V_I slots, 2 x 2 kB
-    static constexpr int kBar = kVi + 2 * 2 * kB;
+    static constexpr int kStaging = kVi + 2 * 2 * kB;  // 128 x t float32 block for the TMA reduce
+    static constexpr int kBar = kStaging + kTile * T * 4;
     static constexpr int kBytes = kBar + 256 + 1024 + 4096;
 };
 
@@ -115,9 +119,49 @@ struct TcsArgs {
     int64_t tiles;           // nb (nb + 1) / 2
     float log2s2;            // exponent offset of the entries: log2 s^2 (bf16) or 15 (f16)
     const float *col_scale;  // [T] multiplier per column (f16 mode), or nullptr
-    int vec4;                // out rows are 16-byte aligned: use the 4-wide reduction
+    int add_mode;            // kAddTma (tm_out is valid), kAddVec4 or kAddScalar
     long long budget;
 };
+
+// How the drain adds its blocks onto out: TMA bulk tensor reduce (out 16-byte aligned with a row
+// stride that is a multiple of 16 bytes), red.global.add.v4.f32 (16-byte aligned rows), or one
+// red.global.add.f32 per element.
+constexpr int kAddTma = 2, kAddVec4 = 1, kAddScalar = 0;
+
+// Byte offset of 16-byte chunk c of row r in the staging tile, in the TMA swizzle pattern of a
+// T-float row (T = 32: 128-byte swizzle, chunk ^= r mod 8; T = 16: 64-byte swizzle, chunk ^=
+// (r / 2) mod 4), which spreads a warp's 32 rows over all banks.
+template <int T>
+__device__ __forceinline__ uint32_t staging_off(int r, int c) {
+    if constexpr (T == 32) return (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4));
+    else return (uint32_t)(r * 64 + ((c ^ ((r >> 1) & 3)) << 4));
+}
+
+__device__ __forceinline__ void tma_reduce_add_2d(const CUtensorMap *map, int c0, int c1, uint32_t src) {
+    asm volatile("cp.reduce.async.bulk.tensor.2d.global.shared::cta.add.tile.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(c0), "r"(c1), "r"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// barrier 1 among the 4 drain warps
+__device__ __forceinline__ void drain_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+// barrier 1 among the 4 drain warps that also returns the AND of `v` over them, so that all four
+// leave their loop together (none is left waiting at a later barrier)
+__device__ __forceinline__ bool drain_all(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 q, %1, 0;\n\t"
+        "bar.red.and.pred p, 1, 128, q;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v)
+        : "memory");
+    return r != 0;
+}
 
 __device__ __forceinline__ void red_add4(float *p, float a, float b, float c, float d) {
     asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
@@ -149,7 +193,7 @@ __device__ __forceinline__ void red_row(float *dst, const float (&s)[NV], const 
 template <int KIND, int D, int T, int FMT>
 __global__ void __launch_bounds__(kThreads, 1)
     mv_tcs_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ CUtensorMap tm_v,
-                  const TcsArgs a) {
+                  const __grid_constant__ CUtensorMap tm_out, const TcsArgs a) {
     constexpr int DP = D <= 4 ? 4 : 8;
     using L = TcsLayout<T, DP>;
     extern __shared__ uint8_t smem_raw[];
@@ -340,7 +384,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             const bool got = mbar_wait(bar_full(s), (it / kStages) & 1, a.budget, abort_flag, a.err, kErrWaitFull);
             if (!__all_sync(0xffffffffu, got)) break;
             uint8_t *st = smem + s * L::kStage;
-#pragma unroll 1
+            // the two 64-column passes: unrolled when D is small (short bodies), kept as a loop for
+            // larger D (measured faster, smaller code)
+            constexpr int kPassUnroll = D <= 4 ? 2 : 1;
+#pragma unroll kPassUnroll
             for (int p = 0; p < 2; ++p) {
                 const int kg = kg0 + 8 * p;
                 const float *xs = reinterpret_cast<const float *>(st + 2 * L::kA + 2 * L::kB + p * (L::kX / 2));
@@ -400,10 +447,29 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else if (warp >= kDrainWarp0) {
         // ------------------------------------------------------------ drain (warps 18-21)
-        const int quarter = warp & 3;  // tensor-memory lanes 32*quarter .. +31
+        const int quarter = warp & 3;       // tensor-memory lanes 32*quarter .. +31
+        const int row = 32 * quarter + lane;  // this thread's row of the 128-row block
+        const bool leader = threadIdx.x == kDrainWarp0 * 32;
+        uint8_t *staging = smem + L::kStaging;
+        const uint32_t staging_u32 = smem_u32(staging);
         float sum_i[T];
 #pragma unroll
         for (int c = 0; c < T; ++c) sum_i[c] = 0.0f;
+        // hands the staged block to the TMA unit (tile rows r0 .. r0 + 127 of out; rows >= N are clipped
+        // by the tensor map, and a block that starts at or after row N holds only padding rows)
+        auto flush_staged = [&](int r0) {
+            fence_async_smem();
+            drain_bar();
+            if (leader && r0 < a.N) {
+                tma_reduce_add_2d(&tm_out, 0, r0, staging_u32);
+                bulk_commit();
+            }
+        };
+        // the staging tile may be rewritten once the previous reduce has read it
+        auto staging_free = [&]() {
+            if (leader) bulk_wait_read_all();
+            drain_bar();
+        };
         for (int it = 0; it < n_it; ++it) {
             const bool diag = w.J == w.I;
             const int I = w.I, J = w.J;
@@ -411,50 +477,76 @@ __global__ void __launch_bounds__(kThreads, 1)
             const bool seg_last = it == n_it - 1 || w.I != I;
             const int buf = it & 1;
             const bool got = mbar_wait(bar_acc_full(buf), (it >> 1) & 1, a.budget, abort_flag, a.err, kErrWaitAcc, 128);
-            if (!__all_sync(0xffffffffu, got)) break;
+            if (!drain_all(got)) break;
             tc_fence_after();
             const uint32_t base = tmem_acc + (uint32_t)(buf * 256) + ((uint32_t)(32 * quarter) << 16);
-            // blocks of each accumulator: K_hi V_hi at +0, K_hi V_lo at +t, K_lo V_hi at +2t
+            // blocks of each accumulator: K_hi V_hi at +0, K_hi V_lo at +t, K_lo V_hi at +2t; 8 columns
+            // of the three blocks per round (three loads, one wait)
 #pragma unroll
-            for (int blk = 0; blk < 3; ++blk) {
+            for (int g = 0; g < T / 8; ++g) {
+                uint32_t v0[8], v1[8], v2[8];
+                tmem_ld<8>(base + (uint32_t)(8 * g), v0);
+                tmem_ld<8>(base + (uint32_t)(T + 8 * g), v1);
+                tmem_ld<8>(base + (uint32_t)(2 * T + 8 * g), v2);
+                tmem_wait_ld();
 #pragma unroll
-                for (int h = 0; h < T / 16; ++h) {
-                    uint32_t v[16];
-                    tmem_ld<16>(base + (uint32_t)(blk * T + 16 * h), v);
-                    tmem_wait_ld();
-#pragma unroll
-                    for (int c = 0; c < 16; ++c) sum_i[16 * h + c] += __uint_as_float(v[c]);
-                }
+                for (int c = 0; c < 8; ++c)
+                    sum_i[8 * g + c] += (__uint_as_float(v0[c]) + __uint_as_float(v1[c])) + __uint_as_float(v2[c]);
             }
-            const int64_t j = (int64_t)J * kTile + 32 * quarter + lane;
+            const bool tma = a.add_mode == kAddTma;
             if (!diag) {
+                if (tma) staging_free();
+                const int64_t j = (int64_t)J * kTile + row;
 #pragma unroll
-                for (int h = 0; h < T / 8; ++h) {
+                for (int g = 0; g < T / 8; ++g) {
+                    uint32_t v0[8], v1[8], v2[8];
+                    tmem_ld<8>(base + 128 + (uint32_t)(8 * g), v0);
+                    tmem_ld<8>(base + 128 + (uint32_t)(T + 8 * g), v1);
+                    tmem_ld<8>(base + 128 + (uint32_t)(2 * T + 8 * g), v2);
+                    tmem_wait_ld();
                     float sj[8];
 #pragma unroll
-                    for (int c = 0; c < 8; ++c) sj[c] = 0.0f;
-#pragma unroll
-                    for (int blk = 0; blk < 3; ++blk) {
-                        uint32_t v[8];
-                        tmem_ld<8>(base + 128 + (uint32_t)(blk * T + 8 * h), v);
-                        tmem_wait_ld();
-#pragma unroll
-                        for (int c = 0; c < 8; ++c) sj[c] += __uint_as_float(v[c]);
+                    for (int c = 0; c < 8; ++c) {
+                        sj[c] = (__uint_as_float(v0[c]) + __uint_as_float(v1[c])) + __uint_as_float(v2[c]);
+                        if (a.col_scale) sj[c] *= a.col_scale[8 * g + c];
                     }
-                    if (j < a.N) red_row<8>(a.out + j * a.ldo + 8 * h, sj, a.col_scale ? a.col_scale + 8 * h : nullptr,
-                                            a.vec4);
+                    if (tma) {
+                        *reinterpret_cast<float4 *>(staging + staging_off<T>(row, 2 * g)) =
+                            make_float4(sj[0], sj[1], sj[2], sj[3]);
+                        *reinterpret_cast<float4 *>(staging + staging_off<T>(row, 2 * g + 1)) =
+                            make_float4(sj[4], sj[5], sj[6], sj[7]);
+                    } else if (j < a.N) {
+                        red_row<8>(a.out + j * a.ldo + 8 * g, sj, nullptr, a.add_mode == kAddVec4);
+                    }
                 }
             }
+            // the accumulator is free once this warp's tensor-memory reads are done
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(bar_acc_empty(buf));
+            if (!diag && tma) flush_staged(J * kTile);
             if (seg_last) {
-                const int64_t i = (int64_t)I * kTile + 32 * quarter + lane;
-                if (i < a.N) red_row<T>(a.out + i * a.ldo, sum_i, a.col_scale, a.vec4);
+                if (a.col_scale) {
+#pragma unroll
+                    for (int c = 0; c < T; ++c) sum_i[c] *= a.col_scale[c];
+                }
+                if (tma) {
+                    staging_free();
+#pragma unroll
+                    for (int c = 0; c < T / 4; ++c)
+                        *reinterpret_cast<float4 *>(staging + staging_off<T>(row, c)) =
+                            make_float4(sum_i[4 * c], sum_i[4 * c + 1], sum_i[4 * c + 2], sum_i[4 * c + 3]);
+                    flush_staged(I * kTile);
+                } else {
+                    const int64_t i = (int64_t)I * kTile + row;
+                    if (i < a.N) red_row<T>(a.out + i * a.ldo, sum_i, nullptr, a.add_mode == kAddVec4);
+                }
 #pragma unroll
                 for (int c = 0; c < T; ++c) sum_i[c] = 0.0f;
             }
         }
+        // every reduce this CTA issued has completed before it exits
+        if (leader) bulk_wait_all();
     }
     tc_fence_before();
     __syncthreads();
