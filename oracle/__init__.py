@@ -41,6 +41,10 @@ def _load():
                                         ctypes.c_double, ctypes.c_double, ctypes.c_int32, ctypes.c_void_p,
                                         ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                         ctypes.c_int32]
+        lib.oracle_kxv_rows.restype = ctypes.c_int
+        lib.oracle_kxv_rows.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
+                                        ctypes.c_int32, ctypes.c_void_p, ctypes.c_double, ctypes.c_int32,
+                                        ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32]
         _lib = lib
     return _lib
 
@@ -68,4 +72,23 @@ def kyv_rows_c(X, V, hyp, rows=None, n_threads: int = 0):
     out = np.empty((nrows, t), dtype=np.float64)
     used = lib.oracle_kyv_rows(X.ctypes.data, N, D, ls.ctypes.data, hyp.s2, hyp.noise, int(hyp.kind),
                                V2.ctypes.data, t, rows_ptr, nrows, out.ctypes.data, int(n_threads))
+    return (out[:, 0] if V.ndim == 1 else out), used
+
+
+def kxv_c(Xr, X, V, hyp, n_threads: int = 0):
+    """K(Xr, X) V in float64 (no noise term) from the C streaming oracle; returns (out, threads used)."""
+    lib = _load()
+    Xr = np.ascontiguousarray(Xr, dtype=np.float32)
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    V = np.ascontiguousarray(V, dtype=np.float32)
+    V2 = np.ascontiguousarray(V[:, None] if V.ndim == 1 else V)
+    N, D = X.shape
+    Nr = Xr.shape[0]
+    t = V2.shape[1]
+    if t > 256 or D > 64 or Xr.shape[1] != D:
+        raise ValueError("oracle_kxv_rows supports t <= 256, D <= 64 and matching dimensions")
+    ls = np.ascontiguousarray(hyp.lengthscale, dtype=np.float64)
+    out = np.empty((Nr, t), dtype=np.float64)
+    used = lib.oracle_kxv_rows(Xr.ctypes.data, Nr, X.ctypes.data, N, D, ls.ctypes.data, hyp.s2, int(hyp.kind),
+                               V2.ctypes.data, t, out.ctypes.data, int(n_threads))
     return (out[:, 0] if V.ndim == 1 else out), used

@@ -27,6 +27,10 @@ Sec. 3 "Kernels" but prints no formula):
 
 * RBF: ``k = s^2 exp(-r^2 / 2)``, ``r^2 = sum_d ((x_d - x'_d) / l_d)^2``.
 * Matern-5/2: ``k = s^2 (1 + sqrt5 r + 5 r^2 / 3) exp(-sqrt5 r)``.
+* Matern-3/2: ``k = s^2 (1 + sqrt3 r) exp(-sqrt3 r)``.
+* Matern-1/2: ``k = s^2 exp(-r)``.
+  (The Matern family of Sec. 3 "Kernels", nu in {1/2, 3/2, 5/2}, in the standard
+  half-integer closed forms of the Bessel definition, Rasmussen & Williams Eq. 4.14-4.17.)
 * Hyperparameters live in log space in the order
   ``(log l_1..log l_D, log s^2, log sigma^2)``; zero prior mean.
 * Probes: ``z[i, c] = +1`` if bit 63 of ``splitmix64(seed XOR (c * 2^32 + i))``
@@ -41,7 +45,11 @@ import numpy as np
 
 RBF = 0
 MATERN52 = 1
+MATERN12 = 2
+MATERN32 = 3
+KINDS = (RBF, MATERN52, MATERN12, MATERN32)
 SQRT5 = math.sqrt(5.0)
+SQRT3 = math.sqrt(3.0)
 
 
 @dataclass
@@ -84,7 +92,28 @@ def phi(kind: int, r2: np.ndarray) -> np.ndarray:
     if kind == MATERN52:
         r = np.sqrt(r2)
         return (1.0 + SQRT5 * r + (5.0 / 3.0) * r2) * np.exp(-SQRT5 * r)
+    if kind == MATERN32:
+        r = np.sqrt(r2)
+        return (1.0 + SQRT3 * r) * np.exp(-SQRT3 * r)
+    if kind == MATERN12:
+        return np.exp(-np.sqrt(r2))
     raise ValueError(f"unknown kernel kind {kind}")
+
+
+def lengthscale_coef(kind: int, r2: np.ndarray) -> np.ndarray:
+    """c(r^2) with d phi / d log l_d = c(r^2) * ((x_d - x'_d) / l_d)^2, i.e. c = -2 d phi / d r^2.
+
+    d r^2 / d log l_d = -2 ((x_d - x'_d) / l_d)^2, so c = -2 dphi/dr^2:
+      RBF exp(-r^2/2); M52 (5/3)(1 + sqrt5 r) exp(-sqrt5 r); M32 3 exp(-sqrt3 r);
+      M12 exp(-r) / r, which is unbounded at r = 0 where every ((x_d - x'_d)/l_d)^2 is 0 and the
+      derivative is 0 (|(x_d - x'_d)/l_d|^2 / r <= r): c is set to 0 there.
+    """
+    r2 = np.asarray(r2, dtype=np.float64)
+    if kind == MATERN12:
+        r = np.sqrt(r2)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            return np.where(r > 0.0, np.exp(-r) / np.where(r > 0.0, r, 1.0), 0.0)
+    return -2.0 * dphi_dr2(kind, r2)
 
 
 def dphi_dr2(kind: int, r2: np.ndarray) -> np.ndarray:
@@ -96,6 +125,13 @@ def dphi_dr2(kind: int, r2: np.ndarray) -> np.ndarray:
         # d phi / d r = -(5/3) r (1 + sqrt5 r) exp(-sqrt5 r);  d r / d r^2 = 1 / (2 r)
         r = np.sqrt(r2)
         return -(5.0 / 6.0) * (1.0 + SQRT5 * r) * np.exp(-SQRT5 * r)
+    if kind == MATERN32:
+        # d phi / d r = -3 r exp(-sqrt3 r)
+        return -1.5 * np.exp(-SQRT3 * np.sqrt(r2))
+    if kind == MATERN12:
+        # d phi / d r = -exp(-r): unbounded in r^2 at r = 0 (see lengthscale_coef)
+        r = np.sqrt(r2)
+        return -np.exp(-r) / (2.0 * r)
     raise ValueError(f"unknown kernel kind {kind}")
 
 
@@ -156,17 +192,18 @@ def matvec_rows(X, V, hyp: Hyper, rows) -> np.ndarray:
 def dK_matrices(X, hyp: Hyper) -> list[np.ndarray]:
     """Explicit dK_y/dtheta_p for theta = (log l_1..log l_D, log s^2, log sigma^2).
 
-    log l_d: s^2 dphi/dr^2 * dr^2/dlog l_d with dr^2/dlog l_d = -2 ((x_d - x'_d)/l_d)^2.
+    log l_d: s^2 dphi/dr^2 * dr^2/dlog l_d with dr^2/dlog l_d = -2 ((x_d - x'_d)/l_d)^2,
+             i.e. s^2 lengthscale_coef(r^2) ((x_d - x'_d)/l_d)^2.
     log s^2: K_ff.   log sigma^2: sigma^2 I.
     """
     X = np.asarray(X, dtype=np.float64)
     ls = hyp.lengthscale
     r2 = scaled_sqdist(X, X, ls)
-    g = hyp.s2 * dphi_dr2(hyp.kind, r2)
+    g = hyp.s2 * lengthscale_coef(hyp.kind, r2)
     mats = []
     for d in range(X.shape[1]):
         rd2 = ((X[:, d][:, None] - X[:, d][None, :]) / ls[d]) ** 2
-        mats.append(g * (-2.0 * rd2))
+        mats.append(g * rd2)
     mats.append(hyp.s2 * phi(hyp.kind, r2))
     mats.append(hyp.noise * np.eye(X.shape[0]))
     return mats

@@ -36,8 +36,10 @@ def _points(N, D, seed=0):
 
 def test_kernel_closed_form_values():
     rows = [l.split() for l in open(os.path.join(GOLDEN, "kernel_values.txt")) if l.strip() and l[0] != "#"]
+    kinds = {"rbf": go.RBF, "m52": go.MATERN52, "m12": go.MATERN12, "m32": go.MATERN32}
+    assert set(n for n, _, _ in rows) == set(kinds)
     for name, r, val in rows:
-        kind = go.RBF if name == "rbf" else go.MATERN52
+        kind = kinds[name]
         got = go.phi(kind, np.array([float(r) ** 2]))[0]
         assert got == pytest.approx(float(val), rel=1e-14, abs=1e-15), (name, r)
 
@@ -54,13 +56,23 @@ def test_rbf_is_gaussian_density_ratio():
         np.testing.assert_allclose(K[i], ref, rtol=1e-12)
 
 
-def test_matern52_is_bessel_form():
-    """Matern nu=5/2 from the modified Bessel function K_nu (Rasmussen & Williams Eq. 4.14)."""
-    nu = 2.5
+@pytest.mark.parametrize("nu,kind", [(2.5, go.MATERN52), (1.5, go.MATERN32), (0.5, go.MATERN12)])
+def test_matern_is_bessel_form(nu, kind):
+    """Matern nu in {1/2, 3/2, 5/2} from the modified Bessel function K_nu (Rasmussen & Williams Eq. 4.14)."""
     r = np.linspace(0.01, 6.0, 200)
     z = math.sqrt(2 * nu) * r
     ref = 2 ** (1 - nu) / sp.gamma(nu) * z ** nu * sp.kv(nu, z)
-    np.testing.assert_allclose(go.phi(go.MATERN52, r * r), ref, rtol=1e-12)
+    np.testing.assert_allclose(go.phi(kind, r * r), ref, rtol=1e-12)
+
+
+@pytest.mark.parametrize("kind", [go.RBF, go.MATERN52, go.MATERN32, go.MATERN12])
+def test_lengthscale_coefficient_is_a_derivative(kind):
+    """d phi / d log l = c(r^2) r^2 for a 1-D problem (so r_d = r): central FD of phi(r^2 e^{-2u})."""
+    r = np.linspace(0.05, 4.0, 60)
+    h = 1e-6
+    fd = (go.phi(kind, (r * math.exp(-h)) ** 2) - go.phi(kind, (r * math.exp(h)) ** 2)) / (2 * h)
+    np.testing.assert_allclose(go.lengthscale_coef(kind, r * r) * r * r, fd, rtol=1e-7, atol=1e-10)
+    assert go.lengthscale_coef(kind, np.array([0.0]))[0] >= 0.0  # finite (0 for M12) at r = 0
 
 
 def test_ard_scaling_and_outputscale():
@@ -74,7 +86,7 @@ def test_ard_scaling_and_outputscale():
     assert K[0, 0] == pytest.approx(3.0, rel=1e-15)
 
 
-@pytest.mark.parametrize("kind", [go.RBF, go.MATERN52])
+@pytest.mark.parametrize("kind", [go.RBF, go.MATERN52, go.MATERN32, go.MATERN12])
 def test_symmetric_and_psd(kind):
     hyp = _hyp(kind, 4, seed=2)
     X = _points(120, 4, seed=2)
@@ -85,7 +97,7 @@ def test_symmetric_and_psd(kind):
 
 # ----------------------------------------------------------------------------- products
 
-@pytest.mark.parametrize("kind", [go.RBF, go.MATERN52])
+@pytest.mark.parametrize("kind", [go.RBF, go.MATERN52, go.MATERN32, go.MATERN12])
 def test_matvec_bruteforce_loop(kind):
     N, D, t = 23, 3, 2
     hyp = _hyp(kind, D, seed=3)
@@ -96,11 +108,15 @@ def test_matvec_bruteforce_loop(kind):
     for i in range(N):
         for j in range(N):
             r2 = sum(((X[i, d] - X[j, d]) / ls[d]) ** 2 for d in range(D))
+            r = math.sqrt(r2)
             if kind == go.RBF:
                 k = hyp.s2 * math.exp(-r2 / 2)
-            else:
-                r = math.sqrt(r2)
+            elif kind == go.MATERN52:
                 k = hyp.s2 * (1 + math.sqrt(5) * r + 5 * r2 / 3) * math.exp(-math.sqrt(5) * r)
+            elif kind == go.MATERN32:
+                k = hyp.s2 * (1 + math.sqrt(3) * r) * math.exp(-math.sqrt(3) * r)
+            else:
+                k = hyp.s2 * math.exp(-r)
             if i == j:
                 k += hyp.noise
             for c in range(t):
@@ -110,7 +126,7 @@ def test_matvec_bruteforce_loop(kind):
     np.testing.assert_allclose(go.matvec_rows(X, V, hyp, rows), ref[rows], rtol=1e-13, atol=1e-13)
 
 
-@pytest.mark.parametrize("kind", [go.RBF, go.MATERN52])
+@pytest.mark.parametrize("kind", [go.RBF, go.MATERN52, go.MATERN32, go.MATERN12])
 def test_c_streaming_oracle_matches_dense(kind):
     N, D, t = 300, 5, 3
     hyp = _hyp(kind, D, seed=4)
@@ -125,8 +141,9 @@ def test_c_streaming_oracle_matches_dense(kind):
     np.testing.assert_allclose(got_r, ref[rows], rtol=1e-12, atol=1e-12)
 
 
-def test_dK_matvec_matches_finite_difference_of_K():
-    hyp = _hyp(go.MATERN52, 2, seed=5)
+@pytest.mark.parametrize("kind", [go.RBF, go.MATERN52, go.MATERN32, go.MATERN12])
+def test_dK_matvec_matches_finite_difference_of_K(kind):
+    hyp = _hyp(kind, 2, seed=5)
     X = _points(30, 2, seed=5)
     W = np.random.default_rng(5).standard_normal((30, 2))
     G = go.dK_matvec(X, W, hyp)
@@ -166,7 +183,7 @@ def test_logdet_three_ways():
     assert a == pytest.approx(c, rel=1e-10)
 
 
-@pytest.mark.parametrize("kind", [go.RBF, go.MATERN52])
+@pytest.mark.parametrize("kind", [go.RBF, go.MATERN52, go.MATERN32, go.MATERN12])
 def test_lml_is_gaussian_logpdf(kind):
     hyp = _hyp(kind, 2, seed=8)
     X = _points(60, 2, seed=8)
@@ -184,7 +201,7 @@ def test_lml_single_point_closed_form():
     assert go.lml(np.array([[0.4]]), y, hyp) == pytest.approx(ref, rel=1e-14)
 
 
-@pytest.mark.parametrize("kind", [go.RBF, go.MATERN52])
+@pytest.mark.parametrize("kind", [go.RBF, go.MATERN52, go.MATERN32, go.MATERN12])
 def test_gradient_matches_central_fd(kind):
     D = 3
     hyp = _hyp(kind, D, seed=9)
@@ -289,3 +306,24 @@ def test_fp64_estimator_hits_probe_conditioned_targets():
     assert est["quad"] == pytest.approx(tg["quad"], rel=1e-8)
     assert est["logdet"] == pytest.approx(tg["logdet"], rel=1e-6)
     np.testing.assert_allclose(est["grad"], tg["grad"], rtol=1e-6, atol=1e-6 * np.abs(tg["grad"]).max())
+
+
+@pytest.mark.parametrize("kind", [go.RBF, go.MATERN52, go.MATERN32, go.MATERN12])
+def test_cross_product_bruteforce_loop(kind):
+    """K(X*, X) V (the predictive-mean product) from the C oracle against a plain double loop."""
+    N, M, D, t = 19, 5, 3, 2
+    hyp = _hyp(kind, D, seed=6)
+    X = _points(N, D, seed=6).astype(np.float32)
+    Xs = _points(M, D, seed=16).astype(np.float32)
+    V = np.random.default_rng(6).standard_normal((N, t)).astype(np.float32)
+    ls = hyp.lengthscale
+    ref = np.zeros((M, t))
+    for i in range(M):
+        for j in range(N):
+            r2 = sum(((float(Xs[i, d]) - float(X[j, d])) / ls[d]) ** 2 for d in range(D))
+            k = hyp.s2 * float(go.phi(kind, np.array([r2]))[0])
+            for c in range(t):
+                ref[i, c] += k * float(V[j, c])
+    got, _ = oracle.kxv_c(Xs, X, V, hyp)
+    np.testing.assert_allclose(got, ref, rtol=1e-13, atol=1e-13)
+    np.testing.assert_allclose(go.cross_kernel(Xs, X, hyp) @ V.astype(np.float64), ref, rtol=1e-13, atol=1e-13)
