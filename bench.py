@@ -196,7 +196,8 @@ def per_pair_ops(kind: int, D: int, split: bool, t: int) -> tuple[float, dict]:
     counted as half an op each); the contraction runs on the tensor pipe. FP32 SIMT
     path: t multiply-adds. MUFU: RBF one ex2; Matern-5/2 one sqrt and one ex2.
     """
-    gen = 2 * D + (0 if kind == 0 else 3)
+    # kernel value beyond the squared distance: RBF 0, M52 3, M12 1 (the exponent), M32 2
+    gen = 2 * D + {0: 0, 1: 3, 2: 1, 3: 2}[kind]
     mufu = {"ex2": 1.0, "sqrt": 0.0 if kind == 0 else 1.0}
     return (gen + 2.0, mufu) if split else (gen + t, mufu)
 

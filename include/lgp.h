@@ -16,11 +16,13 @@
  *     the paper obtains by 2P+1 finite-difference fits (Sec. 5) and this library
  *     obtains analytically in one matrix-free adjoint pass.
  *
- * Kernels (the paper names RBF and Matern-5/2, Sec. 3 "Kernels"; the forms
+ * Kernels (the paper names RBF and Matern-{1/2, 3/2, 5/2}, Sec. 3 "Kernels"; the forms
  * used here are the standard ones, with per-dimension ARD lengthscales l_d):
  *   r^2 = sum_d ((x_d - x'_d) / l_d)^2
  *   LGP_RBF:       k = s^2 exp(-r^2 / 2)
  *   LGP_MATERN52:  k = s^2 (1 + sqrt5 r + 5 r^2 / 3) exp(-sqrt5 r)
+ *   LGP_MATERN32:  k = s^2 (1 + sqrt3 r) exp(-sqrt3 r)
+ *   LGP_MATERN12:  k = s^2 exp(-r)
  *
  * Conventions shared by every entry point:
  *   - All arrays are row-major float32 unless stated. X is [N, D], right-hand
@@ -60,7 +62,7 @@ typedef enum {
     LGP_ERR_WORKSPACE = -7        /* workspace allocation failed */
 } lgp_status;
 
-typedef enum { LGP_RBF = 0, LGP_MATERN52 = 1 } lgp_kernel;
+typedef enum { LGP_RBF = 0, LGP_MATERN52 = 1, LGP_MATERN12 = 2, LGP_MATERN32 = 3 } lgp_kernel;
 
 /* Arithmetic of the K_y V contraction.
  * FP32: entries and products in float32 FMA (any t).

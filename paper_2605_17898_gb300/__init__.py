@@ -33,6 +33,8 @@ LGP_ERR_WORKSPACE = -7
 
 LGP_RBF = 0
 LGP_MATERN52 = 1
+LGP_MATERN12 = 2
+LGP_MATERN32 = 3
 
 LGP_PREC_AUTO = 0
 LGP_PREC_FP32 = 1

@@ -109,12 +109,22 @@ __global__ void __launch_bounds__(kBatchThreads) batch_mv_kernel(BatchArgs a) {
         if (a.gp_done[it.gp]) continue;
         const BatchGp g = a.gps[it.gp];
         const int64_t row0 = (int64_t)it.row_block * kBatchBM;
-        if (g.kind == LGP_RBF) {
-            if (g.dpad == 4) batch_item<LGP_RBF, 4, TT>(g, row0, a.Xs, a.p, a.kp, a.t, xs, vs);
-            else batch_item<LGP_RBF, 8, TT>(g, row0, a.Xs, a.p, a.kp, a.t, xs, vs);
-        } else {
-            if (g.dpad == 4) batch_item<LGP_MATERN52, 4, TT>(g, row0, a.Xs, a.p, a.kp, a.t, xs, vs);
-            else batch_item<LGP_MATERN52, 8, TT>(g, row0, a.Xs, a.p, a.kp, a.t, xs, vs);
+        switch (g.kind) {
+            case LGP_RBF:
+                if (g.dpad == 4) batch_item<LGP_RBF, 4, TT>(g, row0, a.Xs, a.p, a.kp, a.t, xs, vs);
+                else batch_item<LGP_RBF, 8, TT>(g, row0, a.Xs, a.p, a.kp, a.t, xs, vs);
+                break;
+            case LGP_MATERN52:
+                if (g.dpad == 4) batch_item<LGP_MATERN52, 4, TT>(g, row0, a.Xs, a.p, a.kp, a.t, xs, vs);
+                else batch_item<LGP_MATERN52, 8, TT>(g, row0, a.Xs, a.p, a.kp, a.t, xs, vs);
+                break;
+            case LGP_MATERN12:
+                if (g.dpad == 4) batch_item<LGP_MATERN12, 4, TT>(g, row0, a.Xs, a.p, a.kp, a.t, xs, vs);
+                else batch_item<LGP_MATERN12, 8, TT>(g, row0, a.Xs, a.p, a.kp, a.t, xs, vs);
+                break;
+            default:
+                if (g.dpad == 4) batch_item<LGP_MATERN32, 4, TT>(g, row0, a.Xs, a.p, a.kp, a.t, xs, vs);
+                else batch_item<LGP_MATERN32, 8, TT>(g, row0, a.Xs, a.p, a.kp, a.t, xs, vs);
         }
     }
 }

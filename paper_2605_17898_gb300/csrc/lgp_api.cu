@@ -128,7 +128,7 @@ lgp_status check_dev_ptr(lgp_ctx *ctx, const void *p, const char *name) {
 
 lgp_status make_params(lgp_ctx *ctx, const lgp_hyper *h, KernelParams *kp) {
     if (!h) return fail(ctx, LGP_ERR_INVALID_ARG, "hyp is NULL");
-    if (h->kind != LGP_RBF && h->kind != LGP_MATERN52)
+    if (!kind_supported(h->kind))
         return fail(ctx, LGP_ERR_INVALID_ARG, "unknown kernel kind %d", h->kind);
     if (h->D < 1 || h->D > kMaxD) return fail(ctx, LGP_ERR_UNSUPPORTED, "D=%d outside 1..%d", h->D, kMaxD);
     if (!h->log_lengthscale) return fail(ctx, LGP_ERR_INVALID_ARG, "log_lengthscale is NULL");
@@ -138,7 +138,7 @@ lgp_status make_params(lgp_ctx *ctx, const lgp_hyper *h, KernelParams *kp) {
     kp->kind = h->kind;
     kp->D = h->D;
     kp->dpad = dpad_of(h->D);
-    const double c = h->kind == LGP_RBF ? std::sqrt(0.5 / std::log(2.0)) : std::sqrt(5.0);
+    const double c = prescale_of(h->kind);
     for (int d = 0; d < h->D; ++d) {
         const double ll = h->log_lengthscale[d];
         if (!std::isfinite(ll)) return fail(ctx, LGP_ERR_NONFINITE, "non-finite log_lengthscale[%d]", d);
@@ -592,7 +592,7 @@ int32_t lgp_matvec_precision(const lgp_ctx *ctx, int32_t t, int32_t prec) {
 }
 
 int32_t lgp_tc_kernel_choice(const lgp_ctx *ctx, int64_t N, int32_t D, int32_t kind, int32_t t, int32_t prec) {
-    if (!ctx || N < 1 || D < 1 || D > kMaxD || (kind != LGP_RBF && kind != LGP_MATERN52)) return LGP_ERR_INVALID_ARG;
+    if (!ctx || N < 1 || D < 1 || D > kMaxD || !kind_supported(kind)) return LGP_ERR_INVALID_ARG;
     if (t < 1 || t > kMaxT) return LGP_ERR_UNSUPPORTED;
     const int p = resolve_prec(t, prec);
     if (p < 0) return p;

@@ -23,6 +23,7 @@ constexpr int kMaxT = 64;
 constexpr int kMaxLanczos = 64;
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kTwoLn2 = 1.3862943611198906f;
+constexpr float kLn2 = 0.6931471805599453f;
 
 // Padded row width of the prescaled X buffer (floats): 4 for D <= 4, else 8.
 inline int dpad_of(int D) { return D <= 4 ? 4 : 8; }
@@ -78,6 +79,49 @@ template <> struct Entry<LGP_MATERN52> {
         psi = (1.0f + rh) * e * (1.0f / 3.0f);
     }
 };
+
+// Matern-1/2 on x = log2(e) x / l: rh = r log2 e, k = 2^(log2 s^2 - rh). dk/dlog l_d = s^2 e^-r r_d^2 / r
+// = k ln2 dxh_d^2 / rh for r > 0, and 0 at r = 0 (where every dxh_d is 0).
+template <> struct Entry<LGP_MATERN12> {
+    static __device__ __forceinline__ float k(float rh2, float log2s2) { return ex2_approx(log2s2 - sqrt_approx(rh2)); }
+    static __device__ __forceinline__ void k_psi(float rh2, float log2s2, float &k, float &psi) {
+        k = ex2_approx(log2s2 - sqrt_approx(rh2));
+        psi = rh2 > 0.0f ? k * kLn2 * rsqrtf(rh2) : 0.0f;
+    }
+};
+
+// Matern-3/2 on x = sqrt3 x / l: rh = sqrt3 r, k = (1 + rh) e with e = 2^(log2 s^2 - rh log2 e);
+// dk/dlog l_d = 3 s^2 e^(-sqrt3 r) r_d^2 = e dxh_d^2.
+template <> struct Entry<LGP_MATERN32> {
+    static __device__ __forceinline__ float k(float rh2, float log2s2) {
+        const float rh = sqrt_approx(rh2);
+        const float e = ex2_approx(fmaf(-rh, kLog2e, log2s2));
+        return fmaf(e, rh, e);
+    }
+    static __device__ __forceinline__ void k_psi(float rh2, float log2s2, float &k, float &psi) {
+        const float rh = sqrt_approx(rh2);
+        const float e = ex2_approx(fmaf(-rh, kLog2e, log2s2));
+        k = fmaf(e, rh, e);
+        psi = e;
+    }
+};
+
+// Host: the kind is one the library implements.
+inline bool kind_supported(int kind) {
+    return kind == LGP_RBF || kind == LGP_MATERN52 || kind == LGP_MATERN12 || kind == LGP_MATERN32;
+}
+
+// Host: the factor c of the prescaled coordinates x = c x / l, chosen so that each entry needs one
+// ex2: RBF sqrt(log2(e) / 2) (rh^2 = r^2 log2(e) / 2), M52 sqrt5, M32 sqrt3, M12 log2(e).
+inline double prescale_of(int kind) {
+    switch (kind) {
+        case LGP_RBF: return 0.8493218002880191;     // sqrt(0.5 / ln 2)
+        case LGP_MATERN52: return 2.23606797749979;  // sqrt 5
+        case LGP_MATERN32: return 1.7320508075688772;  // sqrt 3
+        case LGP_MATERN12: return 1.4426950408889634;  // log2 e
+    }
+    return 0.0;
+}
 
 // ---------------------------------------------------------------- CG state on the device
 

@@ -111,8 +111,14 @@ cudaError_t launch_mv_simt(const MvLaunch &m, cudaStream_t st) {
     a.log2s2 = m.kp->log2_s2;
     a.noise = m.kp->noise;
     const dim3 grid((unsigned)rb, (unsigned)S, (unsigned)cg);
-    cudaError_t e = m.kp->kind == LGP_RBF ? mv_simt_dispatch_rbf(m.kp->D, sh.TT, sh.R, grid, a, st)
-                                          : mv_simt_dispatch_m52(m.kp->D, sh.TT, sh.R, grid, a, st);
+    cudaError_t e;
+    switch (m.kp->kind) {
+        case LGP_RBF: e = mv_simt_dispatch_rbf(m.kp->D, sh.TT, sh.R, grid, a, st); break;
+        case LGP_MATERN52: e = mv_simt_dispatch_m52(m.kp->D, sh.TT, sh.R, grid, a, st); break;
+        case LGP_MATERN12: e = mv_simt_dispatch_m12(m.kp->D, sh.TT, sh.R, grid, a, st); break;
+        case LGP_MATERN32: e = mv_simt_dispatch_m32(m.kp->D, sh.TT, sh.R, grid, a, st); break;
+        default: e = cudaErrorInvalidValue;
+    }
     if (e != cudaSuccess || S == 1) return e;
     reduce_split_kernel<<<grid_for(m.N * m.t), 256, 0, st>>>(m.partial, (int)S, m.Np, m.N, m.t, m.V, m.ldv, m.out,
                                                              m.ldo, m.kp->noise, m.skip);
@@ -152,8 +158,14 @@ cudaError_t launch_mv_grad(const KernelParams &kp, const float *Xs, int64_t N, i
     a.log2s2 = kp.log2_s2;
     a.noise = kp.noise;
     const dim3 grid((unsigned)rb, (unsigned)S, (unsigned)cg);
-    cudaError_t e = kp.kind == LGP_RBF ? mv_grad_dispatch_rbf(kp.D, TT, grid, a, st)
-                                       : mv_grad_dispatch_m52(kp.D, TT, grid, a, st);
+    cudaError_t e;
+    switch (kp.kind) {
+        case LGP_RBF: e = mv_grad_dispatch_rbf(kp.D, TT, grid, a, st); break;
+        case LGP_MATERN52: e = mv_grad_dispatch_m52(kp.D, TT, grid, a, st); break;
+        case LGP_MATERN12: e = mv_grad_dispatch_m12(kp.D, TT, grid, a, st); break;
+        case LGP_MATERN32: e = mv_grad_dispatch_m32(kp.D, TT, grid, a, st); break;
+        default: e = cudaErrorInvalidValue;
+    }
     if (e != cudaSuccess || S == 1) return e;
     reduce_grad_kernel<<<grid_for((int64_t)(NB + 1) * N * t), 256, 0, st>>>(partial, (int)S, NB, Np, N, t, W,
                                                                            kp.noise, G);
@@ -193,7 +205,13 @@ cudaError_t launch_adjoint_bilinear(const KernelParams &kp, const float *Xs, int
     *n_blocks = (int)(rb * S);
     const dim3 grid((unsigned)rb, (unsigned)S, 1);
     const int TT = adjoint_tt(t);
-    return kp.kind == LGP_RBF ? adjoint_dispatch_rbf(kp.D, TT, grid, a, st) : adjoint_dispatch_m52(kp.D, TT, grid, a, st);
+    switch (kp.kind) {
+        case LGP_RBF: return adjoint_dispatch_rbf(kp.D, TT, grid, a, st);
+        case LGP_MATERN52: return adjoint_dispatch_m52(kp.D, TT, grid, a, st);
+        case LGP_MATERN12: return adjoint_dispatch_m12(kp.D, TT, grid, a, st);
+        case LGP_MATERN32: return adjoint_dispatch_m32(kp.D, TT, grid, a, st);
+    }
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace lgp

@@ -382,6 +382,12 @@ cudaError_t mv_grad_dispatch_rbf(int D, int TT, dim3 grid, const GradArgs &a, cu
 cudaError_t mv_grad_dispatch_m52(int D, int TT, dim3 grid, const GradArgs &a, cudaStream_t st);
 cudaError_t adjoint_dispatch_rbf(int D, int TT, dim3 grid, const AdjArgs &a, cudaStream_t st);
 cudaError_t adjoint_dispatch_m52(int D, int TT, dim3 grid, const AdjArgs &a, cudaStream_t st);
+cudaError_t mv_simt_dispatch_m12(int D, int TT, int R, dim3 grid, const SimtArgs &a, cudaStream_t st);
+cudaError_t mv_grad_dispatch_m12(int D, int TT, dim3 grid, const GradArgs &a, cudaStream_t st);
+cudaError_t adjoint_dispatch_m12(int D, int TT, dim3 grid, const AdjArgs &a, cudaStream_t st);
+cudaError_t mv_simt_dispatch_m32(int D, int TT, int R, dim3 grid, const SimtArgs &a, cudaStream_t st);
+cudaError_t mv_grad_dispatch_m32(int D, int TT, dim3 grid, const GradArgs &a, cudaStream_t st);
+cudaError_t adjoint_dispatch_m32(int D, int TT, dim3 grid, const AdjArgs &a, cudaStream_t st);
 
 }  // namespace lgp
 

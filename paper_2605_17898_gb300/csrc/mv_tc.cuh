@@ -293,6 +293,27 @@ template <> struct Entry2<LGP_MATERN52> {
     }
 };
 
+// Matern-1/2 on x = log2(e) x / l: k = 2^(log2 s^2 - rh).
+template <> struct Entry2<LGP_MATERN12> {
+    static __device__ __forceinline__ float2 acc0(float2 ls2) { (void)ls2; return make_float2(0.0f, 0.0f); }
+    static __device__ __forceinline__ float2 k(float2 rh2, float2 ls2) {
+        const float2 rh = make_float2(sqrt_approx(rh2.x), sqrt_approx(rh2.y));
+        const float2 arg = __ffma2_rn(rh, make_float2(-1.0f, -1.0f), ls2);
+        return make_float2(ex2_approx(arg.x), ex2_approx(arg.y));
+    }
+};
+
+// Matern-3/2 on x = sqrt3 x / l: k = e + e rh, e = 2^(log2 s^2 - rh log2 e).
+template <> struct Entry2<LGP_MATERN32> {
+    static __device__ __forceinline__ float2 acc0(float2 ls2) { (void)ls2; return make_float2(0.0f, 0.0f); }
+    static __device__ __forceinline__ float2 k(float2 rh2, float2 ls2) {
+        const float2 rh = make_float2(sqrt_approx(rh2.x), sqrt_approx(rh2.y));
+        const float2 arg = __ffma2_rn(rh, make_float2(-kLog2e, -kLog2e), ls2);
+        const float2 e = make_float2(ex2_approx(arg.x), ex2_approx(arg.y));
+        return __ffma2_rn(e, rh, e);
+    }
+};
+
 struct TcArgs {
     const float *Xs;     // prescaled x [Np, DP] (row-major; each generation thread reads its own rows)
     const float *V;      // user V [N, ldv] (for the sigma^2 V term)

@@ -38,20 +38,47 @@ cudaError_t dispatch_d(int D, dim3 grid, const CUtensorMap &mx, const CUtensorMa
     return cudaErrorInvalidValue;
 }
 
+// One (format, kind) pair: every D and T. Instantiated in its own translation unit
+// (mv_tc_<fmt>_<kind>.cu) so that the instantiations compile in parallel.
+template <int FMT, int KIND>
+cudaError_t dispatch_kind(int D, int T, dim3 grid, const CUtensorMap &mx, const CUtensorMap &mv, const TcArgs &a,
+                          cudaStream_t st) {
+    return T == 16 ? dispatch_d<KIND, 16, FMT>(D, grid, mx, mv, a, st) : dispatch_d<KIND, 32, FMT>(D, grid, mx, mv, a, st);
+}
+
+#define LGP_TC_KIND_DECL(FMT, KIND)                                                                               \
+    extern template cudaError_t dispatch_kind<FMT, KIND>(int, int, dim3, const CUtensorMap &, const CUtensorMap &, \
+                                                         const TcArgs &, cudaStream_t);
+LGP_TC_KIND_DECL(kFmtBF16, LGP_RBF)
+LGP_TC_KIND_DECL(kFmtBF16, LGP_MATERN52)
+LGP_TC_KIND_DECL(kFmtBF16, LGP_MATERN12)
+LGP_TC_KIND_DECL(kFmtBF16, LGP_MATERN32)
+LGP_TC_KIND_DECL(kFmtF16, LGP_RBF)
+LGP_TC_KIND_DECL(kFmtF16, LGP_MATERN52)
+LGP_TC_KIND_DECL(kFmtF16, LGP_MATERN12)
+LGP_TC_KIND_DECL(kFmtF16, LGP_MATERN32)
+#undef LGP_TC_KIND_DECL
+
 template <int FMT>
 cudaError_t dispatch_fmt(int kind, int D, int T, dim3 grid, const CUtensorMap &mx, const CUtensorMap &mv,
                          const TcArgs &a, cudaStream_t st) {
-    if (kind == LGP_RBF)
-        return T == 16 ? dispatch_d<LGP_RBF, 16, FMT>(D, grid, mx, mv, a, st)
-                       : dispatch_d<LGP_RBF, 32, FMT>(D, grid, mx, mv, a, st);
-    return T == 16 ? dispatch_d<LGP_MATERN52, 16, FMT>(D, grid, mx, mv, a, st)
-                   : dispatch_d<LGP_MATERN52, 32, FMT>(D, grid, mx, mv, a, st);
+    switch (kind) {
+        case LGP_RBF: return dispatch_kind<FMT, LGP_RBF>(D, T, grid, mx, mv, a, st);
+        case LGP_MATERN52: return dispatch_kind<FMT, LGP_MATERN52>(D, T, grid, mx, mv, a, st);
+        case LGP_MATERN12: return dispatch_kind<FMT, LGP_MATERN12>(D, T, grid, mx, mv, a, st);
+        case LGP_MATERN32: return dispatch_kind<FMT, LGP_MATERN32>(D, T, grid, mx, mv, a, st);
+    }
+    return cudaErrorInvalidValue;
 }
 
-cudaError_t dispatch_bf16(int kind, int D, int T, dim3 grid, const CUtensorMap &mx, const CUtensorMap &mv,
-                          const TcArgs &a, cudaStream_t st);
-cudaError_t dispatch_f16(int kind, int D, int T, dim3 grid, const CUtensorMap &mx, const CUtensorMap &mv,
-                         const TcArgs &a, cudaStream_t st);
+inline cudaError_t dispatch_bf16(int kind, int D, int T, dim3 grid, const CUtensorMap &mx, const CUtensorMap &mv,
+                                 const TcArgs &a, cudaStream_t st) {
+    return dispatch_fmt<kFmtBF16>(kind, D, T, grid, mx, mv, a, st);
+}
+inline cudaError_t dispatch_f16(int kind, int D, int T, dim3 grid, const CUtensorMap &mx, const CUtensorMap &mv,
+                                const TcArgs &a, cudaStream_t st) {
+    return dispatch_fmt<kFmtF16>(kind, D, T, grid, mx, mv, a, st);
+}
 
 }  // namespace tc
 }  // namespace lgp

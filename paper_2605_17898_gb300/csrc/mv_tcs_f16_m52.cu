@@ -1,0 +1,9 @@
+// Symmetric-tile tensor-core product: Matern-5/2 kernel, scaled float16 halves.
+#include "mv_tcs_inst.cuh"
+
+namespace lgp {
+namespace tcs {
+template cudaError_t dispatch_kind<kFmtF16, LGP_MATERN52>(int, int, dim3, const CUtensorMap &, const CUtensorMap &,
+                                               const CUtensorMap &, const TcsArgs &, cudaStream_t);
+}  // namespace tcs
+}  // namespace lgp

@@ -85,7 +85,7 @@ extern "C" lgp_status lgp_kernel_matvec_noalloc(const lgp_hyper *hyp, const floa
     if (N > kNoallocMaxN || !(t == 16 || t == 32)) return LGP_ERR_UNSUPPORTED;
     if (!(prec == LGP_PREC_AUTO || prec == LGP_PREC_SPLIT_F16 || prec == LGP_PREC_SPLIT_BF16))
         return LGP_ERR_UNSUPPORTED;
-    if (hyp->kind != LGP_RBF && hyp->kind != LGP_MATERN52) return LGP_ERR_INVALID_ARG;
+    if (!kind_supported(hyp->kind)) return LGP_ERR_INVALID_ARG;
     if (hyp->D < 1 || hyp->D > kMaxD) return LGP_ERR_UNSUPPORTED;
     if (!hyp->log_lengthscale || !std::isfinite(hyp->log_outputscale) || !std::isfinite(hyp->log_noise))
         return LGP_ERR_INVALID_ARG;
@@ -97,7 +97,7 @@ extern "C" lgp_status lgp_kernel_matvec_noalloc(const lgp_hyper *hyp, const floa
     kp.kind = hyp->kind;
     kp.D = hyp->D;
     kp.dpad = dpad_of(hyp->D);
-    const double c = hyp->kind == LGP_RBF ? std::sqrt(0.5 / std::log(2.0)) : std::sqrt(5.0);
+    const double c = prescale_of(hyp->kind);
     for (int d = 0; d < hyp->D; ++d) {
         const double ll = hyp->log_lengthscale[d];
         if (!std::isfinite(ll)) return LGP_ERR_INVALID_ARG;

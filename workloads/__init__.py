@@ -37,6 +37,9 @@ import numpy as np
 
 RBF = 0
 MATERN52 = 1
+MATERN12 = 2
+MATERN32 = 3
+KINDS = (RBF, MATERN52, MATERN12, MATERN32)
 
 
 @dataclass
@@ -45,7 +48,7 @@ class Problem:
 
     X: np.ndarray                    # [N, D] float32
     y: np.ndarray                    # [N] float32
-    kind: int                        # RBF or MATERN52
+    kind: int                        # RBF, MATERN52, MATERN12 or MATERN32
     log_lengthscale: np.ndarray      # [D] float32
     log_outputscale: float           # log s^2
     log_noise: float                 # log sigma^2
