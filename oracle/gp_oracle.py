@@ -433,3 +433,56 @@ def estimator_fp64(X, y, hyp: Hyper, n_probes: int, lanczos_steps: int, seed: in
                      for M in dK_matrices(X64, hyp)])
     return {"logdet": ld, "quad": quad, "lml": -0.5 * (quad + ld + N * math.log(2 * math.pi)),
             "grad": grad, "iters": res.iters, "Z": Z, "cg": res}
+
+
+# --------------------------------------------------------------------------- posterior prediction
+
+def predict_exact(X, y, Xs, hyp: Hyper) -> tuple[np.ndarray, np.ndarray]:
+    """Posterior predictive mean and latent variance at test points Xs (Sec. 2):
+    mu_* = K_*f K_y^{-1} y,  var_* = diag(K_** - K_*f K_y^{-1} K_f*), by a Cholesky solve."""
+    Ky = noisy_kernel_matrix(X, hyp)
+    Ksf = cross_kernel(Xs, X, hyp)
+    mean = Ksf @ cholesky_solve(Ky, np.asarray(y, dtype=np.float64))
+    W = cholesky_solve(Ky, Ksf.T)
+    kss = hyp.s2 * phi(hyp.kind, np.zeros(np.asarray(Xs).shape[0]))
+    var = kss - np.sum(Ksf.T * W, axis=0)
+    return mean, var
+
+
+def predict_var_hutchinson_target(X, Xs, hyp: Hyper, Z: np.ndarray) -> np.ndarray:
+    """What the probe estimate of the predictive variance converges to for given probes Z [M, m]
+    (exact solves): var_i = k_ii - mean_c Z[i, c] (A Z)[i, c], A = K_*f K_y^{-1} K_f*
+    (the diagonal estimator diag(A) ~ mean_c z_c * (A z_c); Bekas, Kokiopoulou & Saad 2007)."""
+    Ky = noisy_kernel_matrix(X, hyp)
+    Ksf = cross_kernel(Xs, X, hyp)
+    AZ = Ksf @ cholesky_solve(Ky, Ksf.T @ np.asarray(Z, dtype=np.float64))
+    kss = hyp.s2 * phi(hyp.kind, np.zeros(np.asarray(Xs).shape[0]))
+    return kss - np.mean(np.asarray(Z, dtype=np.float64) * AZ, axis=1)
+
+
+def predict_fp64(X, y, Xs, hyp: Hyper, n_probes: int, seed: int, tol: float = 1e-6,
+                 max_iter: int | None = None) -> dict:
+    """The CG prediction route in float64, step by step.
+
+    One batched CG solve on [y, K_f* z_1 .. K_f* z_m] (textbook CG, as for the LML) gives
+    a = K_y^{-1} y and w_c = K_y^{-1} K_f* z_c; then mu_* = K_*f a and
+    var_i = k_ii - mean_c z_c[i] (K_*f w_c)[i], with probes z_c = rademacher(seed, M, m).
+    n_probes = 0: exact variance, with columns K_f* e_j for every test point j instead of probes.
+    """
+    X64 = np.asarray(X, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    N = y.shape[0]
+    M = np.asarray(Xs).shape[0]
+    Ky = noisy_kernel_matrix(X64, hyp)
+    Ksf = cross_kernel(Xs, X64, hyp)
+    Z = rademacher(seed, M, n_probes) if n_probes > 0 else np.eye(M)
+    rhs = np.concatenate([y[:, None], Ksf.T @ Z], axis=1)
+    res = cg(lambda P: Ky @ P, rhs, tol, max_iter or 10 * N)
+    mean = Ksf @ res.x[:, 0]
+    kss = hyp.s2 * phi(hyp.kind, np.zeros(M))
+    Q = Ksf @ res.x[:, 1:]
+    if n_probes > 0:
+        var = kss - np.mean(Z * Q, axis=1)
+    else:
+        var = kss - np.diag(Q)
+    return {"mean": mean, "var": var, "Z": Z, "iters": res.iters, "rel_resid": res.rel_resid}

@@ -327,3 +327,68 @@ def test_cross_product_bruteforce_loop(kind):
     got, _ = oracle.kxv_c(Xs, X, V, hyp)
     np.testing.assert_allclose(got, ref, rtol=1e-13, atol=1e-13)
     np.testing.assert_allclose(go.cross_kernel(Xs, X, hyp) @ V.astype(np.float64), ref, rtol=1e-13, atol=1e-13)
+
+
+# ----------------------------------------------------------------------------- posterior prediction
+
+@pytest.mark.parametrize("kind", [go.RBF, go.MATERN52, go.MATERN32, go.MATERN12])
+def test_prediction_is_gaussian_conditioning_via_joint_precision(kind):
+    """mu_* and var_* against Gaussian conditioning computed another way: from the precision
+    matrix P of the joint covariance [[K_y, K_f*], [K_*f, K_**]], Cov(* | y) = inv(P_**) and
+    E[* | y] = -inv(P_**) P_*f y (Schur-complement identities)."""
+    N, M, D = 40, 9, 2
+    hyp = _hyp(kind, D, seed=21)
+    X = _points(N, D, seed=21)
+    Xs = _points(M, D, seed=22)
+    y = np.random.default_rng(21).standard_normal(N)
+    A = np.vstack([X, Xs])
+    C = go.kernel_matrix(A, hyp)
+    C[:N, :N] += hyp.noise * np.eye(N)
+    P = np.linalg.inv(C)
+    cov = np.linalg.inv(P[N:, N:])
+    mean_ref = -cov @ P[N:, :N] @ y
+    mean, var = go.predict_exact(X, y, Xs, hyp)
+    np.testing.assert_allclose(mean, mean_ref, rtol=1e-8, atol=1e-10)
+    np.testing.assert_allclose(var, np.diag(cov), rtol=1e-7, atol=1e-10)
+
+
+def test_prediction_limits():
+    """Far from the data the posterior is the prior (mean 0, variance s^2); at a training input with
+    vanishing noise the mean interpolates y and the latent variance vanishes (Matern-1/2, so that K
+    stays well conditioned at sigma^2 = 1e-9)."""
+    hyp = _hyp(go.MATERN12, 2, seed=23, los=0.4, ln=math.log(1e-9))
+    X = _points(12, 2, seed=23)
+    y = np.random.default_rng(23).standard_normal(12)
+    far = np.array([[1e3, 1e3]])
+    mean, var = go.predict_exact(X, y, far, hyp)
+    assert abs(mean[0]) < 1e-12
+    assert var[0] == pytest.approx(math.exp(0.4), rel=1e-12)
+    mean, var = go.predict_exact(X, y, X[:3], hyp)
+    np.testing.assert_allclose(mean, y[:3], rtol=0, atol=1e-5)
+    assert np.all(np.abs(var) < 1e-5)
+
+
+def test_hadamard_probes_make_variance_estimate_exact():
+    """With all M Hadamard columns as probes, the diagonal estimator is exact (Z Z^T = M I)."""
+    M = 16
+    hyp = _hyp(go.MATERN32, 3, seed=24)
+    X = _points(50, 3, seed=24)
+    Xs = _points(M, 3, seed=25)
+    H = sla.hadamard(M).astype(np.float64)
+    _, var = go.predict_exact(X, np.zeros(50), Xs, hyp)
+    np.testing.assert_allclose(go.predict_var_hutchinson_target(X, Xs, hyp, H), var, rtol=1e-10, atol=1e-12)
+
+
+def test_prediction_cg_route_reaches_the_exact_values():
+    """The float64 CG route (exact-variance mode, and probe mode against its probe target)."""
+    hyp = _hyp(go.MATERN52, 3, seed=26)
+    X = _points(200, 3, seed=26)
+    Xs = _points(21, 3, seed=27)
+    y = np.random.default_rng(26).standard_normal(200)
+    mean, var = go.predict_exact(X, y, Xs, hyp)
+    ex = go.predict_fp64(X, y, Xs, hyp, n_probes=0, seed=0, tol=1e-12)
+    np.testing.assert_allclose(ex["mean"], mean, rtol=1e-8, atol=1e-10)
+    np.testing.assert_allclose(ex["var"], var, rtol=1e-8, atol=1e-10)
+    pr = go.predict_fp64(X, y, Xs, hyp, n_probes=8, seed=5, tol=1e-12)
+    np.testing.assert_allclose(pr["var"], go.predict_var_hutchinson_target(X, Xs, hyp, pr["Z"]), rtol=1e-8,
+                               atol=1e-10)
