@@ -111,6 +111,14 @@ typedef struct {
     int32_t cg_chunks;       /* CUDA-graph replays of the CG iteration chunk */
 } lgp_lml_info;
 
+typedef struct {
+    int32_t solves;          /* batched CG solves run */
+    int32_t iters_max;       /* most CG iterations over all solved columns */
+    double max_rel_resid;    /* largest final recursive ||r||/||b|| over all solved columns */
+    int32_t var_probes;      /* probes of the variance estimate (0: exact per-point variance) */
+    int32_t prec_used;       /* lgp_precision of the products inside the first solve */
+} lgp_predict_info;
+
 typedef struct lgp_ctx lgp_ctx;
 typedef void *lgp_stream;    /* a cudaStream_t */
 
@@ -220,6 +228,29 @@ lgp_status lgp_cg_solve(lgp_ctx *ctx, const lgp_hyper *hyp, const float *X, cons
 lgp_status lgp_lml_and_grad(lgp_ctx *ctx, const lgp_hyper *hyp, const float *X, const float *y, int64_t N,
                             const lgp_options *opt, double *lml, double *grad, lgp_lml_info *info,
                             lgp_stream stream);
+
+/*
+ * Posterior prediction at M test points X* (Sec. 2):
+ *   mean[j] = (K_*f K_y^{-1} y)_j,
+ *   var[j]  = (K_** - K_*f K_y^{-1} K_f*)_jj   (latent f, no noise added),
+ * with K_y^{-1} applied by batched CG (tol and max_iter from opt; the products use
+ * opt->prec where the column count allows it).
+ *   opt->n_probes = 0: exact variance. The right-hand sides [y, k(X, x*_1), ...]
+ *     are solved in blocks of up to 32 columns; var[j] = s^2 - k_j . K_y^{-1} k_j.
+ *   opt->n_probes = m in 1..31: the probe estimate of the diagonal (the CG
+ *     "Hutchinson" route whose CPU/GPU agreement Sec. 4 reports as 3e-3): one
+ *     solve of [y, K_f* z_1 .. K_f* z_m] with Rademacher z_c over the test points
+ *     (the lgp_rademacher_probes stream with opt->seed, N replaced by M), then
+ *     var[j] = s^2 - mean_c z_c[j] (K_*f K_y^{-1} K_f* z_c)[j].
+ * X [N, D], y [N], Xs [M, D], mean [M] and var [M] are device arrays; var may be
+ * NULL (mean only: one single-column solve). info (HOST) may be NULL. The cross
+ * products K_*f v and K_f* Z run on the FP32 path. Errors as lgp_cg_solve (NaN or
+ * Inf in X or Xs gives LGP_ERR_NONFINITE); LGP_WARN_NOT_CONVERGED if a column hit
+ * max_iter. Synchronises `stream`.
+ */
+lgp_status lgp_predict(lgp_ctx *ctx, const lgp_hyper *hyp, const float *X, const float *y, int64_t N,
+                       const float *Xs, int64_t M, const lgp_options *opt, float *mean, float *var,
+                       lgp_predict_info *info, lgp_stream stream);
 
 /*
  * The probes lgp_lml_and_grad draws: Z[i, c] = +1 if bit 63 of

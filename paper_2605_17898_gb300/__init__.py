@@ -49,7 +49,7 @@ EXPORTED = [
     "lgp_workspace_bytes", "lgp_matvec_precision", "lgp_set_wait_budget", "lgp_check_device_status",
     "lgp_kernel_matvec", "lgp_kernel_matvec_grad", "lgp_cg_solve", "lgp_lml_and_grad",
     "lgp_rademacher_probes", "lgp_batch_cg_solve", "lgp_kernel_matvec_noalloc",
-    "lgp_measure_pipe_peak", "lgp_tc_kernel_choice",
+    "lgp_measure_pipe_peak", "lgp_tc_kernel_choice", "lgp_predict",
 ]
 
 
@@ -68,6 +68,11 @@ class lgp_lml_info(ctypes.Structure):
                 ("max_rel_resid", ctypes.c_double), ("iters_max", ctypes.c_int32), ("iters_min", ctypes.c_int32),
                 ("t", ctypes.c_int32), ("prec_used", ctypes.c_int32), ("launches", ctypes.c_int32),
                 ("cg_chunks", ctypes.c_int32)]
+
+
+class lgp_predict_info(ctypes.Structure):
+    _fields_ = [("solves", ctypes.c_int32), ("iters_max", ctypes.c_int32), ("max_rel_resid", ctypes.c_double),
+                ("var_probes", ctypes.c_int32), ("prec_used", ctypes.c_int32)]
 
 
 _lib = None
@@ -111,6 +116,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
                                            c.POINTER(lgp_options), vp, vp, vp]),
         "lgp_measure_pipe_peak": (c.c_int32, [c.c_int32, c.POINTER(c.c_double), vp]),
         "lgp_tc_kernel_choice": (c.c_int32, [vp, c.c_int64, c.c_int32, c.c_int32, c.c_int32, c.c_int32]),
+        "lgp_predict": (c.c_int32, [vp, c.POINTER(lgp_hyper), vp, vp, c.c_int64, vp, c.c_int64,
+                                    c.POINTER(lgp_options), vp, vp, c.POINTER(lgp_predict_info), vp]),
         "lgp_kernel_matvec_noalloc": (c.c_int32, [c.POINTER(lgp_hyper), vp, vp, vp, c.c_int64, c.c_int32, c.c_int32,
                                                   vp]),
     }
@@ -332,6 +339,28 @@ def lgp_lml_and_grad(X, y, hyp, n_probes: int = 15, lanczos_steps: int = 50, see
     d = {k: getattr(info, k) for k, _ in lgp_lml_info._fields_}
     d["status"] = s
     return lml.value, (grad if want_grad else None), d
+
+
+def lgp_predict(X, y, hyp, Xs, n_probes: int = 0, seed: int = 0, tol: float = 1e-6, max_iter: int = 1000,
+                prec: int = LGP_PREC_AUTO, want_var: bool = True, ctx: Context | None = None, stream=None):
+    """Posterior predictive mean [M] and latent variance [M] (or None) at test points Xs [M, D].
+
+    n_probes = 0: exact variance; 1..31: the Rademacher diagonal estimate with that many probes.
+    Returns (mean, var, info dict, status)."""
+    import torch
+    ctx = ctx or default_context(X.device.index or 0)
+    N = int(y.shape[0])
+    M = int(Xs.shape[0])
+    mean = torch.empty(M, device=X.device, dtype=torch.float32)
+    var = torch.empty(M, device=X.device, dtype=torch.float32) if want_var else None
+    info = lgp_predict_info()
+    h, keep = Hyper.of(hyp).to_c()
+    o = _options(tol, max_iter, 0, n_probes, prec, seed)
+    s = ctx._check(ctx.lib.lgp_predict(ctx.h, ctypes.byref(h), _ptr(X), _ptr(y), N, _ptr(Xs), M, ctypes.byref(o),
+                                       _ptr(mean), _ptr(var) if var is not None else None, ctypes.byref(info),
+                                       _stream_ptr(stream)), allow_warn=True)
+    del keep
+    return mean, var, {k: getattr(info, k) for k, _ in info._fields_}, s
 
 
 def lgp_rademacher_probes(seed: int, N: int, m: int, device: int = 0, ctx: Context | None = None, stream=None):

@@ -41,7 +41,7 @@ struct lgp_ctx {
     cudaEvent_t ev_chunk[2] = {nullptr, nullptr};
     // workspace
     DevBuf xs, mv_partial, cg_vec, cg_partial, cg_state, cg_hist, scal, rhs, adj_b, adj_partial, vsplit, flags;
-    DevBuf batch_meta;
+    DevBuf batch_meta, pred_xs, pred_z, pred_q;
     int64_t ws_bytes = 0;
     // pinned host mirrors
     CgState *h_state = nullptr;
@@ -561,7 +561,7 @@ void lgp_destroy(lgp_ctx *ctx) {
     cudaSetDevice(ctx->device);
     if (ctx->work) cudaStreamSynchronize(ctx->work);
     if (ctx->cg_exec) cudaGraphExecDestroy(ctx->cg_exec);
-    DevBuf *bufs[] = {&ctx->xs, &ctx->mv_partial, &ctx->cg_vec, &ctx->cg_partial, &ctx->cg_state, &ctx->cg_hist,
+    DevBuf *bufs[] = {&ctx->pred_xs, &ctx->pred_z, &ctx->pred_q, &ctx->xs, &ctx->mv_partial, &ctx->cg_vec, &ctx->cg_partial, &ctx->cg_state, &ctx->cg_hist,
                       &ctx->scal, &ctx->rhs, &ctx->adj_b, &ctx->adj_partial, &ctx->vsplit, &ctx->flags,
                       &ctx->batch_meta};
     for (DevBuf *b : bufs)
@@ -781,6 +781,157 @@ lgp_status lgp_lml_and_grad(lgp_ctx *ctx, const lgp_hyper *hyp, const float *X, 
         info->launches = 3 + 2 + ran * (kChunk * cg_iteration_launches(ctx, pp, t, prec) + 1) + 2 + 1 + (grad ? 3 : 0);
     }
     return cs;
+}
+
+// Column count of a prediction solve block: padded with zero columns (inactive from the start) up to
+// 16 or 32 when the tensor-core product can then take the block, else t itself.
+static int predict_width(int t, int req_prec) {
+    if (req_prec == LGP_PREC_FP32 || t <= 8 || !tc_supported(16)) return t;
+    return t <= 16 ? 16 : 32;
+}
+
+lgp_status lgp_predict(lgp_ctx *ctx, const lgp_hyper *hyp, const float *X, const float *y, int64_t N,
+                       const float *Xs, int64_t M, const lgp_options *opt, float *mean, float *var,
+                       lgp_predict_info *info, lgp_stream stream) {
+    constexpr int kChunkCols = 32;
+    if (!ctx) return LGP_ERR_INVALID_ARG;
+    if (N < 1) return fail(ctx, LGP_ERR_INVALID_ARG, "N=%lld must be >= 1", (long long)N);
+    if (M < 1) return fail(ctx, LGP_ERR_INVALID_ARG, "M=%lld must be >= 1", (long long)M);
+    lgp_status s;
+    if ((s = check_opts(ctx, opt, false)) != LGP_OK) return s;
+    const int m = var ? opt->n_probes : 0;
+    if (m < 0 || m > kChunkCols - 1)
+        return fail(ctx, LGP_ERR_UNSUPPORTED, "n_probes=%d outside 0..%d", opt->n_probes, kChunkCols - 1);
+    LGP_CUDA(cudaSetDevice(ctx->device));
+    if ((s = check_dev_ptr(ctx, X, "X")) || (s = check_dev_ptr(ctx, y, "y")) || (s = check_dev_ptr(ctx, Xs, "Xs")) ||
+        (s = check_dev_ptr(ctx, mean, "mean")))
+        return s;
+    if (var && (s = check_dev_ptr(ctx, var, "var")) != LGP_OK) return s;
+    if (var == mean) return fail(ctx, LGP_ERR_INVALID_ARG, "var aliases mean");
+    cudaStream_t user = (cudaStream_t)stream;
+    if ((s = enter(ctx, user)) != LGP_OK) return s;
+    cudaStream_t st = ctx->work;
+    LGP_CUDA(cudaMemsetAsync(ctx->flags.p, 0, 4 * sizeof(int), st));
+    Prepared pp;
+    if ((s = prepare_x(ctx, hyp, X, N, st, &pp)) != LGP_OK) return s;
+    // test points, prescaled like X (their non-finite check shares the flag of X)
+    const int64_t Mp = pad_rows(M);
+    if ((s = ensure(ctx, ctx->pred_xs, (size_t)Mp * pp.kp.dpad * sizeof(float))) != LGP_OK) return s;
+    float *xs_star = (float *)ctx->pred_xs.p;
+    launch_prep_x(Xs, M, pp.kp.D, pp.kp.dpad, pp.kp.scale, xs_star, Mp, (int *)ctx->flags.p, st);
+    LGP_CUDA(cudaGetLastError());
+
+    int solves = 0, iters_max = 0, prec_first = LGP_PREC_FP32;
+    double rel_max = 0.0;
+    bool unconverged = false;
+    // one batched CG solve of the block rhs [Np, t]; its state is checked on the host
+    auto solve = [&](const float *rhs, int t, CgBuffers *b) -> lgp_status {
+        int prec = opt->prec;
+        if (prec != LGP_PREC_FP32 && !(tc_supported(t) && (t == 16 || t == 32))) prec = LGP_PREC_FP32;
+        prec = resolve_prec(t, prec);
+        if (prec < 0) return fail(ctx, (lgp_status)prec, "precision %d unsupported for t=%d", opt->prec, t);
+        if (solves == 0) prec_first = prec;
+        lgp_status r = run_cg(ctx, pp, rhs, t, t, opt, 0, prec, b);
+        if (r != LGP_OK) return r;
+        LGP_CUDA(cudaMemcpyAsync(ctx->h_flags, ctx->flags.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        LGP_CUDA(cudaStreamSynchronize(st));
+        if (ctx->h_flags[1]) return fail(ctx, LGP_ERR_TIMEOUT, "a bounded device wait ran out (code %d)", ctx->h_flags[1]);
+        std::vector<int> it(t);
+        std::vector<double> rel(t);
+        const lgp_status cs = cg_status_of(ctx, *ctx->h_state, t, it.data(), rel.data(), ctx->h_flags[0]);
+        if (cs < 0) return cs;
+        unconverged |= cs == LGP_WARN_NOT_CONVERGED;
+        ++solves;
+        iters_max = std::max(iters_max, *std::max_element(it.begin(), it.end()));
+        rel_max = std::max(rel_max, *std::max_element(rel.begin(), rel.end()));
+        return LGP_OK;
+    };
+    // out [Nr, ldo] = K(rows, cols) V on the FP32 cross product
+    auto cross = [&](const float *xr, int64_t nr, int64_t npr, const float *xc, int64_t nc, int64_t npc, const float *V,
+                     int64_t ldv, int t, float *out, int64_t ldo) -> lgp_status {
+        const int64_t pf = mv_simt_cross_partial_floats(nr, npr, nc, t, ctx->num_sms);
+        lgp_status r = ensure(ctx, ctx->mv_partial, (size_t)std::max<int64_t>(pf, 1) * sizeof(float));
+        if (r != LGP_OK) return r;
+        MvLaunch mm;
+        mm.kp = &pp.kp;
+        mm.Xs = xc;
+        mm.N = nc;
+        mm.Np = npc;
+        mm.V = V;
+        mm.ldv = ldv;
+        mm.out = out;
+        mm.ldo = ldo;
+        mm.t = t;
+        mm.partial = (float *)ctx->mv_partial.p;
+        mm.partial_cap = (int64_t)(ctx->mv_partial.bytes / sizeof(float));
+        mm.skip = nullptr;
+        mm.num_sms = ctx->num_sms;
+        mm.Xr = xr;
+        mm.Nr = nr;
+        mm.Npr = npr;
+        LGP_CUDA(launch_mv_simt(mm, st));
+        return LGP_OK;
+    };
+
+    if (m > 0) {
+        // probe route: one solve of [y, K_f* Z], then Q = K_*f K_y^{-1} K_f* Z
+        const int t = m + 1;
+        if ((s = ensure(ctx, ctx->rhs, (size_t)pp.Np * t * sizeof(float))) != LGP_OK) return s;
+        if ((s = ensure(ctx, ctx->pred_z, (size_t)Mp * m * sizeof(float))) != LGP_OK) return s;
+        if ((s = ensure(ctx, ctx->pred_q, (size_t)Mp * m * sizeof(float))) != LGP_OK) return s;
+        float *rhs = (float *)ctx->rhs.p, *Z = (float *)ctx->pred_z.p, *Q = (float *)ctx->pred_q.p;
+        launch_rademacher(opt->seed, M, m, Z, m, 0, st);
+        launch_copy_cols(y, 1, rhs, t, N, 1, 0, st);
+        LGP_CUDA(cudaGetLastError());
+        if ((s = cross(pp.xs, N, pp.Np, xs_star, M, Mp, Z, m, m, rhs + 1, t)) != LGP_OK) return s;
+        CgBuffers b;
+        if ((s = solve(rhs, t, &b)) != LGP_OK) return s;
+        if ((s = cross(xs_star, M, Mp, pp.xs, N, pp.Np, b.x, t, 1, mean, 1)) != LGP_OK) return s;
+        if ((s = cross(xs_star, M, Mp, pp.xs, N, pp.Np, b.x + 1, t, m, Q, m)) != LGP_OK) return s;
+        launch_var_from_probes(Z, m, Q, m, M, m, pp.kp.s2, var, st);
+        LGP_CUDA(cudaGetLastError());
+    } else {
+        // exact route: blocks [y, k(X, x*_0..)] then [k(X, x*_j0..)], up to 32 columns each
+        if ((s = ensure(ctx, ctx->scal, (size_t)(2 * kMaxT + 4 + kMaxD + 2) * sizeof(double))) != LGP_OK) return s;
+        int64_t j0 = 0;
+        for (bool first = true; first || (var && j0 < M); first = false) {
+            const int lead = first ? 1 : 0;
+            const int tc = var ? (int)std::min<int64_t>(kChunkCols - lead, M - j0) : 0;
+            const int t = predict_width(lead + tc, opt->prec);
+            if ((s = ensure(ctx, ctx->rhs, (size_t)pp.Np * t * sizeof(float))) != LGP_OK) return s;
+            float *rhs = (float *)ctx->rhs.p;
+            if (t > lead + tc) LGP_CUDA(cudaMemsetAsync(rhs, 0, (size_t)pp.Np * t * sizeof(float), st));
+            if (first) launch_copy_cols(y, 1, rhs, t, N, 1, 0, st);
+            if (tc) launch_kernel_cols(pp.kp, pp.xs, N, pp.Np, xs_star, j0, tc, rhs, t, lead, st);
+            LGP_CUDA(cudaGetLastError());
+            CgBuffers b;
+            if ((s = solve(rhs, t, &b)) != LGP_OK) return s;
+            if (first && (s = cross(xs_star, M, Mp, pp.xs, N, pp.Np, b.x, t, 1, mean, 1)) != LGP_OK) return s;
+            if (tc) {
+                double *dots = (double *)ctx->scal.p;
+                launch_col_dots(b.x, rhs, N, t, b.partial, b.G, dots, st);
+                launch_var_from_dots(dots, lead, lead + tc, pp.kp.s2, var, j0, st);
+                LGP_CUDA(cudaGetLastError());
+            }
+            j0 += tc;
+        }
+    }
+    LGP_CUDA(cudaMemcpyAsync(ctx->h_flags, ctx->flags.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    if ((s = leave_sync(ctx, user)) != LGP_OK) return s;
+    if (ctx->h_flags[1]) return fail(ctx, LGP_ERR_TIMEOUT, "a bounded device wait ran out (code %d)", ctx->h_flags[1]);
+    if (ctx->h_flags[0]) return fail(ctx, LGP_ERR_NONFINITE, "X or Xs contains NaN or Inf");
+    if (info) {
+        info->solves = solves;
+        info->iters_max = iters_max;
+        info->max_rel_resid = rel_max;
+        info->var_probes = m;
+        info->prec_used = prec_first;
+    }
+    if (unconverged) {
+        fail(ctx, LGP_WARN_NOT_CONVERGED, "CG reached max_iter before tol on some column");
+        return LGP_WARN_NOT_CONVERGED;
+    }
+    return LGP_OK;
 }
 
 lgp_status lgp_batch_cg_solve(lgp_ctx *ctx, int32_t n_gp, const lgp_hyper *hyp, const float *const *X,

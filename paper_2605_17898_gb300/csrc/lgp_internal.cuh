@@ -154,6 +154,13 @@ void launch_scan_finite(const float *A, int64_t n, int *err_flag, cudaStream_t s
 void launch_copy_cols(const float *src, int64_t lds, float *dst, int64_t ldd, int64_t rows, int cols, int dst_col0,
                       cudaStream_t st);
 
+// predict.cu
+void launch_kernel_cols(const KernelParams &kp, const float *Xh, int64_t N, int64_t Np, const float *Xsh, int64_t j0,
+                        int tc, float *B, int64_t ldb, int col0, cudaStream_t st);
+void launch_var_from_dots(const double *dots, int c0, int t, float s2, float *var, int64_t j0, cudaStream_t st);
+void launch_var_from_probes(const float *Z, int64_t ldz, const float *Q, int64_t ldq, int64_t M, int m, float s2,
+                            float *var, cudaStream_t st);
+
 // mv_simt.cu
 struct MvLaunch {
     const KernelParams *kp;
@@ -168,10 +175,16 @@ struct MvLaunch {
     int64_t partial_cap;  // floats available in partial
     const int *skip;      // device flag: skip all work when *skip != 0 (may be nullptr)
     int num_sms;
+    // Cross product out = K(Xr, Xs) V (no noise term): prescaled row points [Npr, dpad] and their
+    // count; Xr == nullptr gives the square product K_y V.
+    const float *Xr = nullptr;
+    int64_t Nr = 0, Npr = 0;
 };
 cudaError_t launch_mv_simt(const MvLaunch &m, cudaStream_t st);
 int mv_simt_launches(int64_t N, int64_t Np, int t, int num_sms);
 int64_t mv_simt_partial_floats(int64_t N, int64_t Np, int t, int num_sms);
+// Split partial floats of the cross product with Nr output rows (Npr padded) and N columns.
+int64_t mv_simt_cross_partial_floats(int64_t Nr, int64_t Npr, int64_t N, int t, int num_sms);
 
 cudaError_t launch_mv_grad(const KernelParams &kp, const float *Xs, int64_t N, int64_t Np, const float *W, int t,
                            float *G, float *partial, int64_t partial_cap, int num_sms, cudaStream_t st);

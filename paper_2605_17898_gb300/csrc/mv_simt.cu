@@ -32,9 +32,10 @@ int64_t choose_split(int64_t N, int64_t row_blocks, int64_t col_groups, int num_
     return (N + *cols_per_split - 1) / *cols_per_split;
 }
 
+// Rows are the output's (N, padded Np); cross = 1 drops the noise term (V has other rows).
 __global__ void reduce_split_kernel(const float *__restrict__ partial, int S, int64_t Np, int64_t N, int t,
                                     const float *__restrict__ V, int64_t ldv, float *__restrict__ out, int64_t ldo,
-                                    float noise, const int *skip) {
+                                    float noise, int cross, const int *skip) {
     if (skip && *skip) return;
     const int64_t total = N * t;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
@@ -42,7 +43,7 @@ __global__ void reduce_split_kernel(const float *__restrict__ partial, int S, in
         const int c = (int)(e - i * t);
         float s = 0.0f;
         for (int k = 0; k < S; ++k) s += partial[((int64_t)k * Np + i) * t + c];
-        out[i * ldo + c] = fmaf(noise, V[i * ldv + c], s);
+        out[i * ldo + c] = cross ? s : fmaf(noise, V[i * ldv + c], s);
     }
 }
 
@@ -81,23 +82,39 @@ int64_t mv_simt_partial_floats(int64_t N, int64_t Np, int t, int num_sms) {
     return S > 1 ? S * Np * t : 0;
 }
 
+int64_t mv_simt_cross_partial_floats(int64_t Nr, int64_t Npr, int64_t N, int t, int num_sms) {
+    const SimtShape sh = simt_shape(t);
+    const int64_t BM = (int64_t)kSimtThreads * sh.R;
+    const int64_t rb = (Nr + BM - 1) / BM;
+    const int64_t cg = (t + sh.TT - 1) / sh.TT;
+    int64_t cps;
+    const int64_t S = choose_split(N, rb, cg, num_sms, &cps);
+    return S > 1 ? S * Npr * t : 0;
+}
+
 int mv_simt_launches(int64_t N, int64_t Np, int t, int num_sms) {
     return mv_simt_partial_floats(N, Np, t, num_sms) > 0 ? 2 : 1;
 }
 
 cudaError_t launch_mv_simt(const MvLaunch &m, cudaStream_t st) {
+    const bool cross = m.Xr != nullptr;
+    const int64_t Nr = cross ? m.Nr : m.N, Npr = cross ? m.Npr : m.Np;
     const SimtShape sh = simt_shape(m.t);
     const int64_t BM = (int64_t)kSimtThreads * sh.R;
-    const int64_t rb = (m.N + BM - 1) / BM;
+    const int64_t rb = (Nr + BM - 1) / BM;
     const int64_t cg = (m.t + sh.TT - 1) / sh.TT;
     int64_t cps;
     int64_t S = choose_split(m.N, rb, cg, m.num_sms, &cps);
-    if (S > 1 && (m.partial == nullptr || S * m.Np * m.t > m.partial_cap)) {
+    if (S > 1 && (m.partial == nullptr || S * Npr * m.t > m.partial_cap)) {
         S = 1;
         cps = m.N;
     }
     SimtArgs a;
     a.Xs = m.Xs;
+    a.Xr = cross ? m.Xr : m.Xs;
+    a.Nr = Nr;
+    a.Npr = Npr;
+    a.cross = cross ? 1 : 0;
     a.V = m.V;
     a.out = m.out;
     a.partial = S > 1 ? m.partial : nullptr;
@@ -120,8 +137,8 @@ cudaError_t launch_mv_simt(const MvLaunch &m, cudaStream_t st) {
         default: e = cudaErrorInvalidValue;
     }
     if (e != cudaSuccess || S == 1) return e;
-    reduce_split_kernel<<<grid_for(m.N * m.t), 256, 0, st>>>(m.partial, (int)S, m.Np, m.N, m.t, m.V, m.ldv, m.out,
-                                                             m.ldo, m.kp->noise, m.skip);
+    reduce_split_kernel<<<grid_for(Nr * m.t), 256, 0, st>>>(m.partial, (int)S, Npr, Nr, m.t, m.V, m.ldv, m.out,
+                                                            m.ldo, m.kp->noise, a.cross, m.skip);
     return cudaGetLastError();
 }
 

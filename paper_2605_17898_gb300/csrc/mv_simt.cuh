@@ -23,12 +23,15 @@ constexpr int kSimtThreads = 128;
 constexpr int kSimtBN = 64;
 
 struct SimtArgs {
-    const float *Xs;   // prescaled [Np, DP]
+    const float *Xs;   // prescaled column points [Np, DP]
+    const float *Xr;   // prescaled row points [Npr, DP] (Xs itself for K_y V)
     const float *V;    // [N, ldv]
-    float *out;        // [N, ldo] (direct mode)
-    float *partial;    // [S, Np, t] (split mode) or nullptr
+    float *out;        // [Nr, ldo] (direct mode)
+    float *partial;    // [S, Npr, t] (split mode) or nullptr
     const int *skip;
     int64_t N, Np, ldv, ldo;
+    int64_t Nr, Npr;   // rows of the output, and of Xr
+    int cross;         // 1: out = K(Xr, Xs) V with no noise term
     int64_t cols_per_split;
     int t;
     float log2s2;
@@ -101,7 +104,7 @@ __global__ void __launch_bounds__(kSimtThreads) mv_simt_kernel(SimtArgs a) {
     for (int r = 0; r < R; ++r) {
         const int64_t i = row0 + r * kSimtThreads + tid;
 #pragma unroll
-        for (int d = 0; d < D; ++d) xi[r][d] = (i < a.Np) ? a.Xs[i * DP + d] : 0.0f;
+        for (int d = 0; d < D; ++d) xi[r][d] = (i < a.Npr) ? a.Xr[i * DP + d] : 0.0f;
 #pragma unroll
         for (int c = 0; c < TT; ++c) tot[r][c] = 0.0f;
     }
@@ -154,9 +157,9 @@ __global__ void __launch_bounds__(kSimtThreads) mv_simt_kernel(SimtArgs a) {
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int64_t i = row0 + r * kSimtThreads + tid;
-        if (i >= a.N) continue;
+        if (i >= a.Nr) continue;
         if (a.partial) {
-            float *dst = a.partial + ((int64_t)blockIdx.y * a.Np + i) * a.t + c0;
+            float *dst = a.partial + ((int64_t)blockIdx.y * a.Npr + i) * a.t + c0;
 #pragma unroll
             for (int c = 0; c < TT; ++c)
                 if (c0 + c < a.t) dst[c] = tot[r][c];
@@ -164,7 +167,7 @@ __global__ void __launch_bounds__(kSimtThreads) mv_simt_kernel(SimtArgs a) {
 #pragma unroll
             for (int c = 0; c < TT; ++c)
                 if (c0 + c < a.t)
-                    a.out[i * a.ldo + c0 + c] = fmaf(a.noise, a.V[i * a.ldv + c0 + c], tot[r][c]);
+                    a.out[i * a.ldo + c0 + c] = a.cross ? tot[r][c] : fmaf(a.noise, a.V[i * a.ldv + c0 + c], tot[r][c]);
         }
     }
 }

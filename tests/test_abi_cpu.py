@@ -74,6 +74,7 @@ def test_struct_layouts_are_packed_as_in_c():
     assert ctypes.sizeof(pkg.lgp_hyper) == 24
     assert ctypes.sizeof(pkg.lgp_options) == 32
     assert ctypes.sizeof(pkg.lgp_lml_info) == 56
+    assert ctypes.sizeof(pkg.lgp_predict_info) == 24
 
 
 def test_workloads_shapes_and_dtypes():
