@@ -54,12 +54,16 @@ def parse():
     ap.add_argument("--lanczos", type=int, default=50)
     ap.add_argument("--tol", type=float, default=1e-2)
     ap.add_argument("--max-iter", type=int, default=1000)
-    ap.add_argument("--prec", choices=["auto", "fp32", "split_bf16"], default="auto")
+    ap.add_argument("--prec", choices=["auto", "fp32", "split_bf16", "split_f16"], default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--plain", action="store_true", help="also time the plain FP32 single-RHS path")
-    ap.add_argument("--mode", choices=["lml", "matvec"], default="lml",
-                    help="lml: the LML+grad step (default); matvec: only the product, for kernel profiling")
+    ap.add_argument("--mode", choices=["lml", "matvec", "predict"], default="lml",
+                    help="lml: the LML+grad step (default); matvec: only the product, for kernel profiling; "
+                         "predict: posterior mean and variance at --M test points")
+    ap.add_argument("--M", type=int, default=10000, help="test points of --mode predict")
+    ap.add_argument("--var-probes", type=int, default=31,
+                    help="--mode predict: probes of the variance estimate (0: exact per-point variance)")
     return ap.parse_args()
 
 
@@ -267,15 +271,18 @@ def main():
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    lgp.build.build() if hasattr(lgp, "build") and False else None
     lgp.load()
     ctx = lgp.Context(local)
-    prec = {"auto": lgp.LGP_PREC_AUTO, "fp32": lgp.LGP_PREC_FP32, "split_bf16": lgp.LGP_PREC_SPLIT_BF16}[args.prec]
+    prec = {"auto": lgp.LGP_PREC_AUTO, "fp32": lgp.LGP_PREC_FP32, "split_bf16": lgp.LGP_PREC_SPLIT_BF16,
+            "split_f16": lgp.LGP_PREC_SPLIT_F16}[args.prec]
 
     p = wl.cfg3(N=args.N, t=args.t)
     m = args.t - 1
     if args.mode == "matvec":
         bench_matvec_only(lgp, ctx, p, args, dev, prec, rank)
+        return
+    if args.mode == "predict":
+        bench_predict(lgp, ctx, p, args, dev, prec, rank)
         return
     X = torch.as_tensor(p.X, device=dev)
     y = torch.as_tensor(p.y, device=dev)
@@ -427,6 +434,39 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def bench_predict(lgp, ctx, p, args, dev, prec, rank):
+    """Posterior mean and variance at M test points drawn like the training inputs (one call of
+    lgp_predict per step: CG solve(s), the cross products and the variance finalisation)."""
+    import numpy as np
+    import torch
+    X = torch.as_tensor(p.X, device=dev)
+    y = torch.as_tensor(p.y, device=dev)
+    Xs = torch.as_tensor(np.random.default_rng(7).uniform(-1.0, 1.0, (args.M, p.D)).astype(np.float32), device=dev)
+
+    def step():
+        return lgp.lgp_predict(X, y, p, Xs, n_probes=args.var_probes, seed=99, tol=args.tol,
+                               max_iter=args.max_iter, prec=prec, ctx=ctx)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ms, infos = [], []
+    for _ in range(args.steps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        _, _, info, _ = step()
+        b.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+        infos.append(info)
+    if rank == 0:
+        print(json.dumps({"mode": "predict", "workload": p.name, "M": args.M, "var_probes": args.var_probes,
+                          "tol": args.tol, "ms": statistics.mean(ms), "ms_all": ms,
+                          "solves": infos[-1]["solves"], "iters_max": infos[-1]["iters_max"],
+                          "prec_used": infos[-1]["prec_used"]}), flush=True)
 
 
 def bench_matvec_only(lgp, ctx, p, args, dev, prec, rank):
