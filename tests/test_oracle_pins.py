@@ -392,3 +392,97 @@ def test_prediction_cg_route_reaches_the_exact_values():
     pr = go.predict_fp64(X, y, Xs, hyp, n_probes=8, seed=5, tol=1e-12)
     np.testing.assert_allclose(pr["var"], go.predict_var_hutchinson_target(X, Xs, hyp, pr["Z"]), rtol=1e-8,
                                atol=1e-10)
+
+
+# ----------------------------------------------------------------------------- preconditioning
+
+def test_pivoted_cholesky_full_rank_and_residual_trace():
+    """Full rank reproduces K_ff; at lower rank the returned residual diagonal is diag(K - L L^T) and
+    its trace falls with the rank (the pivoting rule picks the largest residual each step)."""
+    hyp = _hyp(go.MATERN32, 2, seed=31)
+    X = _points(18, 2, seed=31)
+    K = go.kernel_matrix(X, hyp)
+    L, piv, d = go.pivoted_cholesky(X, hyp, 18)
+    np.testing.assert_allclose(L @ L.T, K, rtol=0, atol=1e-10)
+    assert sorted(piv.tolist()) == list(range(18)) and piv[0] == 0
+    prev = np.inf
+    for k in (2, 5, 9):
+        L, piv, d = go.pivoted_cholesky(X, hyp, k)
+        np.testing.assert_allclose(d, np.diag(K - L @ L.T), rtol=0, atol=1e-12)
+        assert np.all(d >= -1e-12) and d.sum() < prev
+        prev = d.sum()
+
+
+def test_woodbury_inverse_and_determinant_lemma():
+    hyp = _hyp(go.RBF, 3, seed=32)
+    X = _points(40, 3, seed=32)
+    L, _, _ = go.pivoted_cholesky(X, hyp, 6)
+    P = L @ L.T + hyp.noise * np.eye(40)
+    R = np.random.default_rng(32).standard_normal((40, 3))
+    np.testing.assert_allclose(go.precond_inverse(L, hyp.noise)(R), np.linalg.solve(P, R), rtol=1e-9, atol=1e-9)
+    assert go.precond_logdet(L, hyp.noise) == pytest.approx(np.linalg.slogdet(P)[1], rel=1e-12)
+
+
+def test_pcg_special_cases():
+    """Identity preconditioner: the same iterates as CG. Exact preconditioner P = K_y: one step.
+    Any preconditioner: the Cholesky solution."""
+    hyp = _hyp(go.MATERN52, 2, seed=33)
+    X = _points(60, 2, seed=33)
+    Ky = go.noisy_kernel_matrix(X, hyp)
+    B = np.random.default_rng(33).standard_normal((60, 2))
+    a = go.cg(lambda P: Ky @ P, B, 1e-10, 200)
+    b = go.pcg(lambda P: Ky @ P, lambda R: np.array(R, dtype=np.float64), B, 1e-10, 200)
+    np.testing.assert_allclose(b.x, a.x, rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(b.alphas, a.alphas, rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(b.betas, a.betas, rtol=1e-12, atol=1e-14)
+    one = go.pcg(lambda P: Ky @ P, lambda R: np.linalg.solve(Ky, R), B, 1e-10, 200)
+    assert one.iters.max() == 1
+    L, _, _ = go.pivoted_cholesky(X, hyp, 8)
+    pc = go.pcg(lambda P: Ky @ P, go.precond_inverse(L, hyp.noise), B, 1e-12, 500)
+    np.testing.assert_allclose(pc.x, go.cholesky_solve(Ky, B), rtol=1e-9, atol=1e-10)
+    np.testing.assert_allclose(pc.rz0, np.sum(B * go.precond_inverse(L, hyp.noise)(B), axis=0), rtol=1e-12)
+
+
+def test_full_length_preconditioned_quadrature_is_exact():
+    """N PCG steps: (z^T P^{-1} z) e1^T log(T) e1 = w^T log(P^{-1/2} K_y P^{-1/2}) w, w = P^{-1/2} z."""
+    N = 24
+    hyp = _hyp(go.RBF, 2, seed=34, ln=math.log(0.5))
+    X = _points(N, 2, seed=34)
+    Ky = go.noisy_kernel_matrix(X, hyp)
+    L, _, _ = go.pivoted_cholesky(X, hyp, 4)
+    z = go.precond_probes(7, L, hyp.noise, 1)
+    res = go.pcg(lambda P: Ky @ P, go.precond_inverse(L, hyp.noise), z, 0.0, N)
+    T = go.lanczos_tridiag_from_cg(res.alphas[:N, 0], res.betas[:N, 0], N)
+    P = L @ L.T + hyp.noise * np.eye(N)
+    lam, Q = np.linalg.eigh(P)
+    Pm12 = (Q / np.sqrt(lam)) @ Q.T
+    mu, V = np.linalg.eigh(Pm12 @ Ky @ Pm12)
+    w = Pm12 @ z[:, 0]
+    ref = float(np.sum((V.T @ w) ** 2 * np.log(mu)))
+    assert go.quadrature_logdet(T, float(res.rz0[0])) == pytest.approx(ref, rel=1e-8)
+
+
+def test_hadamard_probes_make_preconditioned_estimators_exact():
+    """z = [sigma I, L] e over all N + k Hadamard columns e: z z^T averages to P, so the probe targets
+    are the exact log-determinant and gradient."""
+    N, k = 58, 6
+    hyp = _hyp(go.MATERN32, 2, seed=35)
+    X = _points(N, 2, seed=35)
+    y = np.random.default_rng(35).standard_normal(N)
+    L, _, _ = go.pivoted_cholesky(X, hyp, k)
+    H = sla.hadamard(N + k).astype(np.float64)
+    Z = L @ H[N:] + math.sqrt(hyp.noise) * H[:N]
+    tg = go.precond_probe_targets(X, y, hyp, L, Z)
+    assert tg["logdet"] == pytest.approx(go.logdet(go.noisy_kernel_matrix(X, hyp)), rel=1e-10)
+    np.testing.assert_allclose(tg["grad"], go.grad_exact(X, y, hyp), rtol=1e-8, atol=1e-9)
+
+
+def test_preconditioned_fp64_estimator_hits_its_probe_targets():
+    hyp = _hyp(go.RBF, 3, seed=36, ln=math.log(0.01))
+    X = _points(150, 3, seed=36)
+    y = np.random.default_rng(36).standard_normal(150)
+    est = go.estimator_precond_fp64(X, y, hyp, rank=8, n_probes=6, lanczos_steps=150, seed=9, tol=1e-11,
+                                    max_iter=2000)
+    tg = go.precond_probe_targets(X, y, hyp, est["L"], est["Z"])
+    assert est["logdet"] == pytest.approx(tg["logdet"], rel=1e-8)
+    np.testing.assert_allclose(est["grad"], tg["grad"], rtol=1e-6, atol=1e-6 * np.abs(tg["grad"]).max())
