@@ -96,6 +96,10 @@ typedef struct {
     int32_t n_probes;        /* m Rademacher probes; the solve block is [y, z_1..z_m], t = m + 1 */
     int32_t prec;            /* lgp_precision of the products inside the solve */
     uint64_t seed;           /* probe seed (see lgp_rademacher_probes) */
+    int32_t precond_rank;    /* 0: plain CG (the paper's loop); k in 1..32: CG preconditioned by
+                                P = L L^T + sigma_n^2 I, L the rank-k pivoted Cholesky factor of K_ff
+                                (solves of at most 32 columns) */
+    int32_t reserved;        /* set to 0 */
 } lgp_options;
 
 typedef struct {
@@ -109,6 +113,7 @@ typedef struct {
     int32_t prec_used;       /* lgp_precision actually used for the products */
     int32_t launches;        /* kernel launches this call made on the device */
     int32_t cg_chunks;       /* CUDA-graph replays of the CG iteration chunk */
+    double logdet_precond;   /* log|P| of the preconditioner (0 without one); included in logdet */
 } lgp_lml_info;
 
 typedef struct {

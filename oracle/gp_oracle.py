@@ -501,7 +501,8 @@ def pivoted_cholesky(X, hyp: Hyper, rank: int) -> tuple[np.ndarray, np.ndarray, 
     residual diagonal d = diag(K_ff - L L^T).
 
     Step m: i = argmax d (first index on ties); L[:, m] = (K[:, i] - L[:, :m] L[i, :m]) / sqrt(d_i);
-    d -= L[:, m]^2. A step whose largest remaining d is not positive leaves its column zero.
+    d -= L[:, m]^2. Once the largest remaining d is at most 1e-10 s^2 (K_ff is numerically reproduced),
+    the remaining columns stay zero.
     """
     X = np.asarray(X, dtype=np.float64)
     N = X.shape[0]
@@ -510,7 +511,7 @@ def pivoted_cholesky(X, hyp: Hyper, rank: int) -> tuple[np.ndarray, np.ndarray, 
     piv = []
     for m in range(rank):
         i = int(np.argmax(d))
-        if not d[i] > 0.0:
+        if not d[i] > 1e-10 * hyp.s2:
             break
         piv.append(i)
         row = cross_kernel(X[i:i + 1], X, hyp)[0]

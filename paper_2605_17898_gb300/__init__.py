@@ -60,14 +60,15 @@ class lgp_hyper(ctypes.Structure):
 
 class lgp_options(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("lanczos_steps", ctypes.c_int32),
-                ("n_probes", ctypes.c_int32), ("prec", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+                ("n_probes", ctypes.c_int32), ("prec", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("precond_rank", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class lgp_lml_info(ctypes.Structure):
     _fields_ = [("lml", ctypes.c_double), ("quad", ctypes.c_double), ("logdet", ctypes.c_double),
                 ("max_rel_resid", ctypes.c_double), ("iters_max", ctypes.c_int32), ("iters_min", ctypes.c_int32),
                 ("t", ctypes.c_int32), ("prec_used", ctypes.c_int32), ("launches", ctypes.c_int32),
-                ("cg_chunks", ctypes.c_int32)]
+                ("cg_chunks", ctypes.c_int32), ("logdet_precond", ctypes.c_double)]
 
 
 class lgp_predict_info(ctypes.Structure):
@@ -294,13 +295,13 @@ def lgp_kernel_matvec_grad(X, hyp, W, ctx: Context | None = None, stream=None):
     return G
 
 
-def _options(tol, max_iter, lanczos_steps=0, n_probes=0, prec=LGP_PREC_AUTO, seed=0) -> lgp_options:
+def _options(tol, max_iter, lanczos_steps=0, n_probes=0, prec=LGP_PREC_AUTO, seed=0, precond_rank=0) -> lgp_options:
     return lgp_options(float(tol), int(max_iter), int(lanczos_steps), int(n_probes), int(prec),
-                       int(seed) & ((1 << 64) - 1))
+                       int(seed) & ((1 << 64) - 1), int(precond_rank), 0)
 
 
 def lgp_cg_solve(X, hyp, B, tol: float = 1e-6, max_iter: int = 1000, prec: int = LGP_PREC_AUTO,
-                 ctx: Context | None = None, stream=None, out=None):
+                 ctx: Context | None = None, stream=None, out=None, precond_rank: int = 0):
     """Solve K_y Xsol = B by batched CG. Returns (Xsol, iters[t], rel_resid[t], status)."""
     import torch
     ctx = ctx or default_context(X.device.index or 0)
@@ -312,7 +313,7 @@ def lgp_cg_solve(X, hyp, B, tol: float = 1e-6, max_iter: int = 1000, prec: int =
     iters = np.zeros(t, dtype=np.int32)
     rel = np.zeros(t, dtype=np.float64)
     h, keep = Hyper.of(hyp).to_c()
-    o = _options(tol, max_iter, prec=prec)
+    o = _options(tol, max_iter, prec=prec, precond_rank=precond_rank)
     s = ctx._check(ctx.lib.lgp_cg_solve(ctx.h, ctypes.byref(h), _ptr(X), _ptr(B2), _ptr(out), int(N), int(t),
                                         ctypes.byref(o), iters.ctypes.data_as(ctypes.c_void_p),
                                         rel.ctypes.data_as(ctypes.c_void_p), _stream_ptr(stream)))
@@ -322,7 +323,7 @@ def lgp_cg_solve(X, hyp, B, tol: float = 1e-6, max_iter: int = 1000, prec: int =
 
 def lgp_lml_and_grad(X, y, hyp, n_probes: int = 15, lanczos_steps: int = 50, seed: int = 0, tol: float = 1e-4,
                      max_iter: int = 1000, prec: int = LGP_PREC_AUTO, want_grad: bool = True,
-                     ctx: Context | None = None, stream=None):
+                     ctx: Context | None = None, stream=None, precond_rank: int = 0):
     """LML estimate, its gradient [D+2] (or None) and an info dict."""
     ctx = ctx or default_context(X.device.index or 0)
     N = int(y.shape[0])
@@ -331,7 +332,7 @@ def lgp_lml_and_grad(X, y, hyp, n_probes: int = 15, lanczos_steps: int = 50, see
     grad = np.zeros(D + 2, dtype=np.float64)
     info = lgp_lml_info()
     h, keep = Hyper.of(hyp).to_c()
-    o = _options(tol, max_iter, lanczos_steps, n_probes, prec, seed)
+    o = _options(tol, max_iter, lanczos_steps, n_probes, prec, seed, precond_rank)
     s = ctx._check(ctx.lib.lgp_lml_and_grad(ctx.h, ctypes.byref(h), _ptr(X), _ptr(y), N, ctypes.byref(o),
                                             ctypes.byref(lml), grad.ctypes.data_as(ctypes.c_void_p) if want_grad
                                             else None, ctypes.byref(info), _stream_ptr(stream)))
@@ -342,7 +343,8 @@ def lgp_lml_and_grad(X, y, hyp, n_probes: int = 15, lanczos_steps: int = 50, see
 
 
 def lgp_predict(X, y, hyp, Xs, n_probes: int = 0, seed: int = 0, tol: float = 1e-6, max_iter: int = 1000,
-                prec: int = LGP_PREC_AUTO, want_var: bool = True, ctx: Context | None = None, stream=None):
+                prec: int = LGP_PREC_AUTO, want_var: bool = True, ctx: Context | None = None, stream=None,
+                precond_rank: int = 0):
     """Posterior predictive mean [M] and latent variance [M] (or None) at test points Xs [M, D].
 
     n_probes = 0: exact variance; 1..31: the Rademacher diagonal estimate with that many probes.
@@ -355,7 +357,7 @@ def lgp_predict(X, y, hyp, Xs, n_probes: int = 0, seed: int = 0, tol: float = 1e
     var = torch.empty(M, device=X.device, dtype=torch.float32) if want_var else None
     info = lgp_predict_info()
     h, keep = Hyper.of(hyp).to_c()
-    o = _options(tol, max_iter, 0, n_probes, prec, seed)
+    o = _options(tol, max_iter, 0, n_probes, prec, seed, precond_rank)
     s = ctx._check(ctx.lib.lgp_predict(ctx.h, ctypes.byref(h), _ptr(X), _ptr(y), N, _ptr(Xs), M, ctypes.byref(o),
                                        _ptr(mean), _ptr(var) if var is not None else None, ctypes.byref(info),
                                        _stream_ptr(stream)), allow_warn=True)

@@ -42,6 +42,7 @@ struct lgp_ctx {
     // workspace
     DevBuf xs, mv_partial, cg_vec, cg_partial, cg_state, cg_hist, scal, rhs, adj_b, adj_partial, vsplit, flags;
     DevBuf batch_meta, pred_xs, pred_z, pred_q;
+    DevBuf pc_l64, pc_l32, pc_d, pc_info, pc_part, pc_u, pc_cinv, pc_gram, pc_e, pc_rhs;
     int64_t ws_bytes = 0;
     // pinned host mirrors
     CgState *h_state = nullptr;
@@ -300,6 +301,8 @@ lgp_status check_opts(lgp_ctx *ctx, const lgp_options *o, bool need_probes) {
     if (!o) return fail(ctx, LGP_ERR_INVALID_ARG, "options is NULL");
     if (!(o->tol > 0.0) || !std::isfinite(o->tol)) return fail(ctx, LGP_ERR_INVALID_ARG, "tol must be > 0");
     if (o->max_iter < 1) return fail(ctx, LGP_ERR_INVALID_ARG, "max_iter must be >= 1");
+    if (o->precond_rank < 0 || o->precond_rank > kMaxRank)
+        return fail(ctx, LGP_ERR_UNSUPPORTED, "precond_rank=%d outside 0..%d", o->precond_rank, kMaxRank);
     if (need_probes) {
         if (o->n_probes < 1 || o->n_probes + 1 > kMaxT)
             return fail(ctx, LGP_ERR_UNSUPPORTED, "n_probes=%d outside 1..%d", o->n_probes, kMaxT - 1);
@@ -312,7 +315,7 @@ lgp_status check_opts(lgp_ctx *ctx, const lgp_options *o, bool need_probes) {
 // Workspace layout of one CG run.
 lgp_status cg_buffers(lgp_ctx *ctx, int64_t N, int64_t Np, int t, int hist_len, CgBuffers *b) {
     lgp_status s;
-    if ((s = ensure(ctx, ctx->cg_vec, (size_t)4 * Np * t * sizeof(float))) != LGP_OK) return s;
+    if ((s = ensure(ctx, ctx->cg_vec, (size_t)5 * Np * t * sizeof(float))) != LGP_OK) return s;
     b->G = cg_num_blocks(N, t, ctx->num_sms);
     if ((s = ensure(ctx, ctx->cg_partial, (size_t)b->G * 2 * t * sizeof(double))) != LGP_OK) return s;
     if ((s = ensure(ctx, ctx->cg_state, sizeof(CgState))) != LGP_OK) return s;
@@ -322,10 +325,107 @@ lgp_status cg_buffers(lgp_ctx *ctx, int64_t N, int64_t Np, int t, int hist_len, 
     b->r = v + Np * t;
     b->p = v + 2 * Np * t;
     b->Kp = v + 3 * Np * t;
+    b->z = v + 4 * Np * t;
+    b->pc = Precond();
     b->partial = (double *)ctx->cg_partial.p;
     b->state = (CgState *)ctx->cg_state.p;
     b->hist_alpha = (double *)ctx->cg_hist.p;
     b->hist_beta = b->hist_alpha + (size_t)std::max(hist_len, 1) * t;
+    return LGP_OK;
+}
+
+// Cholesky factor of the symmetric positive definite n x n matrix A (row-major, in place, lower
+// triangle); false if a pivot is not positive.
+bool host_cholesky(std::vector<double> &A, int n) {
+    for (int j = 0; j < n; ++j) {
+        double d = A[j * n + j];
+        for (int q = 0; q < j; ++q) d -= A[j * n + q] * A[j * n + q];
+        if (!(d > 0.0)) return false;
+        const double ljj = std::sqrt(d);
+        A[j * n + j] = ljj;
+        for (int i = j + 1; i < n; ++i) {
+            double v = A[i * n + j];
+            for (int q = 0; q < j; ++q) v -= A[i * n + q] * A[j * n + q];
+            A[i * n + j] = v / ljj;
+        }
+    }
+    return true;
+}
+
+// Builds the rank-k pivoted-Cholesky preconditioner P = L L^T + sigma^2 I of K_y for solves with t
+// columns (precond.cu): L from the raw X in float64, C = sigma^2 I + L^T L reduced on the device and
+// factored on the host (float64), C^{-1} uploaded, log|P| = (N - k) log sigma^2 + log|C|.
+// Synchronises the internal stream once.
+lgp_status build_precond(lgp_ctx *ctx, const lgp_hyper *hyp, const float *X, const Prepared &pp, int k, int t,
+                         Precond *out) {
+    cudaStream_t st = ctx->work;
+    const int64_t N = pp.N, Np = pp.Np;
+    if (k < 1 || k > kMaxRank) return fail(ctx, LGP_ERR_UNSUPPORTED, "precond_rank=%d outside 1..%d", k, kMaxRank);
+    if (t > 32 || k * t > 1024)
+        return fail(ctx, LGP_ERR_UNSUPPORTED, "preconditioned solves take at most 32 columns (t=%d, rank %d)", t, k);
+    const int G2 = std::max(1, std::min(2 * ctx->num_sms, (int)((N + 255) / 256)));
+    lgp_status s;
+    if ((s = ensure(ctx, ctx->pc_l64, (size_t)k * Np * sizeof(double))) != LGP_OK ||
+        (s = ensure(ctx, ctx->pc_l32, (size_t)k * Np * sizeof(float))) != LGP_OK ||
+        (s = ensure(ctx, ctx->pc_d, (size_t)Np * sizeof(double))) != LGP_OK ||
+        (s = ensure(ctx, ctx->pc_info, pivinfo_bytes())) != LGP_OK ||
+        (s = ensure(ctx, ctx->pc_part, (size_t)G2 * k * t * sizeof(double))) != LGP_OK ||
+        (s = ensure(ctx, ctx->pc_u, (size_t)k * t * sizeof(double))) != LGP_OK ||
+        (s = ensure(ctx, ctx->pc_cinv, (size_t)k * k * sizeof(double))) != LGP_OK ||
+        (s = ensure(ctx, ctx->pc_gram, (size_t)G2 * k * k * sizeof(double))) != LGP_OK)
+        return s;
+    const int D = hyp->D;
+    double inv_ls[kMaxD];
+    for (int d = 0; d < D; ++d) inv_ls[d] = std::exp(-(double)hyp->log_lengthscale[d]);
+    const double s2 = std::exp((double)hyp->log_outputscale);
+    const double noise = std::exp((double)hyp->log_noise);
+    double *L64 = (double *)ctx->pc_l64.p;
+    launch_pivchol(X, N, Np, D, inv_ls, s2, hyp->kind, k, L64, (double *)ctx->pc_d.p, ctx->pc_info.p, st);
+    launch_gram(L64, Np, N, k, (double *)ctx->pc_gram.p, G2, st);
+    launch_to_f32(L64, (float *)ctx->pc_l32.p, (int64_t)k * Np, st);
+    LGP_CUDA(cudaGetLastError());
+    std::vector<double> part((size_t)G2 * k * k);
+    LGP_CUDA(cudaMemcpyAsync(part.data(), ctx->pc_gram.p, part.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    LGP_CUDA(cudaStreamSynchronize(st));
+    std::vector<double> C((size_t)k * k, 0.0);
+    for (int b = 0; b < G2; ++b)
+        for (int e = 0; e < k * k; ++e) C[e] += part[(size_t)b * k * k + e];
+    for (int q = 0; q < k; ++q) C[q * k + q] += noise;
+    for (double v : C)
+        if (!std::isfinite(v)) return fail(ctx, LGP_ERR_NONFINITE, "non-finite value in the preconditioner factor");
+    std::vector<double> Lc = C;
+    if (!host_cholesky(Lc, k)) return fail(ctx, LGP_ERR_BREAKDOWN, "preconditioner core matrix not positive definite");
+    double logdet_c = 0.0;
+    for (int q = 0; q < k; ++q) logdet_c += 2.0 * std::log(Lc[q * k + q]);
+    // C^{-1} column by column from the Cholesky factor (forward then backward substitution)
+    std::vector<double> Cinv((size_t)k * k);
+    std::vector<double> col(k);
+    for (int j = 0; j < k; ++j) {
+        for (int i = 0; i < k; ++i) {
+            double v = i == j ? 1.0 : 0.0;
+            for (int q = 0; q < i; ++q) v -= Lc[i * k + q] * col[q];
+            col[i] = v / Lc[i * k + i];
+        }
+        for (int i = k - 1; i >= 0; --i) {
+            double v = col[i];
+            for (int q = i + 1; q < k; ++q) v -= Lc[q * k + i] * col[q];
+            col[i] = v / Lc[i * k + i];
+        }
+        for (int i = 0; i < k; ++i) Cinv[i * k + j] = col[i];
+    }
+    LGP_CUDA(cudaMemcpy(ctx->pc_cinv.p, Cinv.data(), Cinv.size() * sizeof(double), cudaMemcpyHostToDevice));
+    Precond pc;
+    pc.k = k;
+    pc.Np = Np;
+    pc.L64 = L64;
+    pc.L32 = (const float *)ctx->pc_l32.p;
+    pc.Cinv = (const double *)ctx->pc_cinv.p;
+    pc.part = (double *)ctx->pc_part.p;
+    pc.U = (double *)ctx->pc_u.p;
+    pc.G = G2;
+    pc.noise = noise;
+    pc.logdet = (double)(N - k) * std::log(noise) + logdet_c;
+    *out = pc;
     return LGP_OK;
 }
 
@@ -341,7 +441,7 @@ int cg_iteration_launches(const lgp_ctx *ctx, const Prepared &pp, int t, int pre
 }
 
 lgp_status run_cg(lgp_ctx *ctx, const Prepared &pp, const float *B, int64_t ldb, int t, const lgp_options *opt,
-                  int hist_len, int prec, CgBuffers *bout, int *chunks_run = nullptr) {
+                  int hist_len, int prec, CgBuffers *bout, int *chunks_run = nullptr, const Precond *pc = nullptr) {
     cudaStream_t st = ctx->work;
     CgBuffers b;
     lgp_status s = cg_buffers(ctx, pp.N, pp.Np, t, hist_len, &b);
@@ -360,6 +460,7 @@ lgp_status run_cg(lgp_ctx *ctx, const Prepared &pp, const float *B, int64_t ldb,
     // cg_buffers/ensure may have moved memory: re-read pointers
     s = cg_buffers(ctx, pp.N, pp.Np, t, hist_len, &b);
     if (s != LGP_OK) return s;
+    if (pc) b.pc = *pc;
 
     launch_cg_init(B, ldb, pp.N, pp.Np, t, b, opt->tol, opt->max_iter, hist_len, st);
     LGP_CUDA(cudaGetLastError());
@@ -396,7 +497,15 @@ lgp_status run_cg(lgp_ctx *ctx, const Prepared &pp, const float *B, int64_t ldb,
     put(&pp.xs, sizeof pp.xs);
     put(&t, sizeof t);
     put(&prec, sizeof prec);
-    put(&b, sizeof b);
+    // the buffers field by field (the structs have padding bytes)
+    const void *ptrs[] = {b.x, b.r, b.p, b.Kp, b.z, b.partial, b.state, b.hist_alpha, b.hist_beta,
+                          b.pc.L64, b.pc.L32, b.pc.Cinv, b.pc.part, b.pc.U};
+    put(ptrs, sizeof ptrs);
+    put(&b.G, sizeof b.G);
+    put(&b.pc.k, sizeof b.pc.k);
+    put(&b.pc.G, sizeof b.pc.G);
+    put(&b.pc.Np, sizeof b.pc.Np);
+    put(&b.pc.noise, sizeof b.pc.noise);
     put(&ctx->mv_partial.p, sizeof(void *));
     put(&ctx->vsplit.p, sizeof(void *));
     put(&ctx->wait_budget, sizeof ctx->wait_budget);
@@ -561,7 +670,9 @@ void lgp_destroy(lgp_ctx *ctx) {
     cudaSetDevice(ctx->device);
     if (ctx->work) cudaStreamSynchronize(ctx->work);
     if (ctx->cg_exec) cudaGraphExecDestroy(ctx->cg_exec);
-    DevBuf *bufs[] = {&ctx->pred_xs, &ctx->pred_z, &ctx->pred_q, &ctx->xs, &ctx->mv_partial, &ctx->cg_vec, &ctx->cg_partial, &ctx->cg_state, &ctx->cg_hist,
+    DevBuf *bufs[] = {&ctx->pc_l64, &ctx->pc_l32, &ctx->pc_d, &ctx->pc_info, &ctx->pc_part, &ctx->pc_u,
+                      &ctx->pc_cinv, &ctx->pc_gram, &ctx->pc_e, &ctx->pc_rhs, &ctx->pred_xs, &ctx->pred_z,
+                      &ctx->pred_q, &ctx->xs, &ctx->mv_partial, &ctx->cg_vec, &ctx->cg_partial, &ctx->cg_state, &ctx->cg_hist,
                       &ctx->scal, &ctx->rhs, &ctx->adj_b, &ctx->adj_partial, &ctx->vsplit, &ctx->flags,
                       &ctx->batch_meta};
     for (DevBuf *b : bufs)
@@ -692,8 +803,11 @@ lgp_status lgp_cg_solve(lgp_ctx *ctx, const lgp_hyper *hyp, const float *X, cons
     LGP_CUDA(cudaMemsetAsync(ctx->flags.p, 0, 4 * sizeof(int), ctx->work));
     Prepared pp;
     if ((s = prepare_x(ctx, hyp, X, N, ctx->work, &pp)) != LGP_OK) return s;
+    Precond pc;
+    if (opt->precond_rank > 0 && (s = build_precond(ctx, hyp, X, pp, opt->precond_rank, t, &pc)) != LGP_OK) return s;
     CgBuffers b;
-    if ((s = run_cg(ctx, pp, B, t, t, opt, 0, prec, &b)) != LGP_OK) return s;
+    if ((s = run_cg(ctx, pp, B, t, t, opt, 0, prec, &b, nullptr, opt->precond_rank > 0 ? &pc : nullptr)) != LGP_OK)
+        return s;
     launch_cg_copy_out(b, N, t, Xsol, t, ctx->work);
     LGP_CUDA(cudaGetLastError());
     LGP_CUDA(cudaMemcpyAsync(ctx->h_flags, ctx->flags.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, ctx->work));
@@ -721,29 +835,50 @@ lgp_status lgp_lml_and_grad(lgp_ctx *ctx, const lgp_hyper *hyp, const float *X, 
     LGP_CUDA(cudaMemsetAsync(ctx->flags.p, 0, 4 * sizeof(int), st));
     Prepared pp;
     if ((s = prepare_x(ctx, hyp, X, N, st, &pp)) != LGP_OK) return s;
-    // right-hand-side block [y, z_1..z_m]
+    // right-hand-side block [y, z_1..z_m]: Rademacher probes, or probes with covariance P
+    // (z = L e1 + sigma e2 from a Rademacher block of N + k rows) when preconditioned
+    const int k = opt->precond_rank;
+    Precond pc;
+    if (k > 0 && (s = build_precond(ctx, hyp, X, pp, k, t, &pc)) != LGP_OK) return s;
     if ((s = ensure(ctx, ctx->rhs, (size_t)pp.Np * t * sizeof(float))) != LGP_OK) return s;
     float *rhs = (float *)ctx->rhs.p;
     launch_copy_cols(y, 1, rhs, t, N, 1, 0, st);
-    launch_rademacher(opt->seed, N, t - 1, rhs, t, 1, st);
+    if (k > 0) {
+        if ((s = ensure(ctx, ctx->pc_e, (size_t)(N + k) * (t - 1) * sizeof(float))) != LGP_OK) return s;
+        launch_rademacher(opt->seed, N + k, t - 1, (float *)ctx->pc_e.p, t - 1, 0, st);
+        launch_precond_probes(pc.L64, pc.Np, k, (const float *)ctx->pc_e.p, N, t - 1, std::sqrt(pc.noise), rhs, t, 1,
+                              st);
+    } else {
+        launch_rademacher(opt->seed, N, t - 1, rhs, t, 1, st);
+    }
     LGP_CUDA(cudaGetLastError());
     CgBuffers b;
     int chunks = 0;
-    if ((s = run_cg(ctx, pp, rhs, t, t, opt, L, prec, &b, &chunks)) != LGP_OK) return s;
+    if ((s = run_cg(ctx, pp, rhs, t, t, opt, L, prec, &b, &chunks, k > 0 ? &pc : nullptr)) != LGP_OK) return s;
+    // the probe side of the trace terms: P^{-1} z_c (z_c itself without a preconditioner); column 0 stays y
+    const float *rhs_t = rhs;
+    if (k > 0) {
+        if ((s = ensure(ctx, ctx->pc_rhs, (size_t)pp.Np * t * sizeof(float))) != LGP_OK) return s;
+        float *prhs = (float *)ctx->pc_rhs.p;
+        launch_precond_apply(b.pc, rhs, t, prhs, t, nullptr, N, t, nullptr, b.G, nullptr, st);
+        launch_copy_cols(y, 1, prhs, t, N, 1, 0, st);
+        LGP_CUDA(cudaGetLastError());
+        rhs_t = prhs;
+    }
     // scalars: dots[0..2t), slq[4], grad[D+2]
     const int G = b.G;
     if ((s = ensure(ctx, ctx->scal, (size_t)(2 * kMaxT + 4 + kMaxD + 2) * sizeof(double))) != LGP_OK) return s;
     double *dots = (double *)ctx->scal.p;
     double *slq = dots + 2 * kMaxT;
     double *gdev = slq + 4;
-    launch_col_dots(b.x, rhs, N, t, b.partial, G, dots, st);
+    launch_col_dots(b.x, rhs_t, N, t, b.partial, G, dots, st);
     launch_slq_lml(b, t, L, dots, N, slq, st);
     LGP_CUDA(cudaGetLastError());
     if (grad) {
         if ((s = ensure(ctx, ctx->adj_b, (size_t)pp.Np * t * sizeof(float))) != LGP_OK) return s;
         const int64_t pd = adjoint_partial_doubles(N, t, pp.kp.D, ctx->num_sms);
         if ((s = ensure(ctx, ctx->adj_partial, (size_t)pd * sizeof(double))) != LGP_OK) return s;
-        launch_adjoint_rhs(b.x, rhs, N, t, (float *)ctx->adj_b.p, st);
+        launch_adjoint_rhs(b.x, rhs_t, N, t, (float *)ctx->adj_b.p, st);
         int nblk = 0;
         LGP_CUDA(launch_adjoint_bilinear(pp.kp, pp.xs, N, pp.Np, b.x, (const float *)ctx->adj_b.p, t,
                                          (double *)ctx->adj_partial.p, pd, &nblk, ctx->num_sms, st));
@@ -776,9 +911,15 @@ lgp_status lgp_lml_and_grad(lgp_ctx *ctx, const lgp_hyper *hyp, const float *X, 
         // chunks the device loop ran (each: kChunk iterations + the condition kernel)
         const int ran = ctx->h_state->loop_chunks;
         info->cg_chunks = ran;
+        info->logdet_precond = k > 0 ? pc.logdet : 0.0;
         (void)chunks;
         // prep_x, y copy, probes, CG init (2), the loop's chunks, column dots (2), SLQ, adjoint (3)
-        info->launches = 3 + 2 + ran * (kChunk * cg_iteration_launches(ctx, pp, t, prec) + 1) + 2 + 1 + (grad ? 3 : 0);
+        // preconditioned: 3 more launches per iteration and in the CG init; the build (init, 2 per rank step, Gram,
+        // float32 copy), the P-distributed probes, and P^{-1} of the probe block with the y copy
+        const int pc_iter = k > 0 ? 3 : 0;
+        const int pc_once = k > 0 ? (2 * k + 3) + 3 + 1 + 4 : 0;
+        info->launches = 3 + 2 + ran * (kChunk * (cg_iteration_launches(ctx, pp, t, prec) + pc_iter) + 1) + 2 + 1 +
+                         (grad ? 3 : 0) + pc_once;
     }
     return cs;
 }
@@ -821,6 +962,11 @@ lgp_status lgp_predict(lgp_ctx *ctx, const lgp_hyper *hyp, const float *X, const
     launch_prep_x(Xs, M, pp.kp.D, pp.kp.dpad, pp.kp.scale, xs_star, Mp, (int *)ctx->flags.p, st);
     LGP_CUDA(cudaGetLastError());
 
+    Precond pc;
+    if (opt->precond_rank > 0 &&
+        (s = build_precond(ctx, hyp, X, pp, opt->precond_rank, m > 0 ? m + 1 : kChunkCols, &pc)) != LGP_OK)
+        return s;
+    const Precond *pcp = opt->precond_rank > 0 ? &pc : nullptr;
     int solves = 0, iters_max = 0, prec_first = LGP_PREC_FP32;
     double rel_max = 0.0;
     bool unconverged = false;
@@ -831,7 +977,7 @@ lgp_status lgp_predict(lgp_ctx *ctx, const lgp_hyper *hyp, const float *X, const
         prec = resolve_prec(t, prec);
         if (prec < 0) return fail(ctx, (lgp_status)prec, "precision %d unsupported for t=%d", opt->prec, t);
         if (solves == 0) prec_first = prec;
-        lgp_status r = run_cg(ctx, pp, rhs, t, t, opt, 0, prec, b);
+        lgp_status r = run_cg(ctx, pp, rhs, t, t, opt, 0, prec, b, nullptr, pcp);
         if (r != LGP_OK) return r;
         LGP_CUDA(cudaMemcpyAsync(ctx->h_flags, ctx->flags.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
         LGP_CUDA(cudaStreamSynchronize(st));

@@ -21,6 +21,7 @@ namespace lgp {
 constexpr int kMaxD = 8;
 constexpr int kMaxT = 64;
 constexpr int kMaxLanczos = 64;
+constexpr int kMaxRank = 32;  // largest pivoted-Cholesky preconditioner rank
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kTwoLn2 = 1.3862943611198906f;
 constexpr float kLn2 = 0.6931471805599453f;
@@ -140,6 +141,8 @@ struct CgState {
     int iters[kMaxT];
     double bnorm2[kMaxT];
     double rr[kMaxT];
+    double rz[kMaxT];  // r^T z with z = P^{-1} r (= rr without a preconditioner)
+    double w0[kMaxT];  // b^T P^{-1} b: the Lanczos quadrature weight of each column
     double alpha[kMaxT];
     double beta[kMaxT];
 };
@@ -215,14 +218,45 @@ int mv_tc_launches(int64_t Np, int t, int num_sms, int fmt, int forced_splits = 
 void tc_split_candidates(int64_t Np, int num_sms, int *cand, int *n);
 bool tc_symmetric_ok(int64_t Np);
 
+// precond.cu: the rank-k pivoted-Cholesky preconditioner P = L L^T + sigma^2 I (k = 0: none).
+struct Precond {
+    int k = 0;
+    int64_t Np = 0;                // row stride of the L columns
+    const double *L64 = nullptr;   // [k][Np] (column q contiguous over rows)
+    const float *L32 = nullptr;    // float32 copy used inside the CG iterations
+    const double *Cinv = nullptr;  // [k][k] inverse of C = sigma^2 I + L^T L
+    double *part = nullptr;        // [G][k t] block partials of L^T R
+    double *U = nullptr;           // [k][t] C^{-1} L^T R
+    int G = 0;                     // blocks of the L^T R reduction
+    double noise = 0.0;
+    double logdet = 0.0;           // log|P| = (N - k) log sigma^2 + log|C|
+};
+
+size_t pivinfo_bytes();
+// k pivoted-Cholesky steps of K_ff from the raw float32 X [N, D] (float64 arithmetic): L64 [k][Np], residual d [Np]
+void launch_pivchol(const float *X, int64_t N, int64_t Np, int D, const double *inv_ls_host, double s2, int kind,
+                    int k, double *L64, double *d, void *pinfo, cudaStream_t st);
+// Block partials [G][k * k] of L^T L
+void launch_gram(const double *L64, int64_t Np, int64_t N, int k, double *partial, int G, cudaStream_t st);
+void launch_to_f32(const double *src, float *dst, int64_t n, cudaStream_t st);
+// Z = P^{-1} R for rows < N (t <= 32, k t <= 1024); Pcopy (may be null) receives Z too; rz_partial (may be
+// null) gets [G_vec][t] block partials of r^T z; state (may be null) skips the work once the CG is done.
+void launch_precond_apply(const Precond &pc, const float *R, int64_t ldr, float *Z, int64_t ldz, float *Pcopy,
+                          int64_t N, int t, double *rz_partial, int G_vec, const CgState *state, cudaStream_t st);
+// rhs[:, col0 + c] = L E[N:, c] + sigma E[:N, c] for the [N + k, m] Rademacher block E
+void launch_precond_probes(const double *L64, int64_t Np, int k, const float *E, int64_t N, int m, double sigma,
+                           float *rhs, int64_t ldr, int col0, cudaStream_t st);
+
 // solver.cu
 struct CgBuffers {
     float *x, *r, *p, *Kp;   // [Np, t]
+    float *z;                // [Np, t] P^{-1} r (preconditioned solves only)
     double *partial;         // [G, 2t] block partial dots
     int G;                   // blocks of the vector kernels
     CgState *state;
     double *hist_alpha;      // [hist_len, t]
     double *hist_beta;       // [hist_len, t]
+    Precond pc;              // pc.k == 0: plain CG
 };
 void launch_cg_init(const float *B, int64_t ldb, int64_t N, int64_t Np, int t, const CgBuffers &b, double tol,
                     int max_iter, int hist_len, cudaStream_t st);

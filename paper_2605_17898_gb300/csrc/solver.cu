@@ -1,12 +1,13 @@
 // Conjugate-gradient vector updates, float64 scalar recurrences, stochastic Lanczos
 // quadrature and the LML / gradient assembly.
 //
-// CG (Sec. 2 "CG-based inference"; Sec. 5 "our simpler CG loop"): unpreconditioned,
-// x0 = 0, one recurrence per right-hand-side column, all columns advanced by the
-// same launches. Per iteration, after Kp = K_y p:
-//   alpha_c = r_c^T r_c / p_c^T Kp_c,  x_c += alpha_c p_c,  r_c -= alpha_c Kp_c,
-//   beta_c  = r_c'^T r_c' / r_c^T r_c, p_c = r_c' + beta_c p_c,
-// column c stops once ||r_c|| <= tol ||b_c||. Vectors are float32; the dot products
+// CG (Sec. 2 "CG-based inference"; Sec. 5 "our simpler CG loop"): x0 = 0, one recurrence per
+// right-hand-side column, all columns advanced by the same launches. Per iteration, after
+// Kp = K_y p, with z = P^{-1} r (z = r without a preconditioner):
+//   alpha_c = r_c^T z_c / p_c^T Kp_c,  x_c += alpha_c p_c,  r_c -= alpha_c Kp_c,
+//   z_c' = P^{-1} r_c',  beta_c = r_c'^T z_c' / r_c^T z_c,  p_c = z_c' + beta_c p_c,
+// column c stops once ||r_c|| <= tol ||b_c||. The optional preconditioner is the pivoted-Cholesky
+// P of precond.cu (the gap Sec. 5 names; plain CG is the paper's loop). Vectors are float32; the dot products
 // are accumulated in float64 with a fixed reduction order (block partials, then one
 // block sums them in index order), so results are reproducible run to run.
 #include <math.h>
@@ -74,21 +75,24 @@ __global__ void cg_init_kernel(const float *__restrict__ B, int64_t ldb, int64_t
 
 // Scalar kernels run as one block of 32 * min(t, 32) threads: warp w owns columns w, w + 32.
 __global__ void cg_init_scalars_kernel(CgState *st, const double *__restrict__ partial, int G, int t, double tol,
-                                       int max_iter, int hist_len) {
+                                       int max_iter, int hist_len, const double *__restrict__ rz_partial) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     int any = 0;
     int bad = 0;
     for (int c = warp; c < t; c += nw) {
         const double s = warp_sum_partials(partial, G, t, c);
+        const double rz = rz_partial ? warp_sum_partials(rz_partial, G, t, c) : s;
         if (lane != 0) continue;
         st->bnorm2[c] = s;
         st->rr[c] = s;
+        st->rz[c] = rz;
+        st->w0[c] = rz;
         st->alpha[c] = 0.0;
         st->beta[c] = 0.0;
         st->iters[c] = 0;
-        const int b_ = !isfinite(s);
+        const int b_ = !isfinite(s) || !isfinite(rz);
         bad |= b_;
-        const int act = (s > 0.0) && !b_;
+        const int act = (s > 0.0) && (rz > 0.0) && !b_;
         st->active[c] = act;
         any |= act;
     }
@@ -137,7 +141,7 @@ __global__ void cg_alpha_kernel(CgState *st, const double *__restrict__ partial,
                 bad = 1;
                 st->active[c] = 0;
             } else {
-                alpha = st->rr[c] / pkp;
+                alpha = st->rz[c] / pkp;
             }
         }
         if (lane != 0) continue;
@@ -173,7 +177,8 @@ __global__ void cg_xr_kernel(float *__restrict__ x, float *__restrict__ r, const
     block_col_reduce(s, t, red, partial + (int64_t)blockIdx.x * t);
 }
 
-__global__ void cg_beta_kernel(CgState *st, const double *__restrict__ partial, int G, double *hist_beta) {
+__global__ void cg_beta_kernel(CgState *st, const double *__restrict__ partial, int G, double *hist_beta,
+                               const double *__restrict__ rz_partial) {
     if (st->done) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const int t = st->t;
@@ -182,9 +187,11 @@ __global__ void cg_beta_kernel(CgState *st, const double *__restrict__ partial, 
         double beta = 0.0;
         if (st->active[c]) {
             const double rr = warp_sum_partials(partial, G, t, c);
+            const double rz = rz_partial ? warp_sum_partials(rz_partial, G, t, c) : rr;
             if (lane != 0) continue;
-            beta = rr / st->rr[c];
+            beta = rz / st->rz[c];
             st->rr[c] = rr;
+            st->rz[c] = rz;
             st->iters[c] += 1;
             if (!(sqrt(rr) > st->tol * sqrt(st->bnorm2[c]))) st->active[c] = 0;
         }
@@ -318,10 +325,11 @@ __device__ double tridiag_e1_log_e1(double *a, double *b, double *u, int m, int 
 
 // One thread per probe column c = 1..t-1: T_c from the CG coefficients
 // (T[k,k] = 1/alpha_k + beta_{k-1}/alpha_{k-1}, T[k,k+1] = sqrt(beta_k)/alpha_k),
-// gamma_c = ||z_c||^2 e_1^T log(T_c) e_1; logdet = mean_c gamma_c (Sec. 3 "Inference").
+// gamma_c = w_c e_1^T log(T_c) e_1 with w_c = z_c^T P^{-1} z_c (||z_c||^2 without a preconditioner);
+// logdet = logdet_P + mean_c gamma_c (Sec. 3 "Inference"; logdet_P = log|P|, 0 without one).
 __global__ void slq_lml_kernel(const CgState *st, const double *__restrict__ hist_alpha,
                                const double *__restrict__ hist_beta, int t, int hist_len,
-                               const double *__restrict__ dots, int64_t N, double *out) {
+                               const double *__restrict__ dots, int64_t N, double logdet_p, double *out) {
     __shared__ double gam[kMaxT];
     __shared__ int flag[kMaxT];
     const int c = threadIdx.x;
@@ -337,7 +345,7 @@ __global__ void slq_lml_kernel(const CgState *st, const double *__restrict__ his
                 if (k > 0) a[k] += hist_beta[(int64_t)(k - 1) * t + c] / hist_alpha[(int64_t)(k - 1) * t + c];
                 if (k + 1 < m) b[k] = sqrt(hist_beta[(int64_t)k * t + c]) / al;
             }
-            g = st->bnorm2[c] * tridiag_e1_log_e1(a, b, u, m, &nonpos);
+            g = st->w0[c] * tridiag_e1_log_e1(a, b, u, m, &nonpos);
         }
         gam[c] = g;
         flag[c] = nonpos;
@@ -350,7 +358,7 @@ __global__ void slq_lml_kernel(const CgState *st, const double *__restrict__ his
             s += gam[k];
             bad |= flag[k];
         }
-        const double logdet = t > 1 ? s / (t - 1) : 0.0;
+        const double logdet = logdet_p + (t > 1 ? s / (t - 1) : 0.0);
         const double quad = dots[0];
         out[0] = -0.5 * (quad + logdet + (double)N * 1.8378770664093453);  // log(2 pi)
         out[1] = quad;
@@ -403,7 +411,14 @@ void launch_cg_init(const float *B, int64_t ldb, int64_t N, int64_t Np, int t, c
                     int max_iter, int hist_len, cudaStream_t st) {
     (void)Np;
     cg_init_kernel<<<b.G, vec_block(t), 0, st>>>(B, ldb, N, t, b.x, b.r, b.p, b.partial);
-    cg_init_scalars_kernel<<<1, 32 * (t < 32 ? t : 32), 0, st>>>(b.state, b.partial, b.G, t, tol, max_iter, hist_len);
+    double *rz_partial = nullptr;
+    if (b.pc.k > 0) {
+        // z0 = P^{-1} b, p0 = z0, and the r^T z partials in the second half of the partial buffer
+        rz_partial = b.partial + (int64_t)b.G * t;
+        launch_precond_apply(b.pc, b.r, t, b.z, t, b.p, N, t, rz_partial, b.G, nullptr, st);
+    }
+    cg_init_scalars_kernel<<<1, 32 * (t < 32 ? t : 32), 0, st>>>(b.state, b.partial, b.G, t, tol, max_iter, hist_len,
+                                                                 rz_partial);
 }
 
 void launch_cg_after_matvec(int64_t N, int64_t Np, int t, const CgBuffers &b, cudaStream_t st) {
@@ -413,8 +428,13 @@ void launch_cg_after_matvec(int64_t N, int64_t Np, int t, const CgBuffers &b, cu
     const int sb = 32 * (t < 32 ? t : 32);
     cg_alpha_kernel<<<1, sb, 0, st>>>(b.state, b.partial, b.G, b.hist_alpha);
     cg_xr_kernel<<<b.G, bd, 0, st>>>(b.x, b.r, b.p, b.Kp, N, t, b.state, b.partial);
-    cg_beta_kernel<<<1, sb, 0, st>>>(b.state, b.partial, b.G, b.hist_beta);
-    cg_p_kernel<<<b.G, bd, 0, st>>>(b.p, b.r, N, t, b.state);
+    double *rz_partial = nullptr;
+    if (b.pc.k > 0) {
+        rz_partial = b.partial + (int64_t)b.G * t;
+        launch_precond_apply(b.pc, b.r, t, b.z, t, nullptr, N, t, rz_partial, b.G, b.state, st);
+    }
+    cg_beta_kernel<<<1, sb, 0, st>>>(b.state, b.partial, b.G, b.hist_beta, rz_partial);
+    cg_p_kernel<<<b.G, bd, 0, st>>>(b.p, b.pc.k > 0 ? b.z : b.r, N, t, b.state);
 }
 
 void launch_cg_loop_condition(cudaGraphConditionalHandle h, CgState *state, cudaStream_t st) {
@@ -435,7 +455,8 @@ void launch_col_dots(const float *A, const float *B, int64_t N, int t, double *p
 
 void launch_slq_lml(const CgBuffers &b, int t, int hist_len, const double *dots, int64_t N, double *out,
                     cudaStream_t st) {
-    slq_lml_kernel<<<1, kMaxT, 0, st>>>(b.state, b.hist_alpha, b.hist_beta, t, hist_len, dots, N, out);
+    slq_lml_kernel<<<1, kMaxT, 0, st>>>(b.state, b.hist_alpha, b.hist_beta, t, hist_len, dots, N,
+                                        b.pc.k > 0 ? b.pc.logdet : 0.0, out);
 }
 
 void launch_adjoint_rhs(const float *A, const float *RHS, int64_t N, int t, float *Bp, cudaStream_t st) {

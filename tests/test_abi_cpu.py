@@ -72,8 +72,8 @@ def test_create_without_gpu_fails_cleanly(lib):
 def test_struct_layouts_are_packed_as_in_c():
     import paper_2605_17898_gb300 as pkg
     assert ctypes.sizeof(pkg.lgp_hyper) == 24
-    assert ctypes.sizeof(pkg.lgp_options) == 32
-    assert ctypes.sizeof(pkg.lgp_lml_info) == 56
+    assert ctypes.sizeof(pkg.lgp_options) == 40
+    assert ctypes.sizeof(pkg.lgp_lml_info) == 64
     assert ctypes.sizeof(pkg.lgp_predict_info) == 24
 
 
