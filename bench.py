@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--mode", choices=["lml", "matvec", "predict"], default="lml",
                     help="lml: the LML+grad step (default); matvec: only the product, for kernel profiling; "
                          "predict: posterior mean and variance at --M test points")
+    ap.add_argument("--precond-rank", type=int, default=0,
+                    help="pivoted-Cholesky preconditioner rank of the CG solves (0: the paper's plain CG)")
     ap.add_argument("--M", type=int, default=10000, help="test points of --mode predict")
     ap.add_argument("--var-probes", type=int, default=31,
                     help="--mode predict: probes of the variance estimate (0: exact per-point variance)")
@@ -290,7 +292,8 @@ def main():
 
     def step(Xd, yd):
         return lgp.lgp_lml_and_grad(Xd, yd, p, n_probes=m, lanczos_steps=args.lanczos, seed=1234 + rank,
-                                    tol=args.tol, max_iter=args.max_iter, prec=prec, ctx=ctx)
+                                    tol=args.tol, max_iter=args.max_iter, prec=prec, ctx=ctx,
+                                    precond_rank=args.precond_rank)
 
     for _ in range(args.warmup):
         step(X, y)
@@ -421,6 +424,7 @@ def main():
             "config": {"workload": p.name, "N": p.N, "D": p.D, "t": args.t, "kernel": "matern52",
                        "tc_kernel": kname,
                        "lanczos_steps": args.lanczos, "tol": args.tol, "max_iter": args.max_iter,
+                       "precond_rank": args.precond_rank,
                        "cg_iterations": iters,
                        "precision": {1: "fp32", 2: "split_bf16", 3: "split_f16"}.get(kprec, str(kprec)),
                        "l2": "flushed between steps (256 MB write outside the step events)",
@@ -447,7 +451,7 @@ def bench_predict(lgp, ctx, p, args, dev, prec, rank):
 
     def step():
         return lgp.lgp_predict(X, y, p, Xs, n_probes=args.var_probes, seed=99, tol=args.tol,
-                               max_iter=args.max_iter, prec=prec, ctx=ctx)
+                               max_iter=args.max_iter, prec=prec, ctx=ctx, precond_rank=args.precond_rank)
 
     for _ in range(args.warmup):
         step()
