@@ -99,8 +99,13 @@ typedef struct {
     int32_t precond_rank;    /* 0: plain CG (the paper's loop); k in 1..32: CG preconditioned by
                                 P = L L^T + sigma_n^2 I, L the rank-k pivoted Cholesky factor of K_ff
                                 (solves of at most 32 columns) */
-    int32_t reserved;        /* set to 0 */
+    int32_t flags;           /* LGP_OPT_* bits, 0 for the defaults */
 } lgp_options;
+
+/* lgp_options.flags: lgp_cg_solve starts from the initial guess held in Xsol on entry instead of
+ * x0 = 0 (a warm start, e.g. from the previous optimiser step's solution); columns whose initial
+ * residual already meets tol take no iteration. Ignored by the other entry points. */
+enum { LGP_OPT_WARM_START = 1 };
 
 typedef struct {
     double lml;              /* log marginal likelihood estimate */

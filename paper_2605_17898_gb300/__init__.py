@@ -61,7 +61,7 @@ class lgp_hyper(ctypes.Structure):
 class lgp_options(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("lanczos_steps", ctypes.c_int32),
                 ("n_probes", ctypes.c_int32), ("prec", ctypes.c_int32), ("seed", ctypes.c_uint64),
-                ("precond_rank", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("precond_rank", ctypes.c_int32), ("flags", ctypes.c_int32)]
 
 
 class lgp_lml_info(ctypes.Structure):
@@ -295,14 +295,19 @@ def lgp_kernel_matvec_grad(X, hyp, W, ctx: Context | None = None, stream=None):
     return G
 
 
-def _options(tol, max_iter, lanczos_steps=0, n_probes=0, prec=LGP_PREC_AUTO, seed=0, precond_rank=0) -> lgp_options:
+LGP_OPT_WARM_START = 1
+
+
+def _options(tol, max_iter, lanczos_steps=0, n_probes=0, prec=LGP_PREC_AUTO, seed=0, precond_rank=0,
+             flags=0) -> lgp_options:
     return lgp_options(float(tol), int(max_iter), int(lanczos_steps), int(n_probes), int(prec),
-                       int(seed) & ((1 << 64) - 1), int(precond_rank), 0)
+                       int(seed) & ((1 << 64) - 1), int(precond_rank), int(flags))
 
 
 def lgp_cg_solve(X, hyp, B, tol: float = 1e-6, max_iter: int = 1000, prec: int = LGP_PREC_AUTO,
-                 ctx: Context | None = None, stream=None, out=None, precond_rank: int = 0):
-    """Solve K_y Xsol = B by batched CG. Returns (Xsol, iters[t], rel_resid[t], status)."""
+                 ctx: Context | None = None, stream=None, out=None, precond_rank: int = 0, x0=None):
+    """Solve K_y Xsol = B by batched CG. x0 (optional, [N, t] like B): warm start from that initial guess.
+    Returns (Xsol, iters[t], rel_resid[t], status)."""
     import torch
     ctx = ctx or default_context(X.device.index or 0)
     squeeze = B.dim() == 1
@@ -310,10 +315,13 @@ def lgp_cg_solve(X, hyp, B, tol: float = 1e-6, max_iter: int = 1000, prec: int =
     N, t = B2.shape
     if out is None:
         out = torch.empty((N, t), device=B.device, dtype=torch.float32)
+    if x0 is not None:
+        out.copy_(x0.reshape(N, t))
     iters = np.zeros(t, dtype=np.int32)
     rel = np.zeros(t, dtype=np.float64)
     h, keep = Hyper.of(hyp).to_c()
-    o = _options(tol, max_iter, prec=prec, precond_rank=precond_rank)
+    o = _options(tol, max_iter, prec=prec, precond_rank=precond_rank,
+                 flags=LGP_OPT_WARM_START if x0 is not None else 0)
     s = ctx._check(ctx.lib.lgp_cg_solve(ctx.h, ctypes.byref(h), _ptr(X), _ptr(B2), _ptr(out), int(N), int(t),
                                         ctypes.byref(o), iters.ctypes.data_as(ctypes.c_void_p),
                                         rel.ctypes.data_as(ctypes.c_void_p), _stream_ptr(stream)))

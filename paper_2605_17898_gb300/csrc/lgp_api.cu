@@ -317,7 +317,7 @@ lgp_status cg_buffers(lgp_ctx *ctx, int64_t N, int64_t Np, int t, int hist_len, 
     lgp_status s;
     if ((s = ensure(ctx, ctx->cg_vec, (size_t)5 * Np * t * sizeof(float))) != LGP_OK) return s;
     b->G = cg_num_blocks(N, t, ctx->num_sms);
-    if ((s = ensure(ctx, ctx->cg_partial, (size_t)b->G * 2 * t * sizeof(double))) != LGP_OK) return s;
+    if ((s = ensure(ctx, ctx->cg_partial, (size_t)b->G * 3 * t * sizeof(double))) != LGP_OK) return s;
     if ((s = ensure(ctx, ctx->cg_state, sizeof(CgState))) != LGP_OK) return s;
     if ((s = ensure(ctx, ctx->cg_hist, (size_t)2 * std::max(hist_len, 1) * t * sizeof(double))) != LGP_OK) return s;
     float *v = (float *)ctx->cg_vec.p;
@@ -441,7 +441,8 @@ int cg_iteration_launches(const lgp_ctx *ctx, const Prepared &pp, int t, int pre
 }
 
 lgp_status run_cg(lgp_ctx *ctx, const Prepared &pp, const float *B, int64_t ldb, int t, const lgp_options *opt,
-                  int hist_len, int prec, CgBuffers *bout, int *chunks_run = nullptr, const Precond *pc = nullptr) {
+                  int hist_len, int prec, CgBuffers *bout, int *chunks_run = nullptr, const Precond *pc = nullptr,
+                  const float *X0 = nullptr) {
     cudaStream_t st = ctx->work;
     CgBuffers b;
     lgp_status s = cg_buffers(ctx, pp.N, pp.Np, t, hist_len, &b);
@@ -462,7 +463,11 @@ lgp_status run_cg(lgp_ctx *ctx, const Prepared &pp, const float *B, int64_t ldb,
     if (s != LGP_OK) return s;
     if (pc) b.pc = *pc;
 
-    launch_cg_init(B, ldb, pp.N, pp.Np, t, b, opt->tol, opt->max_iter, hist_len, st);
+    if (X0) {
+        // warm start: r0 = b - K_y x0 needs one product first (into Kp)
+        if ((s = matvec_prepared(ctx, pp, X0, t, b.Kp, t, t, prec, nullptr, st)) != LGP_OK) return s;
+    }
+    launch_cg_init(B, ldb, pp.N, pp.Np, t, b, opt->tol, opt->max_iter, hist_len, st, X0, t);
     LGP_CUDA(cudaGetLastError());
 
     const char *graph_env = std::getenv("LGP_CG_GRAPH");
@@ -806,7 +811,8 @@ lgp_status lgp_cg_solve(lgp_ctx *ctx, const lgp_hyper *hyp, const float *X, cons
     Precond pc;
     if (opt->precond_rank > 0 && (s = build_precond(ctx, hyp, X, pp, opt->precond_rank, t, &pc)) != LGP_OK) return s;
     CgBuffers b;
-    if ((s = run_cg(ctx, pp, B, t, t, opt, 0, prec, &b, nullptr, opt->precond_rank > 0 ? &pc : nullptr)) != LGP_OK)
+    const float *x0 = (opt->flags & LGP_OPT_WARM_START) ? Xsol : nullptr;
+    if ((s = run_cg(ctx, pp, B, t, t, opt, 0, prec, &b, nullptr, opt->precond_rank > 0 ? &pc : nullptr, x0)) != LGP_OK)
         return s;
     launch_cg_copy_out(b, N, t, Xsol, t, ctx->work);
     LGP_CUDA(cudaGetLastError());

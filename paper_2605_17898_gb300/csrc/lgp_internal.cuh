@@ -251,15 +251,16 @@ void launch_precond_probes(const double *L64, int64_t Np, int k, const float *E,
 struct CgBuffers {
     float *x, *r, *p, *Kp;   // [Np, t]
     float *z;                // [Np, t] P^{-1} r (preconditioned solves only)
-    double *partial;         // [G, 2t] block partial dots
+    double *partial;         // [G, 3t] block partial dots
     int G;                   // blocks of the vector kernels
     CgState *state;
     double *hist_alpha;      // [hist_len, t]
     double *hist_beta;       // [hist_len, t]
     Precond pc;              // pc.k == 0: plain CG
 };
+// X0 (may be null): warm start x0 [N, ldx0], with K_y x0 already in b.Kp.
 void launch_cg_init(const float *B, int64_t ldb, int64_t N, int64_t Np, int t, const CgBuffers &b, double tol,
-                    int max_iter, int hist_len, cudaStream_t st);
+                    int max_iter, int hist_len, cudaStream_t st, const float *X0 = nullptr, int64_t ldx0 = 0);
 void launch_cg_after_matvec(int64_t N, int64_t Np, int t, const CgBuffers &b, cudaStream_t st);
 void launch_cg_copy_out(const CgBuffers &b, int64_t N, int t, float *Xsol, int64_t ldx, cudaStream_t st);
 // Body tail of the device-side CG loop: sets the while-node condition to "not done and under the chunk cap".

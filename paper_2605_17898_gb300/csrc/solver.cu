@@ -73,26 +73,54 @@ __global__ void cg_init_kernel(const float *__restrict__ B, int64_t ldb, int64_t
     block_col_reduce(s, t, red, partial + (int64_t)blockIdx.x * t);
 }
 
+// Warm start: x = x0, r = b - K_y x0 (KX0 = K_y x0 computed before), p = r; block partials of
+// b^T b (partial) and r^T r (rr_partial).
+__global__ void cg_init_x0_kernel(const float *__restrict__ B, int64_t ldb, const float *__restrict__ X0, int64_t ldx0,
+                                  const float *__restrict__ KX0, int64_t N, int t, float *__restrict__ x,
+                                  float *__restrict__ r, float *__restrict__ p, double *__restrict__ partial,
+                                  double *__restrict__ rr_partial) {
+    __shared__ double red[kVecThreads];
+    int64_t r0, r1;
+    block_rows(N, &r0, &r1);
+    const int c = threadIdx.x % t;
+    double sb = 0.0, sr = 0.0;
+    for (int64_t i = r0 + threadIdx.x / t; i < r1; i += blockDim.x / t) {
+        const float b = B[i * ldb + c];
+        const float rv = b - KX0[i * t + c];
+        x[i * t + c] = X0[i * ldx0 + c];
+        r[i * t + c] = rv;
+        p[i * t + c] = rv;
+        sb += (double)b * (double)b;
+        sr += (double)rv * (double)rv;
+    }
+    block_col_reduce(sb, t, red, partial + (int64_t)blockIdx.x * t);
+    __syncthreads();
+    block_col_reduce(sr, t, red, rr_partial + (int64_t)blockIdx.x * t);
+}
+
 // Scalar kernels run as one block of 32 * min(t, 32) threads: warp w owns columns w, w + 32.
 __global__ void cg_init_scalars_kernel(CgState *st, const double *__restrict__ partial, int G, int t, double tol,
-                                       int max_iter, int hist_len, const double *__restrict__ rz_partial) {
+                                       int max_iter, int hist_len, const double *__restrict__ rz_partial,
+                                       const double *__restrict__ rr_partial) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     int any = 0;
     int bad = 0;
     for (int c = warp; c < t; c += nw) {
         const double s = warp_sum_partials(partial, G, t, c);
-        const double rz = rz_partial ? warp_sum_partials(rz_partial, G, t, c) : s;
+        const double rr0 = rr_partial ? warp_sum_partials(rr_partial, G, t, c) : s;
+        const double rz = rz_partial ? warp_sum_partials(rz_partial, G, t, c) : rr0;
         if (lane != 0) continue;
         st->bnorm2[c] = s;
-        st->rr[c] = s;
+        st->rr[c] = rr0;
         st->rz[c] = rz;
         st->w0[c] = rz;
         st->alpha[c] = 0.0;
         st->beta[c] = 0.0;
         st->iters[c] = 0;
-        const int b_ = !isfinite(s) || !isfinite(rz);
+        const int b_ = !isfinite(s) || !isfinite(rz) || !isfinite(rr0);
         bad |= b_;
-        const int act = (s > 0.0) && (rz > 0.0) && !b_;
+        // a warm start that already meets the tolerance leaves the column inactive
+        const int act = (s > 0.0) && (rz > 0.0) && !b_ && (sqrt(rr0) > tol * sqrt(s));
         st->active[c] = act;
         any |= act;
     }
@@ -408,9 +436,17 @@ int cg_num_blocks(int64_t N, int t, int num_sms) {
 }
 
 void launch_cg_init(const float *B, int64_t ldb, int64_t N, int64_t Np, int t, const CgBuffers &b, double tol,
-                    int max_iter, int hist_len, cudaStream_t st) {
+                    int max_iter, int hist_len, cudaStream_t st, const float *X0, int64_t ldx0) {
     (void)Np;
-    cg_init_kernel<<<b.G, vec_block(t), 0, st>>>(B, ldb, N, t, b.x, b.r, b.p, b.partial);
+    double *rr_partial = nullptr;
+    if (X0) {
+        // b.Kp holds K_y x0; the r^T r partials go to the third slot of the partial buffer
+        rr_partial = b.partial + (int64_t)2 * b.G * t;
+        cg_init_x0_kernel<<<b.G, vec_block(t), 0, st>>>(B, ldb, X0, ldx0, b.Kp, N, t, b.x, b.r, b.p, b.partial,
+                                                        rr_partial);
+    } else {
+        cg_init_kernel<<<b.G, vec_block(t), 0, st>>>(B, ldb, N, t, b.x, b.r, b.p, b.partial);
+    }
     double *rz_partial = nullptr;
     if (b.pc.k > 0) {
         // z0 = P^{-1} b, p0 = z0, and the r^T z partials in the second half of the partial buffer
@@ -418,7 +454,7 @@ void launch_cg_init(const float *B, int64_t ldb, int64_t N, int64_t Np, int t, c
         launch_precond_apply(b.pc, b.r, t, b.z, t, b.p, N, t, rz_partial, b.G, nullptr, st);
     }
     cg_init_scalars_kernel<<<1, 32 * (t < 32 ? t : 32), 0, st>>>(b.state, b.partial, b.G, t, tol, max_iter, hist_len,
-                                                                 rz_partial);
+                                                                 rz_partial, rr_partial);
 }
 
 void launch_cg_after_matvec(int64_t N, int64_t Np, int t, const CgBuffers &b, cudaStream_t st) {
