@@ -86,6 +86,20 @@ def barrier(world):
         dist.barrier()
 
 
+def job_rate(local_units, local_seconds, world, device):
+    """Whole-job throughput: the units every rank processed over the slowest rank's time.
+    Returns (rate, max seconds)."""
+    if world == 1:
+        return local_units / local_seconds, local_seconds
+    import torch
+    import torch.distributed as dist
+    u = torch.tensor([float(local_units)], dtype=torch.float64, device=device)
+    s = torch.tensor([float(local_seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(s, op=dist.ReduceOp.MAX)
+    return float(u.item()) / float(s.item()), float(s.item())
+
+
 def max_over_ranks(x, world, device):
     if world == 1:
         return x
@@ -262,10 +276,11 @@ def bench_reference(args, rank, world):
 
 def main():
     args = parse()
-    rank, world, local = dist_init(args.gpus)
     if args.impl == "reference":
-        bench_reference(args, rank, world)
+        # the oracle runs on rank 0's host cores only; no process group is needed
+        bench_reference(args, int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")))
         return
+    rank, world, local = dist_init(args.gpus)
     import numpy as np
     import torch
     import paper_2605_17898_gb300 as lgp
@@ -316,7 +331,6 @@ def main():
     barrier(world)
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     local_total_s = sum(step_ms) / 1e3
-    total_s = max_over_ranks(local_total_s, world, dev)
     clocks = sampler.stop() if sampler else None
 
     iters = [i["iters_max"] for i in infos]
@@ -326,7 +340,8 @@ def main():
     pairs_rhs = [(n + 1) * float(p.N) ** 2 * args.t for n in n_products]
     # useful work only: products of iterations that ran (later iterations of a chunk exit early)
     useful = [(it + 1) * float(p.N) ** 2 * args.t for it in iters]
-    value = sum(useful) * world / total_s
+    # whole job: every rank's useful products over the slowest rank's time
+    value, total_s = job_rate(sum(useful), local_total_s, world, dev)
     ms_per_step = 1e3 * total_s / args.steps
     launches = int(sum(i["launches"] for i in infos))
 
@@ -399,9 +414,10 @@ def main():
         torch.cuda.synchronize()
         e2e_ms.append(a.elapsed_time(b))
         e2e_iters.append(info_e["iters_max"])
-    e2e_value = statistics.mean((it + 1) * float(p.N) ** 2 * args.t / (ms / 1e3)
-                                for it, ms in zip(e2e_iters, e2e_ms)) * world
-    cg_state_bytes = 2592
+    e2e_value, _ = job_rate(sum((it + 1) * float(p.N) ** 2 * args.t for it in e2e_iters), sum(e2e_ms) / 1e3,
+                            world, dev)
+    # the CG state read back per step: 8 int32 + 1 float64, 2 x 64 int32, 6 x 64 float64
+    cg_state_bytes = 8 * 4 + 8 + 2 * 64 * 4 + 6 * 64 * 8
     d2h = cg_state_bytes + (2 * 64 + 4 + 10) * 8 + 16 + 4 * statistics.mean(chunks)
     e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(Xh.numel() * 4 + yh.numel() * 4),
            "d2h_bytes_per_step": int(d2h), "ms_per_step": statistics.mean(e2e_ms)}
