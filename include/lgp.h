@@ -145,6 +145,8 @@ const char *lgp_status_string(int32_t status);
  *   LGP_TC_SYMMETRIC=1  force the symmetric-tile tensor-core kernel (shapes with N > 768);
  *                       =0 never use it. It adds its tiles' contributions with float32
  *                       atomic reductions, so its last bits can vary between runs;
+ *   LGP_AUTOTUNE_CACHE=<file>  keep the autotuner's choices in a text file (one line per device and
+ *                       shape, appended after tuning), so later processes skip the timing runs;
  *   LGP_CG_GRAPH=0      run the CG iteration loop from the host (one launch per kernel, the
  *                       done flag read back every 8 iterations) instead of one CUDA graph with
  *                       a device-side while loop; meant for profilers. */

@@ -12,6 +12,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "batch.cuh"
 #include "lgp_internal.cuh"
 
@@ -57,6 +59,16 @@ struct lgp_ctx {
 };
 
 namespace {
+
+// NVTX range over the host-side part of a call (no-op unless a profiler is attached), so that a
+// timeline shows the library's phases: entry points, input preparation, autotuning, the
+// preconditioner build and the CG loop.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 lgp_status fail(lgp_ctx *c, lgp_status s, const char *fmt, ...) __attribute__((format(printf, 3, 4)));
 lgp_status fail(lgp_ctx *c, lgp_status s, const char *fmt, ...) {
@@ -174,6 +186,7 @@ struct Prepared {
 };
 
 lgp_status prepare_x(lgp_ctx *ctx, const lgp_hyper *hyp, const float *X, int64_t N, cudaStream_t st, Prepared *pp) {
+    NvtxRange nvtx_range("lgp.prepare_x");
     lgp_status s = make_params(ctx, hyp, &pp->kp);
     if (s != LGP_OK) return s;
     pp->N = N;
@@ -203,8 +216,45 @@ int tc_splits_for(const lgp_ctx *ctx, const Prepared &pp, int t, int prec) {
 // stream) and keep the fastest for that shape. Never runs during a stream capture.
 // LGP_AUTOTUNE=0 keeps the row kernel's wave-efficiency heuristic; LGP_TC_SYMMETRIC=1 forces the
 // symmetric kernel (where the shape allows it), LGP_TC_SYMMETRIC=0 leaves it out.
+// Persistent autotune cache (LGP_AUTOTUNE_CACHE=<file>): one text line per tuned shape,
+// "<device name>|<SMs>|<Np>|<t>|<fmt>|<D>|<kind> <choice>", read before timing and appended after.
+std::string tune_cache_key(const lgp_ctx *ctx, const std::vector<int64_t> &key) {
+    cudaDeviceProp prop;
+    std::string name = cudaGetDeviceProperties(&prop, ctx->device) == cudaSuccess ? prop.name : "unknown";
+    for (char &c : name)
+        if (c == '|' || c == ' ') c = '_';
+    std::string k = name + "|" + std::to_string(ctx->num_sms);
+    for (int64_t v : key) k += "|" + std::to_string(v);
+    return k;
+}
+
+bool tune_cache_lookup(const char *path, const std::string &k, int *choice) {
+    FILE *f = std::fopen(path, "r");
+    if (!f) return false;
+    char line[512];
+    bool found = false;
+    while (std::fgets(line, sizeof line, f)) {
+        char name[400];
+        int v = 0;
+        if (std::sscanf(line, "%399s %d", name, &v) == 2 && k == name) {
+            *choice = v;  // the last entry for a key wins
+            found = true;
+        }
+    }
+    std::fclose(f);
+    return found;
+}
+
+void tune_cache_store(const char *path, const std::string &k, int choice) {
+    FILE *f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "%s %d\n", k.c_str(), choice);
+    std::fclose(f);
+}
+
 lgp_status autotune_tc(lgp_ctx *ctx, const Prepared &pp, const float *V, int64_t ldv, float *out, int64_t ldo, int t,
                        int prec, cudaStream_t st) {
+    NvtxRange nvtx_range("lgp.autotune");
     const std::vector<int64_t> key = tc_key(pp, t, prec);
     if (ctx->tc_splits.count(key)) return LGP_OK;
     const char *env = std::getenv("LGP_AUTOTUNE");
@@ -222,6 +272,17 @@ lgp_status autotune_tc(lgp_ctx *ctx, const Prepared &pp, const float *V, int64_t
     if ((env && env[0] == '0') || n <= 1) {
         ctx->tc_splits[key] = 0;
         return LGP_OK;
+    }
+    const char *cache_path = std::getenv("LGP_AUTOTUNE_CACHE");
+    const std::string cache_key = cache_path ? tune_cache_key(ctx, key) : std::string();
+    int cached = 0;
+    if (cache_path && tune_cache_lookup(cache_path, cache_key, &cached)) {
+        bool allowed = false;
+        for (int k = 0; k < n; ++k) allowed |= cand[k] == cached;
+        if (allowed) {
+            ctx->tc_splits[key] = cached;
+            return LGP_OK;
+        }
     }
     int64_t need = 1;
     for (int k = 0; k < n; ++k) need = std::max(need, mv_tc_partial_floats(pp.Np, t, ctx->num_sms, cand[k]));
@@ -257,6 +318,7 @@ lgp_status autotune_tc(lgp_ctx *ctx, const Prepared &pp, const float *V, int64_t
     cudaEventDestroy(e1);
     if (ce != cudaSuccess) return fail(ctx, LGP_ERR_CUDA, "autotune launch failed: %s", cudaGetErrorString(ce));
     ctx->tc_splits[key] = best;
+    if (cache_path) tune_cache_store(cache_path, cache_key, best);
     return LGP_OK;
 }
 
@@ -358,6 +420,7 @@ bool host_cholesky(std::vector<double> &A, int n) {
 // Synchronises the internal stream once.
 lgp_status build_precond(lgp_ctx *ctx, const lgp_hyper *hyp, const float *X, const Prepared &pp, int k, int t,
                          Precond *out) {
+    NvtxRange nvtx_range("lgp.build_precond");
     cudaStream_t st = ctx->work;
     const int64_t N = pp.N, Np = pp.Np;
     if (k < 1 || k > kMaxRank) return fail(ctx, LGP_ERR_UNSUPPORTED, "precond_rank=%d outside 1..%d", k, kMaxRank);
@@ -443,6 +506,7 @@ int cg_iteration_launches(const lgp_ctx *ctx, const Prepared &pp, int t, int pre
 lgp_status run_cg(lgp_ctx *ctx, const Prepared &pp, const float *B, int64_t ldb, int t, const lgp_options *opt,
                   int hist_len, int prec, CgBuffers *bout, int *chunks_run = nullptr, const Precond *pc = nullptr,
                   const float *X0 = nullptr) {
+    NvtxRange nvtx_range("lgp.cg");
     cudaStream_t st = ctx->work;
     CgBuffers b;
     lgp_status s = cg_buffers(ctx, pp.N, pp.Np, t, hist_len, &b);
@@ -737,6 +801,7 @@ lgp_status lgp_check_device_status(lgp_ctx *ctx, lgp_stream stream) {
 
 lgp_status lgp_kernel_matvec(lgp_ctx *ctx, const lgp_hyper *hyp, const float *X, const float *V, float *out,
                              int64_t N, int32_t t, int32_t prec, lgp_stream stream) {
+    NvtxRange nvtx_range("lgp_kernel_matvec");
     if (!ctx) return LGP_ERR_INVALID_ARG;
     if (N < 1) return fail(ctx, LGP_ERR_INVALID_ARG, "N=%lld must be >= 1", (long long)N);
     if (t < 1 || t > kMaxT) return fail(ctx, LGP_ERR_UNSUPPORTED, "t=%d outside 1..%d", t, kMaxT);
@@ -760,6 +825,7 @@ lgp_status lgp_kernel_matvec(lgp_ctx *ctx, const lgp_hyper *hyp, const float *X,
 
 lgp_status lgp_kernel_matvec_grad(lgp_ctx *ctx, const lgp_hyper *hyp, const float *X, const float *W, float *dK_W,
                                   int64_t N, int32_t t, lgp_stream stream) {
+    NvtxRange nvtx_range("lgp_kernel_matvec_grad");
     if (!ctx) return LGP_ERR_INVALID_ARG;
     if (N < 1) return fail(ctx, LGP_ERR_INVALID_ARG, "N=%lld must be >= 1", (long long)N);
     if (t < 1 || t > kMaxT) return fail(ctx, LGP_ERR_UNSUPPORTED, "t=%d outside 1..%d", t, kMaxT);
@@ -792,6 +858,7 @@ lgp_status lgp_rademacher_probes(lgp_ctx *ctx, uint64_t seed, int64_t N, int32_t
 
 lgp_status lgp_cg_solve(lgp_ctx *ctx, const lgp_hyper *hyp, const float *X, const float *B, float *Xsol, int64_t N,
                         int32_t t, const lgp_options *opt, int32_t *iters, double *rel_resid, lgp_stream stream) {
+    NvtxRange nvtx_range("lgp_cg_solve");
     if (!ctx) return LGP_ERR_INVALID_ARG;
     if (N < 1) return fail(ctx, LGP_ERR_INVALID_ARG, "N=%lld must be >= 1", (long long)N);
     if (t < 1 || t > kMaxT) return fail(ctx, LGP_ERR_UNSUPPORTED, "t=%d outside 1..%d", t, kMaxT);
@@ -825,6 +892,7 @@ lgp_status lgp_cg_solve(lgp_ctx *ctx, const lgp_hyper *hyp, const float *X, cons
 lgp_status lgp_lml_and_grad(lgp_ctx *ctx, const lgp_hyper *hyp, const float *X, const float *y, int64_t N,
                             const lgp_options *opt, double *lml, double *grad, lgp_lml_info *info,
                             lgp_stream stream) {
+    NvtxRange nvtx_range("lgp_lml_and_grad");
     if (!ctx) return LGP_ERR_INVALID_ARG;
     if (N < 1) return fail(ctx, LGP_ERR_INVALID_ARG, "N=%lld must be >= 1", (long long)N);
     lgp_status s;
@@ -940,6 +1008,7 @@ static int predict_width(int t, int req_prec) {
 lgp_status lgp_predict(lgp_ctx *ctx, const lgp_hyper *hyp, const float *X, const float *y, int64_t N,
                        const float *Xs, int64_t M, const lgp_options *opt, float *mean, float *var,
                        lgp_predict_info *info, lgp_stream stream) {
+    NvtxRange nvtx_range("lgp_predict");
     constexpr int kChunkCols = 32;
     if (!ctx) return LGP_ERR_INVALID_ARG;
     if (N < 1) return fail(ctx, LGP_ERR_INVALID_ARG, "N=%lld must be >= 1", (long long)N);
@@ -1089,6 +1158,7 @@ lgp_status lgp_predict(lgp_ctx *ctx, const lgp_hyper *hyp, const float *X, const
 lgp_status lgp_batch_cg_solve(lgp_ctx *ctx, int32_t n_gp, const lgp_hyper *hyp, const float *const *X,
                               const float *const *B, float *const *Xsol, const int64_t *N, int32_t t,
                               const lgp_options *opt, int32_t *iters, double *rel_resid, lgp_stream stream) {
+    NvtxRange nvtx_range("lgp_batch_cg_solve");
     if (!ctx) return LGP_ERR_INVALID_ARG;
     if (n_gp < 1 || n_gp > 4096) return fail(ctx, LGP_ERR_UNSUPPORTED, "n_gp=%d outside 1..4096", n_gp);
     if (t < 1 || t > 16) return fail(ctx, LGP_ERR_UNSUPPORTED, "batched solve supports 1 <= t <= 16 (got %d)", t);

@@ -183,3 +183,28 @@ def test_symmetric_lml_and_grad(lgp, sym):
     assert lml == pytest.approx(est["lml"], rel=1e-3)
     scale = np.maximum(np.abs(tg["grad"]), 1e-2 * np.abs(tg["grad"]).max())
     assert (np.abs(np.asarray(grad) - tg["grad"]) / scale).max() <= 1e-3
+
+
+def test_autotune_cache_file(lgp, tmp_path):
+    """LGP_AUTOTUNE_CACHE: the first context tunes and writes its choice; a second context reads it
+    back (same choice, no new line)."""
+    import torch
+    path = tmp_path / "tune.txt"
+    os.environ["LGP_AUTOTUNE_CACHE"] = str(path)
+    os.environ.pop("LGP_TC_SYMMETRIC", None)
+    try:
+        p = wl.cfg3(N=2600, t=32)
+        X = torch.as_tensor(p.X, device="cuda")
+        V = torch.as_tensor(wl.rhs_block(p.N, 32, seed=2), device="cuda")
+        choices = []
+        for _ in range(2):
+            ctx = lgp.Context(0)
+            lgp.lgp_kernel_matvec(X, p, V, prec=lgp.LGP_PREC_SPLIT_F16, ctx=ctx)
+            torch.cuda.synchronize()
+            choices.append(ctx.tc_kernel_choice(p.N, p.D, p.kind, 32, lgp.LGP_PREC_SPLIT_F16))
+            ctx.close()
+        lines = path.read_text().splitlines()
+        assert len(lines) == 1 and "|2816|32|1|8|1 " in lines[0], lines
+        assert choices[0] == choices[1] and choices[0] in (lgp.LGP_TC_ROW, lgp.LGP_TC_SYMMETRIC)
+    finally:
+        os.environ.pop("LGP_AUTOTUNE_CACHE", None)
