@@ -58,9 +58,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--plain", action="store_true", help="also time the plain FP32 single-RHS path")
-    ap.add_argument("--mode", choices=["lml", "matvec", "predict"], default="lml",
+    ap.add_argument("--mode", choices=["lml", "matvec", "predict", "batch"], default="lml",
                     help="lml: the LML+grad step (default); matvec: only the product, for kernel profiling; "
-                         "predict: posterior mean and variance at --M test points")
+                         "predict: posterior mean and variance at --M test points; "
+                         "batch: the 64 uneven GPs of the batch workload in one call vs one call each")
     ap.add_argument("--precond-rank", type=int, default=0,
                     help="pivoted-Cholesky preconditioner rank of the CG solves (0: the paper's plain CG)")
     ap.add_argument("--M", type=int, default=10000, help="test points of --mode predict")
@@ -301,6 +302,9 @@ def main():
     if args.mode == "predict":
         bench_predict(lgp, ctx, p, args, dev, prec, rank)
         return
+    if args.mode == "batch":
+        bench_batch(lgp, ctx, args, dev, rank)
+        return
     X = torch.as_tensor(p.X, device=dev)
     y = torch.as_tensor(p.y, device=dev)
     flush_buf = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
@@ -454,6 +458,66 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def bench_batch(lgp, ctx, args, dev, rank):
+    """Batched solves (t = 8, CG tol 1e-6): the batch workload (64 GPs, N_g log-uniform in [500, 30000],
+    D_g in 1..6) and 256 small GPs (N_g in [200, 2000]), each as one lgp_batch_cg_solve call against the
+    same solves as one lgp_cg_solve call per problem."""
+    import torch
+    import workloads as wl
+    lines = []
+    for label, probs in [("cfg5: 64 GPs, N in [500, 30000]", wl.cfg5_batch(t=8)),
+                         ("256 small GPs, N in [200, 2000]", wl.cfg5_batch(n_gp=256, t=8, seed=15, n_lo=200, n_hi=2000))]:
+        lines.append(_bench_batch_set(lgp, ctx, args, dev, label, probs))
+    if rank == 0:
+        for line in lines:
+            print(json.dumps(line), flush=True)
+
+
+def _bench_batch_set(lgp, ctx, args, dev, label, probs):
+    import torch
+    import workloads as wl
+    Xs = [torch.as_tensor(q.X, device=dev) for q in probs]
+    Bs = []
+    for g, q in enumerate(probs):
+        B = wl.rhs_block(q.N, 8, seed=g, kind="sign")
+        B[:, 0] = q.y
+        Bs.append(torch.as_tensor(B, device=dev))
+
+    def batched():
+        return lgp.lgp_batch_cg_solve(Xs, probs, Bs, tol=1e-6, max_iter=3000, ctx=ctx)
+
+    def one_by_one():
+        its = []
+        for X, q, B in zip(Xs, probs, Bs):
+            _, it, _, _ = lgp.lgp_cg_solve(X, q, B, tol=1e-6, max_iter=3000, ctx=ctx)
+            its.append(int(it.max()))
+        return its
+
+    res = {}
+    for name, fn in [("batched", batched), ("one_call_per_gp", one_by_one)]:
+        for _ in range(max(1, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(args.steps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            out = fn()
+            b.record()
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        res[name] = {"ms": statistics.mean(ms), "ms_all": ms}
+        if name == "batched":
+            res[name]["iters_max"] = int(out[1].max())
+        else:
+            res[name]["iters_max"] = max(out)
+    pairs = sum(float(q.N) ** 2 for q in probs)
+    return {"mode": "batch", "workload": label, "n_gp": len(probs), "t": 8, "pairs_per_product": pairs,
+            "N_min": min(q.N for q in probs), "N_max": max(q.N for q in probs), **res,
+            "speedup": res["one_call_per_gp"]["ms"] / res["batched"]["ms"]}
 
 
 def bench_predict(lgp, ctx, p, args, dev, prec, rank):

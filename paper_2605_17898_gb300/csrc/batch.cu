@@ -19,25 +19,30 @@ constexpr int kBatchThreads = 128;
 constexpr int kBatchR = 2;
 constexpr int kBatchBM = kBatchThreads * kBatchR;
 
-// One 256-row block of one problem: K_y p for those rows over all of the problem's columns.
-template <int KIND, int DP, int TT>
-__device__ void batch_item(const BatchGp &g, int64_t row0, const float *__restrict__ Xs_all,
-                           const float *__restrict__ p_all, float *__restrict__ kp_all, int t, float *xs, float *vs) {
+// One 256-row block of one problem: K_y p for those rows over all of the problem's columns. The
+// distance runs over the problem's own D coordinates (the rows are stored padded to DP).
+template <int KIND, int D, int TT>
+__device__ void batch_item(const BatchGp &g, int64_t row0, int split, const float *__restrict__ Xs_all,
+                           const float *__restrict__ p_all, float *__restrict__ kp_all, float *__restrict__ part,
+                           int t, float *xs, float *vs) {
+    constexpr int DP = D <= 4 ? 4 : 8;
     const int tid = threadIdx.x;
     const float *Xs = Xs_all + g.xs_off;
     const float *V = p_all + g.vec_off * t;
     float *out = kp_all + g.vec_off * t;
-    float xi[kBatchR][DP];
+    float xi[kBatchR][D];
     float tot[kBatchR][TT];
 #pragma unroll
     for (int r = 0; r < kBatchR; ++r) {
         const int64_t i = row0 + r * kBatchThreads + tid;
 #pragma unroll
-        for (int d = 0; d < DP; ++d) xi[r][d] = (i < g.Np) ? Xs[i * DP + d] : 0.0f;
+        for (int d = 0; d < D; ++d) xi[r][d] = (i < g.Np) ? Xs[i * DP + d] : 0.0f;
 #pragma unroll
         for (int c = 0; c < TT; ++c) tot[r][c] = 0.0f;
     }
-    for (int64_t j0 = 0; j0 < g.N; j0 += kSimtBN) {
+    const int64_t jb = (int64_t)split * g.cols_per_split;
+    const int64_t je = min(g.N, jb + g.cols_per_split);
+    for (int64_t j0 = jb; j0 < je; j0 += kSimtBN) {
         __syncthreads();
         for (int e = tid; e < kSimtBN * DP / 4; e += kBatchThreads) {
             const int64_t j = j0 + (e * 4) / DP;
@@ -49,7 +54,7 @@ __device__ void batch_item(const BatchGp &g, int64_t row0, const float *__restri
             const int jj = e / TT;
             const int c = e - jj * TT;
             const int64_t j = j0 + jj;
-            vs[e] = (j < g.N && c < t) ? V[j * t + c] : 0.0f;
+            vs[e] = (j < je && c < t) ? V[j * t + c] : 0.0f;
         }
         __syncthreads();
         float acc[kBatchR][TT];
@@ -59,21 +64,25 @@ __device__ void batch_item(const BatchGp &g, int64_t row0, const float *__restri
             for (int c = 0; c < TT; ++c) acc[r][c] = 0.0f;
 #pragma unroll 2
         for (int jj = 0; jj < kSimtBN; ++jj) {
-            float xj[DP];
-#pragma unroll
-            for (int d = 0; d < DP; d += 4) {
-                const float4 q = *reinterpret_cast<const float4 *>(xs + jj * DP + d);
-                xj[d] = q.x;
-                xj[d + 1] = q.y;
-                xj[d + 2] = q.z;
-                xj[d + 3] = q.w;
-            }
+            float xj[D];
+            load_x_smem<D>(xs + jj * DP, xj);
             float v[TT];
+            if (TT % 4 == 0) {
 #pragma unroll
-            for (int c = 0; c < TT; ++c) v[c] = vs[jj * TT + c];
+                for (int c = 0; c < TT; c += 4) {
+                    const float4 q = *reinterpret_cast<const float4 *>(vs + jj * TT + c);
+                    v[c] = q.x;
+                    v[(c + 1) % TT] = q.y;
+                    v[(c + 2) % TT] = q.z;
+                    v[(c + 3) % TT] = q.w;
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < TT; ++c) v[c] = vs[jj * TT + c];
+            }
 #pragma unroll
             for (int r = 0; r < kBatchR; ++r) {
-                const float k = Entry<KIND>::k(sqdist<DP>(xi[r], xj), g.log2s2);
+                const float k = Entry<KIND>::k(sqdist<D>(xi[r], xj), g.log2s2);
 #pragma unroll
                 for (int c = 0; c < TT; ++c) acc[r][c] = fmaf(k, v[c], acc[r][c]);
             }
@@ -87,9 +96,31 @@ __device__ void batch_item(const BatchGp &g, int64_t row0, const float *__restri
     for (int r = 0; r < kBatchR; ++r) {
         const int64_t i = row0 + r * kBatchThreads + tid;
         if (i >= g.N) continue;
+        if (g.splits > 1) {
+            float *dst = part + g.part_off + ((int64_t)split * g.Np + i) * t;
 #pragma unroll
-        for (int c = 0; c < TT; ++c)
-            if (c < t) out[i * t + c] = fmaf(g.noise, V[i * t + c], tot[r][c]);
+            for (int c = 0; c < TT; ++c)
+                if (c < t) dst[c] = tot[r][c];
+        } else {
+#pragma unroll
+            for (int c = 0; c < TT; ++c)
+                if (c < t) out[i * t + c] = fmaf(g.noise, V[i * t + c], tot[r][c]);
+        }
+    }
+}
+
+template <int KIND, int TT>
+__device__ __forceinline__ void batch_item_d(const BatchGp &g, int64_t row0, int split, const BatchArgs &a, float *xs,
+                                             float *vs) {
+    switch (g.D) {
+        case 1: batch_item<KIND, 1, TT>(g, row0, split, a.Xs, a.p, a.kp, a.part, a.t, xs, vs); break;
+        case 2: batch_item<KIND, 2, TT>(g, row0, split, a.Xs, a.p, a.kp, a.part, a.t, xs, vs); break;
+        case 3: batch_item<KIND, 3, TT>(g, row0, split, a.Xs, a.p, a.kp, a.part, a.t, xs, vs); break;
+        case 4: batch_item<KIND, 4, TT>(g, row0, split, a.Xs, a.p, a.kp, a.part, a.t, xs, vs); break;
+        case 5: batch_item<KIND, 5, TT>(g, row0, split, a.Xs, a.p, a.kp, a.part, a.t, xs, vs); break;
+        case 6: batch_item<KIND, 6, TT>(g, row0, split, a.Xs, a.p, a.kp, a.part, a.t, xs, vs); break;
+        case 7: batch_item<KIND, 7, TT>(g, row0, split, a.Xs, a.p, a.kp, a.part, a.t, xs, vs); break;
+        default: batch_item<KIND, 8, TT>(g, row0, split, a.Xs, a.p, a.kp, a.part, a.t, xs, vs);
     }
 }
 
@@ -110,21 +141,10 @@ __global__ void __launch_bounds__(kBatchThreads) batch_mv_kernel(BatchArgs a) {
         const BatchGp g = a.gps[it.gp];
         const int64_t row0 = (int64_t)it.row_block * kBatchBM;
         switch (g.kind) {
-            case LGP_RBF:
-                if (g.dpad == 4) batch_item<LGP_RBF, 4, TT>(g, row0, a.Xs, a.p, a.kp, a.t, xs, vs);
-                else batch_item<LGP_RBF, 8, TT>(g, row0, a.Xs, a.p, a.kp, a.t, xs, vs);
-                break;
-            case LGP_MATERN52:
-                if (g.dpad == 4) batch_item<LGP_MATERN52, 4, TT>(g, row0, a.Xs, a.p, a.kp, a.t, xs, vs);
-                else batch_item<LGP_MATERN52, 8, TT>(g, row0, a.Xs, a.p, a.kp, a.t, xs, vs);
-                break;
-            case LGP_MATERN12:
-                if (g.dpad == 4) batch_item<LGP_MATERN12, 4, TT>(g, row0, a.Xs, a.p, a.kp, a.t, xs, vs);
-                else batch_item<LGP_MATERN12, 8, TT>(g, row0, a.Xs, a.p, a.kp, a.t, xs, vs);
-                break;
-            default:
-                if (g.dpad == 4) batch_item<LGP_MATERN32, 4, TT>(g, row0, a.Xs, a.p, a.kp, a.t, xs, vs);
-                else batch_item<LGP_MATERN32, 8, TT>(g, row0, a.Xs, a.p, a.kp, a.t, xs, vs);
+            case LGP_RBF: batch_item_d<LGP_RBF, TT>(g, row0, it.split, a, xs, vs); break;
+            case LGP_MATERN52: batch_item_d<LGP_MATERN52, TT>(g, row0, it.split, a, xs, vs); break;
+            case LGP_MATERN12: batch_item_d<LGP_MATERN12, TT>(g, row0, it.split, a, xs, vs); break;
+            default: batch_item_d<LGP_MATERN32, TT>(g, row0, it.split, a, xs, vs);
         }
     }
 }
@@ -208,6 +228,23 @@ __global__ void bdone_kernel(BatchArgs a, int first) {
     if (threadIdx.x == 0) {
         if (!first) a.st->iter += 1;
         *a.done = (!any_s || a.st->iter >= a.st->max_iter || (first && a.st->status)) ? 1 : 0;
+    }
+}
+
+// K_y p for problems whose product was split over columns: the partial sums in split order plus
+// sigma^2 p (one vector block per CTA).
+__global__ void bsplit_reduce_kernel(BatchArgs a) {
+    if (*a.done) return;
+    const BatchVecBlock vb = a.vblocks[blockIdx.x];
+    const BatchGp g = a.gps[vb.gp];
+    if (g.splits <= 1 || a.gp_done[vb.gp]) return;
+    const int t = a.t;
+    const int c = threadIdx.x % t;
+    for (int64_t i = vb.r0 + threadIdx.x / t; i < vb.r1; i += blockDim.x / t) {
+        float sum = 0.0f;
+        for (int k = 0; k < g.splits; ++k) sum += a.part[g.part_off + ((int64_t)k * g.Np + i) * t + c];
+        const int64_t e = (g.vec_off + i) * t + c;
+        a.kp[e] = fmaf(g.noise, a.p[e], sum);
     }
 }
 
@@ -346,6 +383,7 @@ cudaError_t launch_batch_iteration(const BatchArgs &a, int num_sms, cudaStream_t
     const int n = a.n_gp * a.t;
     const int sb = (n + 255) / 256;
     const int vt = vec_threads(a.t);
+    bsplit_reduce_kernel<<<a.n_vblocks, vt, 0, st>>>(a);
     bpkp_kernel<<<a.n_vblocks, vt, 0, st>>>(a);
     balpha_kernel<<<sb, 256, 0, st>>>(a);
     bxr_kernel<<<a.n_vblocks, vt, 0, st>>>(a);

@@ -11,9 +11,12 @@ struct BatchGp {
     int64_t N, Np;
     int64_t xs_off;    // float offset of this problem's prescaled X in the shared buffer
     int64_t vec_off;   // row offset of this problem's vectors in the shared [rows, t] buffers
-    int kind, dpad;
+    int kind, dpad, D;
     float log2s2, noise;
     int blk0, blk1;    // this problem's vector blocks [blk0, blk1)
+    int splits;        // column splits of the product (1: items write K_y p directly)
+    int64_t cols_per_split;
+    int64_t part_off;  // float offset of this problem's [splits, Np, t] partial sums (splits > 1)
     const float *B;    // caller's right-hand sides [N, t]
     float *Xsol;       // caller's solutions [N, t]
 };
@@ -21,6 +24,7 @@ struct BatchGp {
 struct BatchItem {
     int gp;
     int row_block;     // rows [256 * row_block, 256 * row_block + 256)
+    int split;         // columns [split * cols_per_split, (split + 1) * cols_per_split)
 };
 
 struct BatchVecBlock {
@@ -41,6 +45,7 @@ struct BatchArgs {
     int n_gp, n_items, n_vblocks, t, tt;
     const float *Xs;
     float *x, *r, *p, *kp;
+    float *part;                         // column-split partial sums of the product
     double *partial;                     // [n_vblocks, t]
     double *rr, *bnorm2, *alpha, *beta;  // [n_gp * t]
     int *active, *iters;                 // [n_gp * t]

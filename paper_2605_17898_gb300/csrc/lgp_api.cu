@@ -43,7 +43,7 @@ struct lgp_ctx {
     cudaEvent_t ev_chunk[2] = {nullptr, nullptr};
     // workspace
     DevBuf xs, mv_partial, cg_vec, cg_partial, cg_state, cg_hist, scal, rhs, adj_b, adj_partial, vsplit, flags;
-    DevBuf batch_meta, pred_xs, pred_z, pred_q;
+    DevBuf batch_meta, batch_part, pred_xs, pred_z, pred_q;
     DevBuf pc_l64, pc_l32, pc_d, pc_info, pc_part, pc_u, pc_cinv, pc_gram, pc_e, pc_rhs;
     int64_t ws_bytes = 0;
     // pinned host mirrors
@@ -739,11 +739,12 @@ void lgp_destroy(lgp_ctx *ctx) {
     cudaSetDevice(ctx->device);
     if (ctx->work) cudaStreamSynchronize(ctx->work);
     if (ctx->cg_exec) cudaGraphExecDestroy(ctx->cg_exec);
-    DevBuf *bufs[] = {&ctx->pc_l64, &ctx->pc_l32, &ctx->pc_d, &ctx->pc_info, &ctx->pc_part, &ctx->pc_u,
-                      &ctx->pc_cinv, &ctx->pc_gram, &ctx->pc_e, &ctx->pc_rhs, &ctx->pred_xs, &ctx->pred_z,
-                      &ctx->pred_q, &ctx->xs, &ctx->mv_partial, &ctx->cg_vec, &ctx->cg_partial, &ctx->cg_state, &ctx->cg_hist,
-                      &ctx->scal, &ctx->rhs, &ctx->adj_b, &ctx->adj_partial, &ctx->vsplit, &ctx->flags,
-                      &ctx->batch_meta};
+    DevBuf *bufs[] = {&ctx->pc_l64,     &ctx->pc_l32,   &ctx->pc_d,      &ctx->pc_info,    &ctx->pc_part,
+                      &ctx->pc_u,       &ctx->pc_cinv,  &ctx->pc_gram,   &ctx->pc_e,       &ctx->pc_rhs,
+                      &ctx->batch_part, &ctx->pred_xs,  &ctx->pred_z,    &ctx->pred_q,     &ctx->xs,
+                      &ctx->mv_partial, &ctx->cg_vec,   &ctx->cg_partial, &ctx->cg_state,  &ctx->cg_hist,
+                      &ctx->scal,       &ctx->rhs,      &ctx->adj_b,     &ctx->adj_partial, &ctx->vsplit,
+                      &ctx->flags,      &ctx->batch_meta};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (ctx->h_state) cudaFreeHost(ctx->h_state);
@@ -1172,7 +1173,7 @@ lgp_status lgp_batch_cg_solve(lgp_ctx *ctx, int32_t n_gp, const lgp_hyper *hyp, 
     std::vector<BatchVecBlock> vblocks;
     const int rows_per_vblock = std::max(1, 4096 / t);
     const int bm = batch_item_rows();
-    int64_t xs_total = 0, rows_total = 0;
+    int64_t xs_total = 0, rows_total = 0, part_total = 0;
     for (int g = 0; g < n_gp; ++g) {
         if (N[g] < 1) return fail(ctx, LGP_ERR_INVALID_ARG, "N[%d]=%lld must be >= 1", g, (long long)N[g]);
         if ((s = make_params(ctx, &hyp[g], &kps[g])) != LGP_OK) return s;
@@ -1191,6 +1192,7 @@ lgp_status lgp_batch_cg_solve(lgp_ctx *ctx, int32_t n_gp, const lgp_hyper *hyp, 
         G.vec_off = rows_total;
         G.kind = kps[g].kind;
         G.dpad = kps[g].dpad;
+        G.D = kps[g].D;
         G.log2s2 = kps[g].log2_s2;
         G.noise = kps[g].noise;
         G.B = B[g];
@@ -1199,13 +1201,26 @@ lgp_status lgp_batch_cg_solve(lgp_ctx *ctx, int32_t n_gp, const lgp_hyper *hyp, 
         for (int64_t r0 = 0; r0 < G.N; r0 += rows_per_vblock)
             vblocks.push_back({g, r0, std::min<int64_t>(G.N, r0 + rows_per_vblock)});
         G.blk1 = (int)vblocks.size();
-        for (int64_t rb = 0; rb * bm < G.N; ++rb) items.push_back({g, (int)rb});
+        // column splits so that this problem alone gives about two items per CTA slot of the persistent
+        // product (its last iterations may run with no other problem left), each split a whole number
+        // of 64-column tiles
+        const int64_t rb_n = (G.N + bm - 1) / bm;
+        const int64_t col_tiles = (G.N + 63) / 64;
+        int64_t S = std::max<int64_t>(1, (2 * ctx->num_sms + rb_n - 1) / rb_n);
+        S = std::min<int64_t>(S, std::max<int64_t>(1, col_tiles / 4));
+        G.cols_per_split = (col_tiles + S - 1) / S * 64;
+        G.splits = (int)((G.N + G.cols_per_split - 1) / G.cols_per_split);
+        G.part_off = part_total;
+        if (G.splits > 1) part_total += (int64_t)G.splits * G.Np * t;
+        for (int64_t rb = 0; rb < rb_n; ++rb)
+            for (int sp = 0; sp < G.splits; ++sp) items.push_back({g, (int)rb, sp});
         xs_total += G.Np * G.dpad;
         rows_total += G.Np;
     }
-    // longest items first: every item of problem g costs ~N_g
-    std::stable_sort(items.begin(), items.end(),
-                     [&](const BatchItem &a, const BatchItem &b) { return gps[a.gp].N > gps[b.gp].N; });
+    // longest items first: an item of problem g costs ~min(N_g, cols_per_split_g)
+    std::stable_sort(items.begin(), items.end(), [&](const BatchItem &a, const BatchItem &b) {
+        return std::min(gps[a.gp].N, gps[a.gp].cols_per_split) > std::min(gps[b.gp].N, gps[b.gp].cols_per_split);
+    });
     const int ng_t = n_gp * t;
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     size_t off = 0;
@@ -1220,6 +1235,8 @@ lgp_status lgp_batch_cg_solve(lgp_ctx *ctx, int32_t n_gp, const lgp_hyper *hyp, 
     if ((s = ensure(ctx, ctx->xs, (size_t)xs_total * sizeof(float))) != LGP_OK) return s;
     if ((s = ensure(ctx, ctx->cg_vec, (size_t)4 * rows_total * t * sizeof(float))) != LGP_OK) return s;
     if ((s = ensure(ctx, ctx->cg_partial, vblocks.size() * (size_t)t * sizeof(double))) != LGP_OK) return s;
+    if ((s = ensure(ctx, ctx->batch_part, (size_t)std::max<int64_t>(part_total, 1) * sizeof(float))) != LGP_OK)
+        return s;
     if ((s = ensure(ctx, ctx->flags, 64)) != LGP_OK) return s;
     unsigned char *meta = (unsigned char *)ctx->batch_meta.p;
     BatchArgs A;
@@ -1238,6 +1255,7 @@ lgp_status lgp_batch_cg_solve(lgp_ctx *ctx, int32_t n_gp, const lgp_hyper *hyp, 
     A.r = v + rows_total * t;
     A.p = v + 2 * rows_total * t;
     A.kp = v + 3 * rows_total * t;
+    A.part = (float *)ctx->batch_part.p;
     A.partial = (double *)ctx->cg_partial.p;
     double *dd = (double *)(meta + o_rr);
     A.rr = dd;
