@@ -24,6 +24,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -120,8 +121,10 @@ class ClockSampler:
 
     def __init__(self, uuid: str | None):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
-        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        # raw samples go to LGP_CLOCKS_DIR when set (kept for inspection), else to a temporary file
+        out_dir = os.environ.get("LGP_CLOCKS_DIR") or tempfile.gettempdir()
+        os.makedirs(out_dir, exist_ok=True)
+        self.path = os.path.join(out_dir, f"lgp_clocks_{os.getpid()}.csv")
         cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
         if uuid:
             cmd[1:1] = ["-i", uuid]

@@ -54,7 +54,7 @@ typedef enum {
     LGP_OK = 0,
     LGP_WARN_NOT_CONVERGED = 1,   /* some column hit max_iter; outputs valid */
     LGP_ERR_INVALID_ARG = -1,     /* bad pointer, size, alignment or value */
-    LGP_ERR_UNSUPPORTED = -2,     /* a size or mode this build does not handle */
+    LGP_ERR_UNSUPPORTED = -2,     /* a size or mode the library does not handle */
     LGP_ERR_CUDA = -3,            /* a CUDA runtime call failed */
     LGP_ERR_NONFINITE = -4,       /* NaN/Inf in inputs or in a CG scalar */
     LGP_ERR_BREAKDOWN = -5,       /* p^T K_y p <= 0 in CG (K_y not positive definite) */
