@@ -177,6 +177,20 @@ int32_t lgp_matvec_precision(const lgp_ctx *ctx, int32_t t, int32_t prec);
 enum { LGP_TC_UNTUNED = 0, LGP_TC_ROW = 1, LGP_TC_SYMMETRIC = 2 };
 int32_t lgp_tc_kernel_choice(const lgp_ctx *ctx, int64_t N, int32_t D, int32_t kind, int32_t t, int32_t prec);
 
+/* How the last symmetric-tile product launched through this context formed its squared
+ * distances (diagnostic). The difference form sums (x_id - x_jd)^2 over d in float32; the dot
+ * form takes r^2 = |u_i|^2 + |u_j|^2 - 2 u_i . u_j for the box-centred coordinates u, with the
+ * inner products on the tensor cores (split float16 operands, float32 accumulation; Sec. 3 names
+ * this rewriting of the distance as the reason its product time barely depends on D). The dot
+ * form is used for RBF, Matern-3/2 and Matern-5/2 at D >= 3 when max_j |u_j|^2 stays below a
+ * per-kernel limit that bounds its rounding error; otherwise, for Matern-1/2, D < 3, or with
+ * LGP_DISTANCE=diff in the environment, the difference form runs.
+ * *form receives LGP_DIST_NONE (no symmetric product yet), LGP_DIST_DIFF or LGP_DIST_DOT;
+ * *norm_max (may be NULL) the measured max_j |u_j|^2 when the dot form was considered, else -1.
+ * Waits for the context's work and the given stream to finish. */
+enum { LGP_DIST_NONE = -1, LGP_DIST_DIFF = 0, LGP_DIST_DOT = 1 };
+lgp_status lgp_tc_distance_form(lgp_ctx *ctx, lgp_stream stream, int32_t *form, float *norm_max);
+
 /* Bound, in GPU clock cycles, on every device-side wait of the tensor-core product
  * (pipeline barriers between its copy, generation and MMA stages). A wait that
  * runs out sets the context's device error word and the kernel returns early;

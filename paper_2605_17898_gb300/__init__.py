@@ -43,13 +43,16 @@ LGP_PREC_SPLIT_F16 = 3
 LGP_TC_UNTUNED = 0
 LGP_TC_ROW = 1
 LGP_TC_SYMMETRIC = 2
+LGP_DIST_NONE = -1
+LGP_DIST_DIFF = 0
+LGP_DIST_DOT = 1
 
 EXPORTED = [
     "lgp_version", "lgp_status_string", "lgp_create", "lgp_destroy", "lgp_last_error_message",
     "lgp_workspace_bytes", "lgp_matvec_precision", "lgp_set_wait_budget", "lgp_check_device_status",
     "lgp_kernel_matvec", "lgp_kernel_matvec_grad", "lgp_cg_solve", "lgp_lml_and_grad",
     "lgp_rademacher_probes", "lgp_batch_cg_solve", "lgp_kernel_matvec_noalloc",
-    "lgp_measure_pipe_peak", "lgp_tc_kernel_choice", "lgp_predict",
+    "lgp_measure_pipe_peak", "lgp_tc_kernel_choice", "lgp_predict", "lgp_tc_distance_form",
 ]
 
 
@@ -117,6 +120,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
                                            c.POINTER(lgp_options), vp, vp, vp]),
         "lgp_measure_pipe_peak": (c.c_int32, [c.c_int32, c.POINTER(c.c_double), vp]),
         "lgp_tc_kernel_choice": (c.c_int32, [vp, c.c_int64, c.c_int32, c.c_int32, c.c_int32, c.c_int32]),
+        "lgp_tc_distance_form": (c.c_int32, [vp, vp, vp, vp]),
         "lgp_predict": (c.c_int32, [vp, c.POINTER(lgp_hyper), vp, vp, c.c_int64, vp, c.c_int64,
                                     c.POINTER(lgp_options), vp, vp, c.POINTER(lgp_predict_info), vp]),
         "lgp_kernel_matvec_noalloc": (c.c_int32, [c.POINTER(lgp_hyper), vp, vp, vp, c.c_int64, c.c_int32, c.c_int32,
@@ -215,6 +219,13 @@ class Context:
     def tc_kernel_choice(self, N: int, D: int, kind: int, t: int, prec: int = LGP_PREC_AUTO) -> int:
         """LGP_TC_UNTUNED / LGP_TC_ROW / LGP_TC_SYMMETRIC for that product shape (or a negative status)."""
         return int(self.lib.lgp_tc_kernel_choice(self.h, int(N), int(D), int(kind), int(t), int(prec)))
+
+    def tc_distance_form(self, stream=None) -> tuple[int, float]:
+        """(LGP_DIST_NONE / LGP_DIST_DIFF / LGP_DIST_DOT, max |u|^2 or -1) of the last symmetric product."""
+        form = ctypes.c_int32(0)
+        amax = ctypes.c_float(0.0)
+        self._check(self.lib.lgp_tc_distance_form(self.h, _stream_ptr(stream), ctypes.byref(form), ctypes.byref(amax)))
+        return int(form.value), float(amax.value)
 
     def set_wait_budget(self, cycles: int):
         self.lib.lgp_set_wait_budget(self.h, int(cycles))

@@ -56,6 +56,9 @@ struct lgp_ctx {
     std::vector<unsigned char> cg_key;
     // autotuned column-split counts of the tensor-core product, keyed by (Np, t, fmt, D, kind)
     std::map<std::vector<int64_t>, int> tc_splits;
+    // the last symmetric-tile product: its kind, padded rows and columns (for the distance-form query)
+    int sym_kind = -1, sym_D = 0, sym_t = 0;
+    int64_t sym_Np = 0;
 };
 
 namespace {
@@ -336,6 +339,12 @@ lgp_status matvec_prepared(lgp_ctx *ctx, const Prepared &pp, const float *V, int
                               (float *)ctx->mv_partial.p,
                               (int64_t)(ctx->mv_partial.bytes / sizeof(float)), skip, (int *)ctx->flags.p + 1,
                               ctx->wait_budget, ctx->num_sms, st, forced));
+        if (forced == kTcSymmetric) {
+            ctx->sym_kind = pp.kp.kind;
+            ctx->sym_D = pp.kp.D;
+            ctx->sym_t = t;
+            ctx->sym_Np = pp.Np;
+        }
         return LGP_OK;
     }
     const int64_t pf = mv_simt_partial_floats(pp.N, pp.Np, t, ctx->num_sms);
@@ -494,7 +503,8 @@ lgp_status build_precond(lgp_ctx *ctx, const lgp_hyper *hyp, const float *X, con
 
 // Run CG on the internal stream: init, then replay a captured chunk of iterations until done.
 int matvec_launches(const lgp_ctx *ctx, const Prepared &pp, int t, int prec) {
-    return is_tc(prec) ? mv_tc_launches(pp.Np, t, ctx->num_sms, tc_fmt(prec), tc_splits_for(ctx, pp, t, prec))
+    return is_tc(prec) ? mv_tc_launches(pp.Np, t, ctx->num_sms, tc_fmt(prec), tc_splits_for(ctx, pp, t, prec), pp.kp.kind,
+                                        pp.kp.D)
                        : mv_simt_launches(pp.N, pp.Np, t, ctx->num_sms);
 }
 
@@ -782,6 +792,30 @@ int32_t lgp_tc_kernel_choice(const lgp_ctx *ctx, int64_t N, int32_t D, int32_t k
     auto it = ctx->tc_splits.find(key);
     if (it == ctx->tc_splits.end()) return LGP_TC_UNTUNED;
     return it->second == kTcSymmetric ? LGP_TC_SYMMETRIC : LGP_TC_ROW;
+}
+
+lgp_status lgp_tc_distance_form(lgp_ctx *ctx, lgp_stream stream, int32_t *form, float *norm_max) {
+    if (!ctx || !form) return LGP_ERR_INVALID_ARG;
+    if (norm_max) *norm_max = -1.0f;
+    if (ctx->sym_kind < 0) {
+        *form = LGP_DIST_NONE;
+        return LGP_OK;
+    }
+    if (!dot_form_allowed(ctx->sym_kind, ctx->sym_D)) {
+        *form = LGP_DIST_DIFF;
+        return LGP_OK;
+    }
+    LGP_CUDA(cudaSetDevice(ctx->device));
+    LGP_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    LGP_CUDA(cudaStreamSynchronize(ctx->work));
+    unsigned int bits = 0;
+    LGP_CUDA(cudaMemcpy(&bits, (const char *)ctx->vsplit.p + tc_dot_gate_offset(ctx->sym_Np, ctx->sym_t), sizeof bits,
+                        cudaMemcpyDeviceToHost));
+    float a;
+    std::memcpy(&a, &bits, sizeof a);
+    if (norm_max) *norm_max = a;
+    *form = a <= dot_gate_limit(ctx->sym_kind) ? LGP_DIST_DOT : LGP_DIST_DIFF;
+    return LGP_OK;
 }
 
 void lgp_set_wait_budget(lgp_ctx *ctx, int64_t cycles) {

@@ -212,11 +212,18 @@ cudaError_t launch_mv_tc(const KernelParams &kp, const float *Xs, int64_t N, int
                          int forced_splits = 0);
 int64_t mv_tc_partial_floats(int64_t Np, int t, int num_sms);
 int64_t mv_tc_partial_floats(int64_t Np, int t, int num_sms, int forced_splits);
-int mv_tc_launches(int64_t Np, int t, int num_sms, int fmt, int forced_splits = 0);
+// Kernels one split tensor-core product launches (the symmetric product with the dot form runs
+// its operand kernels and both gated instances).
+int mv_tc_launches(int64_t Np, int t, int num_sms, int fmt, int forced_splits = 0, int kind = -1, int D = 0);
 // Up to four kernel choices worth timing: kTcSymmetric (when tc_symmetric_ok) and the three most
 // wave-efficient split counts.
 void tc_split_candidates(int64_t Np, int num_sms, int *cand, int *n);
 bool tc_symmetric_ok(int64_t Np);
+// Dot-form distance of the symmetric product: whether it is considered for (kind, D), its limit on
+// max |u|^2, and the byte offset of the word holding the measured max in the V-split workspace.
+bool dot_form_allowed(int kind, int D);
+float dot_gate_limit(int kind);
+int64_t tc_dot_gate_offset(int64_t Np, int t);
 
 // precond.cu: the rank-k pivoted-Cholesky preconditioner P = L L^T + sigma^2 I (k = 0: none).
 struct Precond {

@@ -1,5 +1,6 @@
 // Host side of the split tensor-core product: V splitting, tensor maps, grid shape, launch.
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 
 #include "mv_tc_inst.cuh"
@@ -84,6 +85,114 @@ __global__ void transpose_x_kernel(const float *__restrict__ Xs, int64_t Np, int
         const int64_t j = e - (int64_t)d * Np;
         XsT[e] = Xs[j * dpad + d];
     }
+}
+
+// Monotone map of a float onto unsigned integers (and back), so that atomicMax orders floats.
+__device__ __forceinline__ unsigned int ord_of(float f) {
+    const unsigned int u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float float_of_ord(unsigned int o) {
+    return __uint_as_float((o & 0x80000000u) ? (o & 0x7FFFFFFFu) : ~o);
+}
+
+// Dot-form distance, step 1: bounding box of the prescaled rows i < N. words[d] = ord(max x_d),
+// words[8 + d] = ord(max -x_d); the words start at zero (below every ordered float).
+__global__ void dot_bbox_kernel(const float *__restrict__ Xs, int64_t N, int dpad, unsigned int *__restrict__ words,
+                                const int *skip) {
+    if (skip && *skip) return;
+    unsigned int hi[8], lo[8];
+#pragma unroll
+    for (int d = 0; d < 8; ++d) hi[d] = lo[d] = 0u;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+            if (d < dpad) {
+                const float x = Xs[i * dpad + d];
+                hi[d] = max(hi[d], ord_of(x));
+                lo[d] = max(lo[d], ord_of(-x));
+            }
+        }
+    }
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+        const unsigned int h = __reduce_max_sync(0xffffffffu, hi[d]);
+        const unsigned int l = __reduce_max_sync(0xffffffffu, lo[d]);
+        if ((threadIdx.x & 31) == 0 && d < dpad) {
+            atomicMax(words + d, h);
+            atomicMax(words + 8 + d, l);
+        }
+    }
+}
+
+// Dot-form distance, step 2: per row j, the centred coordinates u = x - c (c the box centre)
+// split as u = h + m (h = f16(u), m = f16(u - h)), the squared norm a_j = sum_d (h^2 + 2 h m)
+// (what the Gram products below give for <u_j, u_j> without the m m term) in float32 and in three
+// float16 parts, and the two Gram operand rows, K-major, in the tile layout the MMA reads
+// (element (r, k) of 128-row tile q at q kU + ((k / 8) 16 + r / 8) 128 + (r % 8) 16 + (k % 8) 2):
+//   A role:  [h | m | h | 1 1 1 | 0 ...]
+//   B role:  [2h | 2h | 2m | -a_h -a_m -a_l | 0 ...]
+// so that A_i . B_j = 2 (h_i h_j + m_i h_j + h_i m_j) - a_j = 2 u_i . u_j - a_j to about 22 bits.
+// words[16] collects max a_j over rows j < N (float bits, a_j >= 0).
+template <int DP>
+__global__ void dot_operands_kernel(const float *__restrict__ Xs, int64_t N, int64_t Np,
+                                    unsigned int *__restrict__ words, float *__restrict__ arow,
+                                    uint4 *__restrict__ ua, uint4 *__restrict__ ub, const int *skip) {
+    if (skip && *skip) return;
+    constexpr int KG = DP <= 4 ? 16 : 32;
+    constexpr int kTileBytes = 128 * KG * 2;
+    float c[DP];
+#pragma unroll
+    for (int d = 0; d < DP; ++d) c[d] = 0.5f * (float_of_ord(words[d]) - float_of_ord(words[8 + d]));
+    unsigned int amax = 0u;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < Np; j += (int64_t)gridDim.x * blockDim.x) {
+        __half h[DP], m[DP];
+        double a = 0.0;
+#pragma unroll
+        for (int d = 0; d < DP; ++d) {
+            const float u = Xs[j * DP + d] - c[d];
+            h[d] = __float2half_rn(u);
+            const float hf = __half2float(h[d]);
+            m[d] = __float2half_rn(u - hf);
+            const double hd = hf, md = __half2float(m[d]);
+            a += hd * hd + 2.0 * hd * md;
+        }
+        const float a32 = (float)a;
+        const __half ah = __float2half_rn(a32);
+        const float r1 = a32 - __half2float(ah);
+        const __half am = __float2half_rn(r1);
+        const __half al = __float2half_rn(r1 - __half2float(am));
+        __half ra[KG], rb[KG];
+        const __half zero = __float2half_rn(0.0f), one = __float2half_rn(1.0f);
+#pragma unroll
+        for (int k = 0; k < KG; ++k) ra[k] = rb[k] = zero;
+#pragma unroll
+        for (int d = 0; d < DP; ++d) {
+            const __half h2 = __hadd(h[d], h[d]), m2 = __hadd(m[d], m[d]);
+            ra[d] = h[d];
+            ra[DP + d] = m[d];
+            ra[2 * DP + d] = h[d];
+            rb[d] = h2;
+            rb[DP + d] = h2;
+            rb[2 * DP + d] = m2;
+        }
+        ra[3 * DP] = ra[3 * DP + 1] = ra[3 * DP + 2] = one;
+        rb[3 * DP] = __hneg(ah);
+        rb[3 * DP + 1] = __hneg(am);
+        rb[3 * DP + 2] = __hneg(al);
+        arow[j] = a32;
+        const int64_t q = j / 128;
+        const int r = (int)(j - q * 128);
+#pragma unroll
+        for (int kg = 0; kg < KG / 8; ++kg) {
+            const int64_t off = (q * kTileBytes + (int64_t)((kg * 16 + (r >> 3)) * 128 + (r & 7) * 16)) / 16;
+            ua[off] = *reinterpret_cast<const uint4 *>(ra + 8 * kg);
+            ub[off] = *reinterpret_cast<const uint4 *>(rb + 8 * kg);
+        }
+        if (j < N) amax = max(amax, __float_as_uint(a32));
+    }
+    amax = __reduce_max_sync(0xffffffffu, amax);
+    if ((threadIdx.x & 31) == 0) atomicMax(words + 16, amax);
 }
 
 __global__ void tc_reduce_kernel(const float *__restrict__ partial, int S, int64_t Np, int64_t N, int t,
@@ -196,9 +305,36 @@ TcGrid tc_grid(int64_t Np, int num_sms, int forced_splits = 0) {
 
 bool tc_supported(int t) { return (t == 16 || t == 32) && encode_fn() != nullptr; }
 
-// V_hi, V_lo [Np, t] 16-bit each, per-column max bits [64] and epilogue scales [64], then the
-// transposed prescaled X [8, Np] float32.
-int64_t tc_vsplit_bytes(int64_t Np, int t) { return 2 * Np * t * 2 + 2 * 64 * 4 + 8 * Np * 4; }
+// V_hi, V_lo [Np, t] 16-bit each, per-column max bits [64] and epilogue scales [64], the
+// transposed prescaled X [8, Np] float32, then the dot-form distance data of the symmetric
+// product: 32 words (bounding box, largest squared norm), a [Np] float32 and the A- and B-role
+// Gram operands (up to 64 bytes per row each).
+int64_t tc_vsplit_bytes(int64_t Np, int t) {
+    return 2 * Np * t * 2 + 2 * 64 * 4 + 8 * Np * 4 + 32 * 4 + Np * 4 + 2 * Np * 64;
+}
+
+int64_t tc_dot_gate_offset(int64_t Np, int t) { return 2 * Np * t * 2 + 2 * 64 * 4 + 8 * Np * 4 + 16 * 4; }
+
+// Squared-norm limits of the dot form, per kernel: with a = max_j |u_j|^2 the rounding error of
+// a_i + a_j - 2 u_i . u_j is about 4 a 2^-24, and an entry moves by at most |dk / dr^2| times that
+// (ln 2 s^2 for the RBF on its prescaled coordinates, s^2 / 6 for Matern-5/2, s^2 / 2 for
+// Matern-3/2). The limits hold that bound near 1.6e-5 s^2; data that spread wider take the
+// difference form.
+float dot_gate_limit(int kind) {
+    switch (kind) {
+        case LGP_RBF: return 97.0f;
+        case LGP_MATERN52: return 403.0f;
+        case LGP_MATERN32: return 134.0f;
+    }
+    return -1.0f;
+}
+
+// LGP_DISTANCE=diff keeps the symmetric product on the difference form.
+bool dot_form_allowed(int kind, int D) {
+    if (dot_gate_limit(kind) <= 0.0f || D < 3) return false;
+    const char *env = std::getenv("LGP_DISTANCE");
+    return !(env && std::strcmp(env, "diff") == 0);
+}
 
 int64_t mv_tc_partial_floats(int64_t Np, int t, int num_sms, int forced_splits) {
     if (forced_splits == kTcSymmetric) return 0;
@@ -234,8 +370,9 @@ void tc_split_candidates(int64_t Np, int num_sms, int *cand, int *n) {
     }
 }
 
-int mv_tc_launches(int64_t Np, int t, int num_sms, int fmt, int forced_splits) {
-    return (mv_tc_partial_floats(Np, t, num_sms, forced_splits) > 0 ? 4 : 3) + (fmt == kFmtF16 ? 1 : 0);
+int mv_tc_launches(int64_t Np, int t, int num_sms, int fmt, int forced_splits, int kind, int D) {
+    const int dot = forced_splits == kTcSymmetric && dot_form_allowed(kind, D) ? 3 : 0;
+    return (mv_tc_partial_floats(Np, t, num_sms, forced_splits) > 0 ? 4 : 3) + (fmt == kFmtF16 ? 1 : 0) + dot;
 }
 
 cudaError_t launch_mv_tc(const KernelParams &kp, const float *Xs, int64_t N, int64_t Np, const float *V, int64_t ldv,
@@ -304,9 +441,42 @@ cudaError_t launch_mv_tc(const KernelParams &kp, const float *Xs, int64_t N, int
                                          t == 32 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B))
             a.add_mode = tcs::kAddVec4;
         a.budget = wait_budget;
+        a.gate = nullptr;
+        a.gate_lim = 0.0f;
+        a.dot = 0;
+        a.arow = nullptr;
+        a.ua = a.ub = nullptr;
         const dim3 grid((unsigned)std::min<int64_t>(num_sms, a.tiles), 1, 1);
-        return fmt == kFmtF16 ? tcs::dispatch_f16(kp.kind, kp.D, t, grid, mx, mv, mo, a, st)
-                              : tcs::dispatch_bf16(kp.kind, kp.D, t, grid, mx, mv, mo, a, st);
+        auto launch = [&]() {
+            return fmt == kFmtF16 ? tcs::dispatch_f16(kp.kind, kp.D, t, grid, mx, mv, mo, a, st)
+                                  : tcs::dispatch_bf16(kp.kind, kp.D, t, grid, mx, mv, mo, a, st);
+        };
+        if (!dot_form_allowed(kp.kind, kp.D)) return launch();
+        // dot form: operands, then both instances; the gate word lets exactly one of them work
+        unsigned int *words = (unsigned int *)(XsT + 8 * Np);
+        float *arow = (float *)(words + 32);
+        uint8_t *ua = (uint8_t *)(arow + Np);
+        uint8_t *ub = ua + Np * 64;
+        e = cudaMemsetAsync(words, 0, 32 * sizeof(unsigned int), st);
+        if (e != cudaSuccess) return e;
+        const int bb = (int)std::min<int64_t>((N + 255) / 256, 1024);
+        dot_bbox_kernel<<<bb, 256, 0, st>>>(Xs, N, kp.dpad, words, skip);
+        const int ob = (int)std::min<int64_t>((Np + 255) / 256, 4096);
+        if (kp.dpad <= 4)
+            dot_operands_kernel<4><<<ob, 256, 0, st>>>(Xs, N, Np, words, arow, (uint4 *)ua, (uint4 *)ub, skip);
+        else
+            dot_operands_kernel<8><<<ob, 256, 0, st>>>(Xs, N, Np, words, arow, (uint4 *)ua, (uint4 *)ub, skip);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        a.gate = words + 16;
+        a.gate_lim = dot_gate_limit(kp.kind);
+        a.arow = arow;
+        a.ua = ua;
+        a.ub = ub;
+        a.dot = 1;
+        if ((e = launch()) != cudaSuccess) return e;
+        a.dot = 0;
+        return launch();
     }
     const TcGrid g = tc_grid(Np, num_sms, forced_splits);
     if (g.S > 1 && (partial == nullptr || (int64_t)g.S * Np * t > partial_cap)) return cudaErrorInvalidValue;

@@ -32,6 +32,8 @@
 // Waits are bounded and abort the CTA as in mv_tc.cuh.
 #pragma once
 
+#include <type_traits>
+
 #include "mv_tc.cuh"
 
 namespace lgp {
@@ -64,9 +66,17 @@ using tc::tmem_wait_ld;
 
 constexpr int kTile = 128;          // tile rows = tile columns = MMA M
 constexpr int kStages = 2;
-constexpr int kTmemCols = 512;      // 2 buffers x [out_I 128 | out_J 128]
+constexpr int kTmemCols = 512;      // 2 accumulator buffers (+ the Gram tile in the dot form)
 constexpr int kErrWaitVi = 0x100;
+constexpr int kErrWaitGram = 0x200;
+// The dot form adds a second MMA-issuing warp: one thread issues a tcgen05.mma about every 100
+// cycles, while the tensor pipe finishes an M = 128, N <= 64, K = 16 product in about 50, so a
+// single issuer leaves it half idle. Warp 17 issues the Gram tiles and the out_I products, warp 22
+// the out_J products.
+constexpr int kMmaWarpJ = 22;
+constexpr int kDotThreads = 736;
 
+// Difference form: a 2-stage ring of [entry tile hi | lo | V_J hi; lo | x_J], two V_I slots.
 template <int T, int DP>
 struct TcsLayout {
     static constexpr int kA = kTile * kTile * 2;  // one 16-bit half of the entry tile
@@ -77,6 +87,39 @@ struct TcsLayout {
     static constexpr int kStaging = kVi + 2 * 2 * kB;  // 128 x t float32 block for the TMA reduce
     static constexpr int kBar = kStaging + kTile * T * 4;
     static constexpr int kBytes = kBar + 256 + 1024 + 4096;
+    // tensor-memory columns: accumulator buffer stride, out_J block inside a buffer, and the block
+    // that K_lo V_hi accumulates into (its own third block here)
+    static constexpr int kAccStride = 256;
+    static constexpr int kAccJ = 128;
+    static constexpr bool kMerged = false;
+    static constexpr int kLoCol = 2 * T;
+};
+
+// Dot form: the operands that the copies bring in live in rings of their own, so that no copy
+// waits on the entry tiles. Two entry buffers [hi | lo], a V_J ring (released by the contraction),
+// a U_J ring (the B-role Gram operand, released by the Gram MMA), one tile-row slot [V_I hi; lo |
+// U_I], the staging tile. Tensor memory: two accumulator buffers of 128 columns, [out_I | out_J],
+// then two 128 x 128 float32 Gram tiles. At t = 32 each direction has 2t = 64 columns: K_lo V_hi
+// accumulates into the K_hi V_lo block (both are the small split corrections, summed in float32
+// by the tensor pipe instead of by the drain); at t = 16 the three t-column blocks fit in 64.
+template <int T, int DP>
+struct TcdLayout {
+    static constexpr int kA = kTile * kTile * 2;
+    static constexpr int kB = T * kTile * 2;
+    static constexpr int kKg = DP <= 4 ? 16 : 32;  // Gram operand width (16-bit values per row)
+    static constexpr int kU = kTile * kKg * 2;
+    static constexpr int kK = 0;                   // entry buffers: 2 x [hi | lo]
+    static constexpr int kV = 4 * kA;              // V_J ring: 2 x [hi; lo]
+    static constexpr int kUr = kV + 4 * kB;        // U_J ring: 2 slots
+    static constexpr int kVi = kUr + 2 * kU;       // tile-row slot: V_I [hi; lo], then U_I
+    static constexpr int kStaging = kVi + 2 * kB + kU;
+    static constexpr int kBar = kStaging + kTile * T * 4;
+    static constexpr int kBytes = kBar + 256 + 1024 + 4096;
+    static constexpr int kAccStride = 128;
+    static constexpr int kAccJ = 64;
+    static constexpr bool kMerged = T == 32;
+    static constexpr int kLoCol = kMerged ? T : 2 * T;
+    static constexpr int kGramCol = 256;
 };
 
 // Instruction descriptor with A read MN-major (bit 15), B K-major, M = 128, N = NCOLS.
@@ -121,6 +164,15 @@ struct TcsArgs {
     const float *col_scale;  // [T] multiplier per column (f16 mode), or nullptr
     int add_mode;            // kAddTma (tm_out is valid), kAddVec4 or kAddScalar
     long long budget;
+    // Distance form. gate (device word, float bits) holds the largest squared norm of the centred
+    // prescaled rows; with gate set, the dot-form kernel runs only when *gate <= gate_lim and the
+    // difference-form kernel only otherwise (both are launched; the other returns at once).
+    const unsigned int *gate;
+    float gate_lim;
+    int dot;                 // host side: launch the dot-form instance
+    const float *arow;       // dot form: a_i, the squared norm of centred row i, [Np]
+    const uint8_t *ua;       // dot form: A-role Gram operand, kU bytes per 128-row tile
+    const uint8_t *ub;       // dot form: B-role Gram operand
 };
 
 // How the drain adds its blocks onto out: TMA bulk tensor reduce (out 16-byte aligned with a row
@@ -141,6 +193,12 @@ __device__ __forceinline__ void tma_reduce_add_2d(const CUtensorMap *map, int c0
     asm volatile("cp.reduce.async.bulk.tensor.2d.global.shared::cta.add.tile.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
                      reinterpret_cast<uint64_t>(map)),
                  "r"(c0), "r"(c1), "r"(src)
+                 : "memory");
+}
+// 1-D bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16), completing on bar
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
                  : "memory");
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
@@ -190,14 +248,51 @@ __device__ __forceinline__ void red_row(float *dst, const float (&s)[NV], const 
     }
 }
 
-template <int KIND, int D, int T, int FMT>
-__global__ void __launch_bounds__(kThreads, 1)
+// Entries from the dot-form Gram value d = 2 x_i . x_j - a_j (tensor memory) and a per-row
+// constant: the squared distance is a_i - d (clamped at 0 against rounding); RBF folds a_i and
+// the exponent offset into its row constant, ls2 - a_i, so that k = 2^(d + ls2 - a_i). The
+// Matern forms are those of Entry2 (mv_tc.cuh) on the reconstructed squared distance.
+template <int KIND> struct DotEntry2;
+template <> struct DotEntry2<LGP_RBF> {
+    static __device__ __forceinline__ float row_const(float ai, float ls2) { return ls2 - ai; }
+    static __device__ __forceinline__ float2 k(float2 d, float2 c, float ls2) {
+        (void)ls2;
+        const float2 arg = __fadd2_rn(d, c);
+        return make_float2(ex2_approx(arg.x), ex2_approx(arg.y));
+    }
+};
+template <> struct DotEntry2<LGP_MATERN52> {
+    static __device__ __forceinline__ float row_const(float ai, float ls2) { (void)ls2; return ai; }
+    static __device__ __forceinline__ float2 k(float2 d, float2 c, float ls2) {
+        float2 rh2 = __ffma2_rn(d, make_float2(-1.0f, -1.0f), c);
+        rh2 = make_float2(fmaxf(rh2.x, 0.0f), fmaxf(rh2.y, 0.0f));
+        return tc::Entry2<LGP_MATERN52>::k(rh2, make_float2(ls2, ls2));
+    }
+};
+template <> struct DotEntry2<LGP_MATERN32> {
+    static __device__ __forceinline__ float row_const(float ai, float ls2) { (void)ls2; return ai; }
+    static __device__ __forceinline__ float2 k(float2 d, float2 c, float ls2) {
+        float2 rh2 = __ffma2_rn(d, make_float2(-1.0f, -1.0f), c);
+        rh2 = make_float2(fmaxf(rh2.x, 0.0f), fmaxf(rh2.y, 0.0f));
+        return tc::Entry2<LGP_MATERN32>::k(rh2, make_float2(ls2, ls2));
+    }
+};
+// Matern-1/2 has no dot form (its entries are not smooth in r^2 at r = 0); this stub is never launched.
+template <> struct DotEntry2<LGP_MATERN12> {
+    static __device__ __forceinline__ float row_const(float ai, float ls2) { (void)ls2; return ai; }
+    static __device__ __forceinline__ float2 k(float2 d, float2 c, float ls2) { (void)c; (void)ls2; return d; }
+};
+
+// DOT selects the dot form of the squared distance (D is then 4 or 8, the padded width DP).
+template <int KIND, int D, int T, int FMT, bool DOT = false>
+__global__ void __launch_bounds__(DOT ? kDotThreads : kThreads, 1)
     mv_tcs_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ CUtensorMap tm_v,
                   const __grid_constant__ CUtensorMap tm_out, const TcsArgs a) {
     constexpr int DP = D <= 4 ? 4 : 8;
-    using L = TcsLayout<T, DP>;
+    using L = std::conditional_t<DOT, TcdLayout<T, DP>, TcsLayout<T, DP>>;
     extern __shared__ uint8_t smem_raw[];
     if (a.skip && *a.skip) return;
+    if (a.gate && (__uint_as_float(*a.gate) <= a.gate_lim) != DOT) return;
 
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L::kBar);
@@ -219,20 +314,34 @@ __global__ void __launch_bounds__(kThreads, 1)
     auto bar_vi_full = [&](int b) { return smem_u32(&bars[10 + b]); };
     auto bar_vi_empty = [&](int b) { return smem_u32(&bars[12 + b]); };
     const uint32_t bar_fin = smem_u32(&bars[14]);
+    const uint32_t bar_fin_j = smem_u32(&bars[21]);  // dot form: the out_J issuer's final commit
+    // dot form: the entry buffer / V_J slot, the accumulators and the tile-row slot are released
+    // by both MMA issuers
+    constexpr uint32_t kIssuers = DOT ? 2 : 1;
+    // dot form: Gram tile buffer b in tensor memory written (gram_full), the U_J ring
+    auto bar_gram_full = [&](int b) { return smem_u32(&bars[15 + b]); };
+    auto bar_u_full = [&](int b) { return smem_u32(&bars[17 + b]); };
+    auto bar_u_empty = [&](int b) { return smem_u32(&bars[19 + b]); };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(bar_full(s), 1);
             mbar_init(bar_ready(s), kGenWarps);
-            mbar_init(bar_empty(s), 1);
+            mbar_init(bar_empty(s), kIssuers);
         }
         for (int b = 0; b < 2; ++b) {
-            mbar_init(bar_acc_full(b), 1);
+            mbar_init(bar_acc_full(b), kIssuers);
             mbar_init(bar_acc_empty(b), 4);
             mbar_init(bar_vi_full(b), 1);
-            mbar_init(bar_vi_empty(b), 1);
+            mbar_init(bar_vi_empty(b), kIssuers);
         }
         mbar_init(bar_fin, 1);
+        mbar_init(bar_fin_j, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(bar_gram_full(b), 1);
+            mbar_init(bar_u_full(b), 1);
+            mbar_init(bar_u_empty(b), 1);
+        }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_async_smem();
@@ -252,198 +361,448 @@ __global__ void __launch_bounds__(kThreads, 1)
     w.init(t0, a.nb);
 
     if (warp == kProducerWarp) {
-        // ------------------------------------------------------------ producer (TMA)
-        if (lane == 0) {
-            int last_it[kStages] = {-1, -1};
-            int last_sg[2] = {-1, -1};
-            int sg = -1;
-            for (int it = 0; it < n_it; ++it, w.next()) {
-                if (it == 0 || w.J == w.I) {
-                    // new tile row: V_I [hi; lo] (two 64-row chunks) into slot sg & 1
-                    ++sg;
-                    const int b = sg & 1;
-                    if (sg >= 2 && !mbar_wait(bar_vi_empty(b), ((sg >> 1) - 1) & 1, a.budget, abort_flag, a.err,
-                                              kErrWaitVi, 64))
+        if constexpr (DOT) {
+            // -------------------------------------------------------- producer, dot form
+            // lane 0: the tile-row slot (V_I, U_I) and the V_J ring, released by the contraction;
+            // lane 1: the U_J ring, released by the Gram MMA, so it runs a tile ahead
+            if (lane == 0) {
+                int last_v[2] = {-1, -1};
+                int last_sg = -1;
+                int sg = -1;
+                for (int it = 0; it < n_it; ++it, w.next()) {
+                    if (it == 0 || w.J == w.I) {
+                        ++sg;
+                        if (sg >= 1 &&
+                            !mbar_wait(bar_vi_empty(0), (sg - 1) & 1, a.budget, abort_flag, a.err, kErrWaitVi, 64))
+                            break;
+                        const uint32_t dst = smem_u32(smem + L::kVi);
+                        mbar_arrive_expect_tx(bar_vi_full(0), (uint32_t)(2 * L::kB + L::kU));
+                        tma_load_2d(dst, &tm_v, 0, (2 * w.I) * 2 * T, bar_vi_full(0));
+                        tma_load_2d(dst + L::kB, &tm_v, 0, (2 * w.I + 1) * 2 * T, bar_vi_full(0));
+                        bulk_load(dst + 2 * L::kB, a.ua + (int64_t)w.I * L::kU, (uint32_t)L::kU, bar_vi_full(0));
+                        last_sg = sg;
+                    }
+                    const int s = it & 1;
+                    if (it >= 2 &&
+                        !mbar_wait(bar_empty(s), ((it >> 1) - 1) & 1, a.budget, abort_flag, a.err, kErrWaitEmpty, 64))
                         break;
-                    const uint32_t dst = smem_u32(smem + L::kVi + b * 2 * L::kB);
-                    mbar_arrive_expect_tx(bar_vi_full(b), (uint32_t)(2 * L::kB));
-                    tma_load_2d(dst, &tm_v, 0, (2 * w.I) * 2 * T, bar_vi_full(b));
-                    tma_load_2d(dst + L::kB, &tm_v, 0, (2 * w.I + 1) * 2 * T, bar_vi_full(b));
-                    last_sg[b] = sg;
+                    const uint32_t vdst = smem_u32(smem + L::kV + s * 2 * L::kB);
+                    mbar_arrive_expect_tx(bar_full(s), (uint32_t)(2 * L::kB));
+                    tma_load_2d(vdst, &tm_v, 0, (2 * w.J) * 2 * T, bar_full(s));
+                    tma_load_2d(vdst + L::kB, &tm_v, 0, (2 * w.J + 1) * 2 * T, bar_full(s));
+                    last_v[s] = it;
                 }
-                const int s = it % kStages;
-                if (it >= kStages &&
-                    !mbar_wait(bar_empty(s), ((it / kStages) - 1) & 1, a.budget, abort_flag, a.err, kErrWaitEmpty, 64))
-                    break;
-                uint8_t *st = smem + s * L::kStage;
-                mbar_arrive_expect_tx(bar_full(s), (uint32_t)(2 * L::kB + L::kX));
-                const uint32_t xdst = smem_u32(st + 2 * L::kA + 2 * L::kB);
-                tma_load_2d(xdst, &tm_x, w.J * kTile, 0, bar_full(s));
-                tma_load_2d(xdst + L::kX / 2, &tm_x, w.J * kTile + 64, 0, bar_full(s));
-                const uint32_t vdst = smem_u32(st + 2 * L::kA);
-                tma_load_2d(vdst, &tm_v, 0, (2 * w.J) * 2 * T, bar_full(s));
-                tma_load_2d(vdst + L::kB, &tm_v, 0, (2 * w.J + 1) * 2 * T, bar_full(s));
-                last_it[s] = it;
+                if (*abort_flag) {
+                    volatile int no_abort = 0;
+                    for (int s = 0; s < 2; ++s)
+                        if (last_v[s] >= 0) mbar_wait(bar_full(s), (last_v[s] >> 1) & 1, kDrainBudget, &no_abort, a.err, 0);
+                    if (last_sg >= 0) mbar_wait(bar_vi_full(0), last_sg & 1, kDrainBudget, &no_abort, a.err, 0);
+                }
+            } else if (lane == 1) {
+                int last_u[2] = {-1, -1};
+                for (int it = 0; it < n_it; ++it, w.next()) {
+                    const int s = it & 1;
+                    if (it >= 2 &&
+                        !mbar_wait(bar_u_empty(s), ((it >> 1) - 1) & 1, a.budget, abort_flag, a.err, kErrWaitEmpty, 64))
+                        break;
+                    mbar_arrive_expect_tx(bar_u_full(s), (uint32_t)L::kU);
+                    bulk_load(smem_u32(smem + L::kUr + s * L::kU), a.ub + (int64_t)w.J * L::kU, (uint32_t)L::kU,
+                              bar_u_full(s));
+                    last_u[s] = it;
+                }
+                if (*abort_flag) {
+                    volatile int no_abort = 0;
+                    for (int s = 0; s < 2; ++s)
+                        if (last_u[s] >= 0) mbar_wait(bar_u_full(s), (last_u[s] >> 1) & 1, kDrainBudget, &no_abort, a.err, 0);
+                }
             }
-            if (*abort_flag) {
-                // drain the copies this thread issued
-                volatile int no_abort = 0;
-                for (int s = 0; s < kStages; ++s)
-                    if (last_it[s] >= 0)
-                        mbar_wait(bar_full(s), (last_it[s] / kStages) & 1, kDrainBudget, &no_abort, a.err, 0);
-                for (int b = 0; b < 2; ++b)
-                    if (last_sg[b] >= 0)
-                        mbar_wait(bar_vi_full(b), (last_sg[b] >> 1) & 1, kDrainBudget, &no_abort, a.err, 0);
+        } else {
+            // ------------------------------------------------------------ producer (TMA)
+            if (lane == 0) {
+                int last_it[kStages] = {-1, -1};
+                int last_sg[2] = {-1, -1};
+                int sg = -1;
+                for (int it = 0; it < n_it; ++it, w.next()) {
+                    if (it == 0 || w.J == w.I) {
+                        // new tile row: V_I [hi; lo] (two 64-row chunks) into slot sg & 1
+                        ++sg;
+                        const int b = sg & 1;
+                        if (sg >= 2 && !mbar_wait(bar_vi_empty(b), ((sg >> 1) - 1) & 1, a.budget, abort_flag, a.err,
+                                                  kErrWaitVi, 64))
+                            break;
+                        const uint32_t dst = smem_u32(smem + L::kVi + b * 2 * L::kB);
+                        mbar_arrive_expect_tx(bar_vi_full(b), (uint32_t)(2 * L::kB));
+                        tma_load_2d(dst, &tm_v, 0, (2 * w.I) * 2 * T, bar_vi_full(b));
+                        tma_load_2d(dst + L::kB, &tm_v, 0, (2 * w.I + 1) * 2 * T, bar_vi_full(b));
+                        last_sg[b] = sg;
+                    }
+                    const int s = it % kStages;
+                    if (it >= kStages &&
+                        !mbar_wait(bar_empty(s), ((it / kStages) - 1) & 1, a.budget, abort_flag, a.err, kErrWaitEmpty, 64))
+                        break;
+                    uint8_t *st = smem + s * L::kStage;
+                    mbar_arrive_expect_tx(bar_full(s), (uint32_t)(2 * L::kB + L::kX));
+                    const uint32_t xdst = smem_u32(st + 2 * L::kA + 2 * L::kB);
+                    tma_load_2d(xdst, &tm_x, w.J * kTile, 0, bar_full(s));
+                    tma_load_2d(xdst + L::kX / 2, &tm_x, w.J * kTile + 64, 0, bar_full(s));
+                    const uint32_t vdst = smem_u32(st + 2 * L::kA);
+                    tma_load_2d(vdst, &tm_v, 0, (2 * w.J) * 2 * T, bar_full(s));
+                    tma_load_2d(vdst + L::kB, &tm_v, 0, (2 * w.J + 1) * 2 * T, bar_full(s));
+                    last_it[s] = it;
+                }
+                if (*abort_flag) {
+                    // drain the copies this thread issued
+                    volatile int no_abort = 0;
+                    for (int s = 0; s < kStages; ++s)
+                        if (last_it[s] >= 0)
+                            mbar_wait(bar_full(s), (last_it[s] / kStages) & 1, kDrainBudget, &no_abort, a.err, 0);
+                    for (int b = 0; b < 2; ++b)
+                        if (last_sg[b] >= 0)
+                            mbar_wait(bar_vi_full(b), (last_sg[b] >> 1) & 1, kDrainBudget, &no_abort, a.err, 0);
+                }
             }
         }
     } else if (warp == kMmaWarp) {
-        // ------------------------------------------------------------ MMA issuer
-        if (lane == 0) {
-            const uint32_t idesc2 = tc::instr_desc<2 * T, FMT>();  // K_hi x [V_hi V_lo]
-            const uint32_t idesc1 = tc::instr_desc<T, FMT>();      // K_lo x V_hi
-            const uint32_t idesc2t = instr_desc_amn<2 * T, FMT>();
-            const uint32_t idesc1t = instr_desc_amn<T, FMT>();
-            bool issued = false;
-            int sg = -1;
-            for (int it = 0; it < n_it; ++it) {
-                const bool seg_first = it == 0 || w.J == w.I;
-                const bool diag = w.J == w.I;
-                const int I = w.I;
-                w.next();
-                const bool seg_last = it == n_it - 1 || w.I != I;
-                if (seg_first) ++sg;
-                const int s = it % kStages;
-                const int buf = it & 1;
-                if (it >= 2 &&
-                    !mbar_wait(bar_acc_empty(buf), ((it >> 1) - 1) & 1, a.budget, abort_flag, a.err, kErrWaitAcc, 32))
-                    break;
-                if (seg_first &&
-                    !mbar_wait(bar_vi_full(sg & 1), (sg >> 1) & 1, a.budget, abort_flag, a.err, kErrWaitVi, 32))
-                    break;
-                if (!mbar_wait(bar_ready(s), (it / kStages) & 1, a.budget, abort_flag, a.err, kErrWaitReady, 32)) break;
-                tc_fence_after();
-                const uint32_t acc_i = tmem_acc + (uint32_t)(buf * 256);
-                const uint32_t acc_j = acc_i + 128;
-                const uint32_t st = smem_u32(smem + s * L::kStage);
-                const uint32_t b_vj = st + 2 * L::kA;
-                const uint32_t b_vi = smem_u32(smem + L::kVi + (sg & 1) * 2 * L::kB);
-                // A core matrix (row group rg of i, column group kg of j) at (kg * 16 + rg) * 128 bytes.
-                // K-major read (K = j): step ks covers kg = 2ks, 2ks+1: start + ks * 4096, K-group stride
-                // 2048, row-group stride 128. MN-major read (M = j, K = i): step ks covers rg = 2ks, 2ks+1:
-                // start + ks * 256, K-group (rg) stride 128, M-group (kg) stride 2048.
-                // B (V tile, 128 rows): core matrix (column group cg of the stacked 2t, row group kg) at
-                // (kg * 2t/8 + cg) * 128 bytes.
+        if constexpr (DOT) {
+            // -------------------------------------------------------- MMA issuer (Gram, out_I), dot form
+            if (lane == 0) {
+                const uint32_t idesc2 = tc::instr_desc<2 * T, FMT>();  // K_hi x [V_hi V_lo]
+                const uint32_t idesc1 = tc::instr_desc<T, FMT>();      // K_lo x V_hi
+                const uint32_t idg = tc::instr_desc<kTile, kFmtF16>();  // Gram: M = N = 128, float16
+                // K_lo V_hi starts its own block (first K step) or adds onto K_hi V_lo (merged)
+                const uint32_t lo_first = L::kMerged ? 1u : 0u;
+                bool issued = false;
+                // Gram tile of tile it_g into tensor-memory buffer it_g & 1: A = the tile-row operand
+                // U_I, B = U_J from the ring. The ring runs two tiles ahead of the contraction: Gram
+                // it + 2 is issued right after contraction it (the generation warps have finished tile
+                // it, so buffer it & 1 has been read), unless tile it + 2 opens a tile row whose U_I
+                // can only load once the current row's last contraction has been issued.
+                TileWalk wg = w;
+                int it_g = 0, sg_g = -1;
+                auto issue_gram = [&]() -> bool {
+                    const int su = it_g & 1;
+                    if (!mbar_wait(bar_u_full(su), (it_g >> 1) & 1, a.budget, abort_flag, a.err, kErrWaitFull, 32))
+                        return false;
+                    if (it_g == 0 || wg.J == wg.I) {
+                        ++sg_g;
+                        if (!mbar_wait(bar_vi_full(0), sg_g & 1, a.budget, abort_flag, a.err, kErrWaitVi, 32))
+                            return false;
+                    }
+                    tc_fence_after();
+                    const uint32_t ua = smem_u32(smem + L::kVi + 2 * L::kB);
+                    const uint32_t ub = smem_u32(smem + L::kUr + su * L::kU);
+                    const uint32_t dg = tmem_acc + (uint32_t)(L::kGramCol + su * kTile);
 #pragma unroll
-                for (int ks = 0; ks < kTile / 16; ++ks) {
-                    const uint32_t first = ks == 0 ? 0u : 1u;
-                    const uint64_t dbv = smem_desc(b_vj + ks * 2 * (2 * T) * 16, 2 * T * 16, 128);
-                    mma_ss(acc_i, smem_desc(st + ks * 4096, 2048, 128), dbv, idesc2, first);
-                    mma_ss(acc_i + 2 * T, smem_desc(st + L::kA + ks * 4096, 2048, 128), dbv, idesc1, first);
-                }
-                if (!diag) {
+                    for (int ks = 0; ks < L::kKg / 16; ++ks)
+                        mma_ss(dg, smem_desc(ua + ks * 4096, 2048, 128), smem_desc(ub + ks * 4096, 2048, 128), idg,
+                               ks == 0 ? 0u : 1u);
+                    mma_commit(bar_u_empty(su));
+                    mma_commit(bar_gram_full(su));
+                    issued = true;
+                    ++it_g;
+                    wg.next();
+                    return true;
+                };
+                // Gram tiles up to tile `limit`, stopping at a tile that opens a new row while an
+                // earlier tile (before `limit`) of the current row still needs its contraction
+                auto issue_grams = [&](int limit, int last_contracted) -> bool {
+                    while (it_g < n_it && it_g <= limit) {
+                        const bool opens_row = it_g > 0 && wg.J == wg.I;
+                        if (opens_row && it_g - 1 > last_contracted) break;
+                        if (!issue_gram()) return false;
+                    }
+                    return true;
+                };
+                bool ok = issue_grams(1, -1);
+                for (int it = 0; ok && it < n_it; ++it) {
+                    const int I = w.I;
+                    w.next();
+                    const bool seg_last = it == n_it - 1 || w.I != I;
+                    const int s = it & 1;
+                    const int buf = it & 1;
+                    // a Gram tile held back at a row change (tile it opens the row) goes out now
+                    if (!issue_grams(it, it - 1)) break;
+                    if (it >= 2 &&
+                        !mbar_wait(bar_acc_empty(buf), ((it >> 1) - 1) & 1, a.budget, abort_flag, a.err, kErrWaitAcc, 32))
+                        break;
+                    if (!mbar_wait(bar_full(s), (it >> 1) & 1, a.budget, abort_flag, a.err, kErrWaitFull, 32)) break;
+                    if (!mbar_wait(bar_ready(s), (it >> 1) & 1, a.budget, abort_flag, a.err, kErrWaitReady, 32)) break;
+                    tc_fence_after();
+                    const uint32_t acc_i = tmem_acc + (uint32_t)(buf * L::kAccStride);
+                    const uint32_t ka = smem_u32(smem + L::kK + s * 2 * L::kA);
+                    const uint32_t b_vj = smem_u32(smem + L::kV + s * 2 * L::kB);
+                    // descriptors as in the difference form (entry buffer ka in place of the stage)
 #pragma unroll
                     for (int ks = 0; ks < kTile / 16; ++ks) {
                         const uint32_t first = ks == 0 ? 0u : 1u;
-                        const uint64_t dbv = smem_desc(b_vi + ks * 2 * (2 * T) * 16, 2 * T * 16, 128);
-                        mma_ss(acc_j, smem_desc(st + ks * 256, 128, 2048), dbv, idesc2t, first);
-                        mma_ss(acc_j + 2 * T, smem_desc(st + L::kA + ks * 256, 128, 2048), dbv, idesc1t, first);
+                        const uint64_t dbv = smem_desc(b_vj + ks * 2 * (2 * T) * 16, 2 * T * 16, 128);
+                        mma_ss(acc_i, smem_desc(ka + ks * 4096, 2048, 128), dbv, idesc2, first);
+                        mma_ss(acc_i + L::kLoCol, smem_desc(ka + L::kA + ks * 4096, 2048, 128), dbv, idesc1,
+                               first | lo_first);
                     }
+                    mma_commit(bar_empty(s));  // V_J slot and entry buffer s (with the out_J issuer)
+                    mma_commit(bar_acc_full(buf));
+                    if (seg_last) mma_commit(bar_vi_empty(0));  // U_I read by this row's Gram tiles
+                    if (!issue_grams(it + 2, it)) break;
                 }
-                mma_commit(bar_empty(s));
-                mma_commit(bar_acc_full(buf));
-                if (seg_last) mma_commit(bar_vi_empty(sg & 1));
-                issued = true;
+                if (issued) {
+                    // every MMA this thread issued has completed before the CTA frees tensor memory
+                    mma_commit(bar_fin);
+                    volatile int no_abort = 0;
+                    mbar_wait(bar_fin, 0, kDrainBudget, &no_abort, a.err, 0);
+                }
             }
-            if (issued) {
-                // every MMA this thread issued has completed before the CTA frees tensor memory
-                mma_commit(bar_fin);
-                volatile int no_abort = 0;
-                mbar_wait(bar_fin, 0, kDrainBudget, &no_abort, a.err, 0);
+        } else {
+            // ------------------------------------------------------------ MMA issuer
+            if (lane == 0) {
+                const uint32_t idesc2 = tc::instr_desc<2 * T, FMT>();  // K_hi x [V_hi V_lo]
+                const uint32_t idesc1 = tc::instr_desc<T, FMT>();      // K_lo x V_hi
+                const uint32_t idesc2t = instr_desc_amn<2 * T, FMT>();
+                const uint32_t idesc1t = instr_desc_amn<T, FMT>();
+                bool issued = false;
+                int sg = -1;
+                for (int it = 0; it < n_it; ++it) {
+                    const bool seg_first = it == 0 || w.J == w.I;
+                    const bool diag = w.J == w.I;
+                    const int I = w.I;
+                    w.next();
+                    const bool seg_last = it == n_it - 1 || w.I != I;
+                    if (seg_first) ++sg;
+                    const int s = it % kStages;
+                    const int buf = it & 1;
+                    if (it >= 2 &&
+                        !mbar_wait(bar_acc_empty(buf), ((it >> 1) - 1) & 1, a.budget, abort_flag, a.err, kErrWaitAcc, 32))
+                        break;
+                    if (seg_first &&
+                        !mbar_wait(bar_vi_full(sg & 1), (sg >> 1) & 1, a.budget, abort_flag, a.err, kErrWaitVi, 32))
+                        break;
+                    if (!mbar_wait(bar_ready(s), (it / kStages) & 1, a.budget, abort_flag, a.err, kErrWaitReady, 32)) break;
+                    tc_fence_after();
+                    const uint32_t acc_i = tmem_acc + (uint32_t)(buf * 256);
+                    const uint32_t acc_j = acc_i + 128;
+                    const uint32_t st = smem_u32(smem + s * L::kStage);
+                    const uint32_t b_vj = st + 2 * L::kA;
+                    const uint32_t b_vi = smem_u32(smem + L::kVi + (sg & 1) * 2 * L::kB);
+                    // A core matrix (row group rg of i, column group kg of j) at (kg * 16 + rg) * 128 bytes.
+                    // K-major read (K = j): step ks covers kg = 2ks, 2ks+1: start + ks * 4096, K-group stride
+                    // 2048, row-group stride 128. MN-major read (M = j, K = i): step ks covers rg = 2ks, 2ks+1:
+                    // start + ks * 256, K-group (rg) stride 128, M-group (kg) stride 2048.
+                    // B (V tile, 128 rows): core matrix (column group cg of the stacked 2t, row group kg) at
+                    // (kg * 2t/8 + cg) * 128 bytes.
+    #pragma unroll
+                    for (int ks = 0; ks < kTile / 16; ++ks) {
+                        const uint32_t first = ks == 0 ? 0u : 1u;
+                        const uint64_t dbv = smem_desc(b_vj + ks * 2 * (2 * T) * 16, 2 * T * 16, 128);
+                        mma_ss(acc_i, smem_desc(st + ks * 4096, 2048, 128), dbv, idesc2, first);
+                        mma_ss(acc_i + 2 * T, smem_desc(st + L::kA + ks * 4096, 2048, 128), dbv, idesc1, first);
+                    }
+                    if (!diag) {
+    #pragma unroll
+                        for (int ks = 0; ks < kTile / 16; ++ks) {
+                            const uint32_t first = ks == 0 ? 0u : 1u;
+                            const uint64_t dbv = smem_desc(b_vi + ks * 2 * (2 * T) * 16, 2 * T * 16, 128);
+                            mma_ss(acc_j, smem_desc(st + ks * 256, 128, 2048), dbv, idesc2t, first);
+                            mma_ss(acc_j + 2 * T, smem_desc(st + L::kA + ks * 256, 128, 2048), dbv, idesc1t, first);
+                        }
+                    }
+                    mma_commit(bar_empty(s));
+                    mma_commit(bar_acc_full(buf));
+                    if (seg_last) mma_commit(bar_vi_empty(sg & 1));
+                    issued = true;
+                }
+                if (issued) {
+                    // every MMA this thread issued has completed before the CTA frees tensor memory
+                    mma_commit(bar_fin);
+                    volatile int no_abort = 0;
+                    mbar_wait(bar_fin, 0, kDrainBudget, &no_abort, a.err, 0);
+                }
             }
         }
     } else if (warp < kGenWarps) {
-        // ------------------------------------------------------------ generation (warps 0-15)
-        const int kg0 = warp & 7;    // column groups kg0 and kg0 + 8 of every tile
-        const int half = warp >> 3;  // rows 64*half .. 64*half + 63
-        const float2 m1 = make_float2(-1.0f, -1.0f);
-        const float2 ls2 = make_float2(a.log2s2, a.log2s2);
-        const float2 acc_init = tc::Entry2<KIND>::acc0(ls2);
-        float2 xi2[2][D];
-        for (int it = 0; it < n_it; ++it, w.next()) {
-            if (it == 0 || w.J == w.I) {
-                // this thread's 2 rows of tile row I, each coordinate duplicated into both halves of
-                // a float2 (rows < Np because Np % 128 == 0)
-#pragma unroll
-                for (int r = 0; r < 2; ++r) {
-                    const float *xr = a.Xs + ((int64_t)w.I * kTile + 64 * half + 32 * r + lane) * DP;
-#pragma unroll
-                    for (int d = 0; d < D; ++d) xi2[r][d] = make_float2(xr[d], xr[d]);
-                }
-            }
-            const int s = it % kStages;
-            const bool got = mbar_wait(bar_full(s), (it / kStages) & 1, a.budget, abort_flag, a.err, kErrWaitFull);
-            if (!__all_sync(0xffffffffu, got)) break;
-            uint8_t *st = smem + s * L::kStage;
-            // the two 64-column passes: unrolled when D is small (short bodies), kept as a loop for
-            // larger D (measured faster, smaller code)
-            constexpr int kPassUnroll = D <= 4 ? 2 : 1;
-#pragma unroll kPassUnroll
-            for (int p = 0; p < 2; ++p) {
-                const int kg = kg0 + 8 * p;
-                const float *xs = reinterpret_cast<const float *>(st + 2 * L::kA + 2 * L::kB + p * (L::kX / 2));
-                float k[2][8];
-#pragma unroll
-                for (int jh = 0; jh < 2; ++jh) {
-                    // columns j = 8*kg + 4*jh + {0,1} (pair 0) and {2,3} (pair 1): the squared
-                    // distances of 2 rows x 4 columns accumulate one coordinate at a time
-                    float2 r2[2][2];
-#pragma unroll
-                    for (int r = 0; r < 2; ++r) r2[r][0] = r2[r][1] = acc_init;
-#pragma unroll
-                    for (int d = 0; d < D; ++d) {
-                        const float4 q = *reinterpret_cast<const float4 *>(xs + d * 64 + 8 * kg0 + 4 * jh);
-                        const float2 xa = make_float2(q.x, q.y), xb = make_float2(q.z, q.w);
-#pragma unroll
-                        for (int r = 0; r < 2; ++r) {
-                            const float2 da = __ffma2_rn(xa, m1, xi2[r][d]);
-                            const float2 db = __ffma2_rn(xb, m1, xi2[r][d]);
-                            r2[r][0] = __ffma2_rn(da, da, r2[r][0]);
-                            r2[r][1] = __ffma2_rn(db, db, r2[r][1]);
-                        }
-                    }
-#pragma unroll
-                    for (int r = 0; r < 2; ++r) {
-#pragma unroll
-                        for (int jp = 0; jp < 2; ++jp) {
-                            const float2 kv = tc::Entry2<KIND>::k(r2[r][jp], ls2);
-                            k[r][4 * jh + 2 * jp] = kv.x;
-                            k[r][4 * jh + 2 * jp + 1] = kv.y;
-                        }
-                    }
-                }
-                uint8_t *ahi = st;
-                uint8_t *alo = st + L::kA;
-#pragma unroll
-                for (int r = 0; r < 2; ++r) {
+        if constexpr (DOT) {
+            // ------------------------------------------------------------ generation, dot form (warps 0-15)
+            // Warp w reads tensor-memory lanes 32 (w % 4) .. +31 (its rows i of the tile) and Gram
+            // columns 32 (w / 4) .. +31 (j): 32 entries per thread.
+            const int q = warp & 3, cb = warp >> 2;
+            const int rloc = 32 * q + lane;
+            const uint32_t taddr = tmem_acc + ((uint32_t)(32 * q) << 16) + (uint32_t)(L::kGramCol + 32 * cb);
+            const float2 m1 = make_float2(-1.0f, -1.0f);
+            const float ls2 = a.log2s2;
+            float ci = 0.0f;
+            for (int it = 0; it < n_it; ++it, w.next()) {
+                if (it == 0 || w.J == w.I) ci = DotEntry2<KIND>::row_const(a.arow[(int64_t)w.I * kTile + rloc], ls2);
+                // Gram tile it (buffer it & 1), and entry buffer it & 1 released by both issuers'
+                // products of tile it - 2
+                bool got = mbar_wait(bar_gram_full(it & 1), (it >> 1) & 1, a.budget, abort_flag, a.err, kErrWaitGram);
+                if (it >= 2 && got)
+                    got = mbar_wait(bar_empty(it & 1), ((it >> 1) - 1) & 1, a.budget, abort_flag, a.err, kErrWaitEmpty);
+                if (!__all_sync(0xffffffffu, got)) break;
+                tc_fence_after();
+                uint32_t g[32];
+                tmem_ld<32>(taddr + (uint32_t)((it & 1) * kTile), g);
+                tmem_wait_ld();
+                // the MMA thread reuses this Gram buffer after this tile's ready arrival below, which
+                // follows the fence
+                tc_fence_before();
+                const int s = it & 1;
+                uint8_t *st = smem + L::kK + s * 2 * L::kA;  // entry buffer s: [hi | lo]
+                const float2 c2 = make_float2(ci, ci);
+    #pragma unroll
+                for (int u = 0; u < 4; ++u) {
                     uint32_t h[4], l[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        h[u] = tc::pack2<FMT>(k[r][2 * u], k[r][2 * u + 1]);
+    #pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        const float2 dv = make_float2(__uint_as_float(g[8 * u + 2 * v]), __uint_as_float(g[8 * u + 2 * v + 1]));
+                        const float2 kv = DotEntry2<KIND>::k(dv, c2, ls2);
+                        h[v] = tc::pack2<FMT>(kv.x, kv.y);
                         float h0, h1;
-                        tc::unpack2<FMT>(h[u], h0, h1);
-                        const float2 lo =
-                            __ffma2_rn(make_float2(h0, h1), m1, make_float2(k[r][2 * u], k[r][2 * u + 1]));
-                        l[u] = tc::pack2<FMT>(lo.x, lo.y);
+                        tc::unpack2<FMT>(h[v], h0, h1);
+                        const float2 lo = __ffma2_rn(make_float2(h0, h1), m1, kv);
+                        l[v] = tc::pack2<FMT>(lo.x, lo.y);
                     }
-                    const int rg = 8 * half + 4 * r + (lane >> 3);
-                    const int off = (kg * 16 + rg) * 128 + (lane & 7) * 16;
-                    *reinterpret_cast<uint4 *>(ahi + off) = make_uint4(h[0], h[1], h[2], h[3]);
-                    *reinterpret_cast<uint4 *>(alo + off) = make_uint4(l[0], l[1], l[2], l[3]);
+                    // columns j = 32 cb + 8 u .. +7 of row rloc: one 16-byte row of core matrix (rg, kg)
+                    const int off = ((4 * cb + u) * 16 + (rloc >> 3)) * 128 + (rloc & 7) * 16;
+                    *reinterpret_cast<uint4 *>(st + off) = make_uint4(h[0], h[1], h[2], h[3]);
+                    *reinterpret_cast<uint4 *>(st + L::kA + off) = make_uint4(l[0], l[1], l[2], l[3]);
+                }
+                fence_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(bar_ready(s));
+            }
+        } else {
+            // ------------------------------------------------------------ generation (warps 0-15)
+            const int kg0 = warp & 7;    // column groups kg0 and kg0 + 8 of every tile
+            const int half = warp >> 3;  // rows 64*half .. 64*half + 63
+            const float2 m1 = make_float2(-1.0f, -1.0f);
+            const float2 ls2 = make_float2(a.log2s2, a.log2s2);
+            const float2 acc_init = tc::Entry2<KIND>::acc0(ls2);
+            float2 xi2[2][D];
+            for (int it = 0; it < n_it; ++it, w.next()) {
+                if (it == 0 || w.J == w.I) {
+                    // this thread's 2 rows of tile row I, each coordinate duplicated into both halves of
+                    // a float2 (rows < Np because Np % 128 == 0)
+    #pragma unroll
+                    for (int r = 0; r < 2; ++r) {
+                        const float *xr = a.Xs + ((int64_t)w.I * kTile + 64 * half + 32 * r + lane) * DP;
+    #pragma unroll
+                        for (int d = 0; d < D; ++d) xi2[r][d] = make_float2(xr[d], xr[d]);
+                    }
+                }
+                const int s = it % kStages;
+                const bool got = mbar_wait(bar_full(s), (it / kStages) & 1, a.budget, abort_flag, a.err, kErrWaitFull);
+                if (!__all_sync(0xffffffffu, got)) break;
+                uint8_t *st = smem + s * L::kStage;
+                // the two 64-column passes: unrolled when D is small (short bodies), kept as a loop for
+                // larger D (measured faster, smaller code)
+                constexpr int kPassUnroll = D <= 4 ? 2 : 1;
+    #pragma unroll kPassUnroll
+                for (int p = 0; p < 2; ++p) {
+                    const int kg = kg0 + 8 * p;
+                    const float *xs = reinterpret_cast<const float *>(st + 2 * L::kA + 2 * L::kB + p * (L::kX / 2));
+                    float k[2][8];
+    #pragma unroll
+                    for (int jh = 0; jh < 2; ++jh) {
+                        // columns j = 8*kg + 4*jh + {0,1} (pair 0) and {2,3} (pair 1): the squared
+                        // distances of 2 rows x 4 columns accumulate one coordinate at a time
+                        float2 r2[2][2];
+    #pragma unroll
+                        for (int r = 0; r < 2; ++r) r2[r][0] = r2[r][1] = acc_init;
+    #pragma unroll
+                        for (int d = 0; d < D; ++d) {
+                            const float4 q = *reinterpret_cast<const float4 *>(xs + d * 64 + 8 * kg0 + 4 * jh);
+                            const float2 xa = make_float2(q.x, q.y), xb = make_float2(q.z, q.w);
+    #pragma unroll
+                            for (int r = 0; r < 2; ++r) {
+                                const float2 da = __ffma2_rn(xa, m1, xi2[r][d]);
+                                const float2 db = __ffma2_rn(xb, m1, xi2[r][d]);
+                                r2[r][0] = __ffma2_rn(da, da, r2[r][0]);
+                                r2[r][1] = __ffma2_rn(db, db, r2[r][1]);
+                            }
+                        }
+    #pragma unroll
+                        for (int r = 0; r < 2; ++r) {
+    #pragma unroll
+                            for (int jp = 0; jp < 2; ++jp) {
+                                const float2 kv = tc::Entry2<KIND>::k(r2[r][jp], ls2);
+                                k[r][4 * jh + 2 * jp] = kv.x;
+                                k[r][4 * jh + 2 * jp + 1] = kv.y;
+                            }
+                        }
+                    }
+                    uint8_t *ahi = st;
+                    uint8_t *alo = st + L::kA;
+    #pragma unroll
+                    for (int r = 0; r < 2; ++r) {
+                        uint32_t h[4], l[4];
+    #pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            h[u] = tc::pack2<FMT>(k[r][2 * u], k[r][2 * u + 1]);
+                            float h0, h1;
+                            tc::unpack2<FMT>(h[u], h0, h1);
+                            const float2 lo =
+                                __ffma2_rn(make_float2(h0, h1), m1, make_float2(k[r][2 * u], k[r][2 * u + 1]));
+                            l[u] = tc::pack2<FMT>(lo.x, lo.y);
+                        }
+                        const int rg = 8 * half + 4 * r + (lane >> 3);
+                        const int off = (kg * 16 + rg) * 128 + (lane & 7) * 16;
+                        *reinterpret_cast<uint4 *>(ahi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+                        *reinterpret_cast<uint4 *>(alo + off) = make_uint4(l[0], l[1], l[2], l[3]);
+                    }
+                }
+                fence_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(bar_ready(s));
+            }
+        }
+    } else if (warp == kMmaWarpJ) {
+        if constexpr (DOT) {
+            // -------------------------------------------------------- MMA issuer (out_J), dot form
+            if (lane == 0) {
+                const uint32_t idesc2t = instr_desc_amn<2 * T, FMT>();  // K_hi^T x [V_hi V_lo]
+                const uint32_t idesc1t = instr_desc_amn<T, FMT>();      // K_lo^T x V_hi
+                const uint32_t lo_first = L::kMerged ? 1u : 0u;
+                bool issued = false;
+                int sg = -1;
+                for (int it = 0; it < n_it; ++it) {
+                    const bool seg_first = it == 0 || w.J == w.I;
+                    const bool diag = w.J == w.I;
+                    const int I = w.I;
+                    w.next();
+                    const bool seg_last = it == n_it - 1 || w.I != I;
+                    if (seg_first) ++sg;
+                    const int s = it & 1;
+                    const int buf = it & 1;
+                    if (it >= 2 &&
+                        !mbar_wait(bar_acc_empty(buf), ((it >> 1) - 1) & 1, a.budget, abort_flag, a.err, kErrWaitAcc, 32))
+                        break;
+                    if (seg_first && !mbar_wait(bar_vi_full(0), sg & 1, a.budget, abort_flag, a.err, kErrWaitVi, 32)) break;
+                    if (!mbar_wait(bar_ready(s), (it >> 1) & 1, a.budget, abort_flag, a.err, kErrWaitReady, 32)) break;
+                    tc_fence_after();
+                    if (!diag) {
+                        const uint32_t acc_j = tmem_acc + (uint32_t)(buf * L::kAccStride + L::kAccJ);
+                        const uint32_t ka = smem_u32(smem + L::kK + s * 2 * L::kA);
+                        const uint32_t b_vi = smem_u32(smem + L::kVi);
+#pragma unroll
+                        for (int ks = 0; ks < kTile / 16; ++ks) {
+                            const uint32_t first = ks == 0 ? 0u : 1u;
+                            const uint64_t dbv = smem_desc(b_vi + ks * 2 * (2 * T) * 16, 2 * T * 16, 128);
+                            mma_ss(acc_j, smem_desc(ka + ks * 256, 128, 2048), dbv, idesc2t, first);
+                            mma_ss(acc_j + L::kLoCol, smem_desc(ka + L::kA + ks * 256, 128, 2048), dbv, idesc1t,
+                                   first | lo_first);
+                        }
+                    }
+                    // (a commit with nothing outstanding arrives at once: diagonal tiles)
+                    mma_commit(bar_empty(s));
+                    mma_commit(bar_acc_full(buf));
+                    if (seg_last) mma_commit(bar_vi_empty(0));
+                    issued = true;
+                }
+                if (issued) {
+                    mma_commit(bar_fin_j);
+                    volatile int no_abort = 0;
+                    mbar_wait(bar_fin_j, 0, kDrainBudget, &no_abort, a.err, 0);
                 }
             }
-            fence_async_smem();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(bar_ready(s));
         }
     } else if (warp >= kDrainWarp0) {
         // ------------------------------------------------------------ drain (warps 18-21)
@@ -479,19 +838,22 @@ __global__ void __launch_bounds__(kThreads, 1)
             const bool got = mbar_wait(bar_acc_full(buf), (it >> 1) & 1, a.budget, abort_flag, a.err, kErrWaitAcc, 128);
             if (!drain_all(got)) break;
             tc_fence_after();
-            const uint32_t base = tmem_acc + (uint32_t)(buf * 256) + ((uint32_t)(32 * quarter) << 16);
-            // blocks of each accumulator: K_hi V_hi at +0, K_hi V_lo at +t, K_lo V_hi at +2t; 8 columns
-            // of the three blocks per round (three loads, one wait)
+            const uint32_t base = tmem_acc + (uint32_t)(buf * L::kAccStride) + ((uint32_t)(32 * quarter) << 16);
+            // blocks of each accumulator: K_hi V_hi at +0, K_hi V_lo at +t, K_lo V_hi at +2t (or, merged,
+            // added onto the +t block by the tensor pipe); 8 columns of each block per round (one wait)
 #pragma unroll
             for (int g = 0; g < T / 8; ++g) {
                 uint32_t v0[8], v1[8], v2[8];
                 tmem_ld<8>(base + (uint32_t)(8 * g), v0);
                 tmem_ld<8>(base + (uint32_t)(T + 8 * g), v1);
-                tmem_ld<8>(base + (uint32_t)(2 * T + 8 * g), v2);
+                if constexpr (!L::kMerged) tmem_ld<8>(base + (uint32_t)(2 * T + 8 * g), v2);
                 tmem_wait_ld();
 #pragma unroll
-                for (int c = 0; c < 8; ++c)
-                    sum_i[8 * g + c] += (__uint_as_float(v0[c]) + __uint_as_float(v1[c])) + __uint_as_float(v2[c]);
+                for (int c = 0; c < 8; ++c) {
+                    float v = __uint_as_float(v0[c]) + __uint_as_float(v1[c]);
+                    if constexpr (!L::kMerged) v += __uint_as_float(v2[c]);
+                    sum_i[8 * g + c] += v;
+                }
             }
             const bool tma = a.add_mode == kAddTma;
             if (!diag) {
@@ -500,14 +862,15 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                 for (int g = 0; g < T / 8; ++g) {
                     uint32_t v0[8], v1[8], v2[8];
-                    tmem_ld<8>(base + 128 + (uint32_t)(8 * g), v0);
-                    tmem_ld<8>(base + 128 + (uint32_t)(T + 8 * g), v1);
-                    tmem_ld<8>(base + 128 + (uint32_t)(2 * T + 8 * g), v2);
+                    tmem_ld<8>(base + L::kAccJ + (uint32_t)(8 * g), v0);
+                    tmem_ld<8>(base + L::kAccJ + (uint32_t)(T + 8 * g), v1);
+                    if constexpr (!L::kMerged) tmem_ld<8>(base + L::kAccJ + (uint32_t)(2 * T + 8 * g), v2);
                     tmem_wait_ld();
                     float sj[8];
 #pragma unroll
                     for (int c = 0; c < 8; ++c) {
-                        sj[c] = (__uint_as_float(v0[c]) + __uint_as_float(v1[c])) + __uint_as_float(v2[c]);
+                        sj[c] = __uint_as_float(v0[c]) + __uint_as_float(v1[c]);
+                        if constexpr (!L::kMerged) sj[c] += __uint_as_float(v2[c]);
                         if (a.col_scale) sj[c] *= a.col_scale[8 * g + c];
                     }
                     if (tma) {

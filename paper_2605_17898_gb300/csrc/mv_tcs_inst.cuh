@@ -7,22 +7,26 @@
 namespace lgp {
 namespace tcs {
 
-template <int KIND, int D, int T, int FMT>
+template <int KIND, int D, int T, int FMT, bool DOT = false>
 cudaError_t launch_tcs_inst(dim3 grid, const CUtensorMap &mx, const CUtensorMap &mv, const CUtensorMap &mo,
                             const TcsArgs &a,
                             cudaStream_t st) {
     constexpr int DP = D <= 4 ? 4 : 8;
-    constexpr int bytes = TcsLayout<T, DP>::kBytes;
+    constexpr int bytes = DOT ? TcdLayout<T, DP>::kBytes : TcsLayout<T, DP>::kBytes;
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(mv_tcs_kernel<KIND, D, T, FMT>,
+        cudaError_t e = cudaFuncSetAttribute(mv_tcs_kernel<KIND, D, T, FMT, DOT>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    mv_tcs_kernel<KIND, D, T, FMT><<<grid, kThreads, bytes, st>>>(mx, mv, mo, a);
+    mv_tcs_kernel<KIND, D, T, FMT, DOT><<<grid, DOT ? kDotThreads : kThreads, bytes, st>>>(mx, mv, mo, a);
     return cudaGetLastError();
 }
+
+// Dot-form instances exist for RBF, Matern-5/2 and Matern-3/2 at the padded widths 4 and 8.
+template <int KIND>
+constexpr bool has_dot_form() { return KIND == LGP_RBF || KIND == LGP_MATERN52 || KIND == LGP_MATERN32; }
 
 template <int KIND, int T, int FMT>
 cudaError_t dispatch_d(int D, dim3 grid, const CUtensorMap &mx, const CUtensorMap &mv, const CUtensorMap &mo,
@@ -46,6 +50,17 @@ cudaError_t dispatch_d(int D, dim3 grid, const CUtensorMap &mx, const CUtensorMa
 template <int FMT, int KIND>
 cudaError_t dispatch_kind(int D, int T, dim3 grid, const CUtensorMap &mx, const CUtensorMap &mv, const CUtensorMap &mo,
                           const TcsArgs &a, cudaStream_t st) {
+    if (a.dot) {
+        if constexpr (has_dot_form<KIND>()) {
+            if (D < 1 || D > 8) return cudaErrorInvalidValue;
+            if (D <= 4)
+                return T == 16 ? launch_tcs_inst<KIND, 4, 16, FMT, true>(grid, mx, mv, mo, a, st)
+                               : launch_tcs_inst<KIND, 4, 32, FMT, true>(grid, mx, mv, mo, a, st);
+            return T == 16 ? launch_tcs_inst<KIND, 8, 16, FMT, true>(grid, mx, mv, mo, a, st)
+                           : launch_tcs_inst<KIND, 8, 32, FMT, true>(grid, mx, mv, mo, a, st);
+        }
+        return cudaErrorInvalidValue;
+    }
     return T == 16 ? dispatch_d<KIND, 16, FMT>(D, grid, mx, mv, mo, a, st)
                    : dispatch_d<KIND, 32, FMT>(D, grid, mx, mv, mo, a, st);
 }

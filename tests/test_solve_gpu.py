@@ -174,3 +174,24 @@ def test_autograd_function(lgp):
     np.testing.assert_allclose(ll.grad.numpy(), -2.0 * g[:p.D], rtol=1e-4)
     assert float(lo.grad) == pytest.approx(-2.0 * g[p.D], rel=1e-4)
     assert float(ln.grad) == pytest.approx(-2.0 * g[p.D + 1], rel=1e-4)
+
+
+def test_host_driven_loop_matches_the_graph_loop(lgp):
+    """LGP_CG_GRAPH=0 (one launch per kernel, done flag read on the host) runs the same kernels as the
+    device-side while loop: on the deterministic FP32 path the solutions agree bit for bit, and the
+    LML info reports the same iterations."""
+    import os
+    p = wl.cfg2(N=3000, kind=wl.MATERN52)
+    B = wl.rhs_block(p.N, 4, seed=12)
+    outs = {}
+    for flag in ("1", "0"):
+        os.environ["LGP_CG_GRAPH"] = flag
+        ctx = lgp.Context(0)
+        x, it, rel, s = lgp.lgp_cg_solve(_dev(p.X), p, _dev(B), tol=1e-6, max_iter=3000, prec=lgp.LGP_PREC_FP32,
+                                         ctx=ctx)
+        assert s == lgp.LGP_OK
+        outs[flag] = (x.cpu().numpy(), it.copy())
+        ctx.close()
+    os.environ.pop("LGP_CG_GRAPH", None)
+    np.testing.assert_array_equal(outs["1"][0], outs["0"][0])
+    np.testing.assert_array_equal(outs["1"][1], outs["0"][1])
