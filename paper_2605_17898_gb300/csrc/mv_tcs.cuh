@@ -69,12 +69,14 @@ constexpr int kStages = 2;
 constexpr int kTmemCols = 512;      // 2 accumulator buffers (+ the Gram tile in the dot form)
 constexpr int kErrWaitVi = 0x100;
 constexpr int kErrWaitGram = 0x200;
-// The dot form adds a second MMA-issuing warp: one thread issues a tcgen05.mma about every 100
-// cycles, while the tensor pipe finishes an M = 128, N <= 64, K = 16 product in about 50, so a
-// single issuer leaves it half idle. Warp 17 issues the Gram tiles and the out_I products, warp 22
-// the out_J products.
+// The dot form issues its MMAs from three warps: one thread issues a tcgen05.mma about every 100
+// cycles (measured), while the tensor pipe finishes an M = 128, N <= 64, K = 16 product in about
+// 50, so a single issuer leaves it half idle; and the Gram tile that the generation warps wait for
+// must not queue behind a contraction's issue. Warp 17 issues the out_I products, warp 22 the
+// out_J products, warp 23 the Gram tiles.
 constexpr int kMmaWarpJ = 22;
-constexpr int kDotThreads = 736;
+constexpr int kGramWarp = 23;
+constexpr int kDotThreads = 768;
 
 // Difference form: a 2-stage ring of [entry tile hi | lo | V_J hi; lo | x_J], two V_I slots.
 template <int T, int DP>
@@ -93,6 +95,7 @@ struct TcsLayout {
     static constexpr int kAccJ = 128;
     static constexpr bool kMerged = false;
     static constexpr int kLoCol = 2 * T;
+    static constexpr int kAccBufs = 2;
 };
 
 // Dot form: the operands that the copies bring in live in rings of their own, so that no copy
@@ -119,6 +122,7 @@ struct TcdLayout {
     static constexpr int kAccJ = 64;
     static constexpr bool kMerged = T == 32;
     static constexpr int kLoCol = kMerged ? T : 2 * T;
+    static constexpr int kAccBufs = 2;
     static constexpr int kGramCol = 256;
 };
 
@@ -283,6 +287,23 @@ template <> struct DotEntry2<LGP_MATERN12> {
     static __device__ __forceinline__ float2 k(float2 d, float2 c, float ls2) { (void)c; (void)ls2; return d; }
 };
 
+// hi/lo split of two entries for the MMA: hi = k rounded to the format's significand (Veltkamp's
+// splitting, t = (2^s + 1) k, hi = t - (t - k), with s = 13 for float16's 11 bits and s = 16 for
+// bfloat16's 8), lo = k - hi (exact), then both packed. The float32 arithmetic replaces the
+// unpacking of the rounded pair that the conversion route needs (one conversion instead of two
+// per pair for hi). Entries stay below 2^16 in magnitude, so t cannot overflow.
+template <int FMT>
+__device__ __forceinline__ void split_pair(float2 k, uint32_t &h, uint32_t &l) {
+    constexpr float c = FMT == kFmtF16 ? 8193.0f : 65537.0f;
+    const float2 m1 = make_float2(-1.0f, -1.0f);
+    const float2 t = __fmul2_rn(k, make_float2(c, c));
+    const float2 u = __ffma2_rn(k, m1, t);   // t - k
+    const float2 hi = __ffma2_rn(u, m1, t);  // t - (t - k)
+    const float2 lo = __ffma2_rn(hi, m1, k);
+    h = tc::pack2<FMT>(hi.x, hi.y);
+    l = tc::pack2<FMT>(lo.x, lo.y);
+}
+
 // DOT selects the dot form of the squared distance (D is then 4 or 8, the padded width DP).
 template <int KIND, int D, int T, int FMT, bool DOT = false>
 __global__ void __launch_bounds__(DOT ? kDotThreads : kThreads, 1)
@@ -296,8 +317,8 @@ __global__ void __launch_bounds__(DOT ? kDotThreads : kThreads, 1)
 
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L::kBar);
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + L::kBar + 192);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + L::kBar + 200);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + L::kBar + 240);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + L::kBar + 248);
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -311,10 +332,14 @@ __global__ void __launch_bounds__(DOT ? kDotThreads : kThreads, 1)
     auto bar_empty = [&](int s) { return smem_u32(&bars[4 + s]); };
     auto bar_acc_full = [&](int b) { return smem_u32(&bars[6 + b]); };
     auto bar_acc_empty = [&](int b) { return smem_u32(&bars[8 + b]); };
+    constexpr int NB = L::kAccBufs;  // accumulator buffers (2)
     auto bar_vi_full = [&](int b) { return smem_u32(&bars[10 + b]); };
     auto bar_vi_empty = [&](int b) { return smem_u32(&bars[12 + b]); };
     const uint32_t bar_fin = smem_u32(&bars[14]);
     const uint32_t bar_fin_j = smem_u32(&bars[21]);  // dot form: the out_J issuer's final commit
+    const uint32_t bar_fin_g = smem_u32(&bars[22]);  // dot form: the Gram issuer's final commit
+    // dot form: generation warps have read Gram buffer b (16 arrivals)
+    auto bar_gram_empty = [&](int b) { return smem_u32(&bars[23 + b]); };
     // dot form: the entry buffer / V_J slot, the accumulators and the tile-row slot are released
     // by both MMA issuers
     constexpr uint32_t kIssuers = DOT ? 2 : 1;
@@ -337,6 +362,9 @@ __global__ void __launch_bounds__(DOT ? kDotThreads : kThreads, 1)
         }
         mbar_init(bar_fin, 1);
         mbar_init(bar_fin_j, 1);
+        mbar_init(bar_fin_g, 1);
+        mbar_init(bar_gram_empty(0), kGenWarps);
+        mbar_init(bar_gram_empty(1), kGenWarps);
         for (int b = 0; b < 2; ++b) {
             mbar_init(bar_gram_full(b), 1);
             mbar_init(bar_u_full(b), 1);
@@ -346,6 +374,9 @@ __global__ void __launch_bounds__(DOT ? kDotThreads : kThreads, 1)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_async_smem();
     }
+    // the per-column epilogue factors (float16 halves), read by the drain from shared memory
+    float *col_scale = reinterpret_cast<float *>(smem + L::kBar + 256);
+    if (a.col_scale && threadIdx.x < T) col_scale[threadIdx.x] = a.col_scale[threadIdx.x];
     if (warp == kMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                      "n"(kTmemCols)
@@ -464,66 +495,18 @@ __global__ void __launch_bounds__(DOT ? kDotThreads : kThreads, 1)
         }
     } else if (warp == kMmaWarp) {
         if constexpr (DOT) {
-            // -------------------------------------------------------- MMA issuer (Gram, out_I), dot form
+            // -------------------------------------------------------- MMA issuer (out_I), dot form
             if (lane == 0) {
                 const uint32_t idesc2 = tc::instr_desc<2 * T, FMT>();  // K_hi x [V_hi V_lo]
                 const uint32_t idesc1 = tc::instr_desc<T, FMT>();      // K_lo x V_hi
-                const uint32_t idg = tc::instr_desc<kTile, kFmtF16>();  // Gram: M = N = 128, float16
                 // K_lo V_hi starts its own block (first K step) or adds onto K_hi V_lo (merged)
                 const uint32_t lo_first = L::kMerged ? 1u : 0u;
                 bool issued = false;
-                // Gram tile of tile it_g into tensor-memory buffer it_g & 1: A = the tile-row operand
-                // U_I, B = U_J from the ring. The ring runs two tiles ahead of the contraction: Gram
-                // it + 2 is issued right after contraction it (the generation warps have finished tile
-                // it, so buffer it & 1 has been read), unless tile it + 2 opens a tile row whose U_I
-                // can only load once the current row's last contraction has been issued.
-                TileWalk wg = w;
-                int it_g = 0, sg_g = -1;
-                auto issue_gram = [&]() -> bool {
-                    const int su = it_g & 1;
-                    if (!mbar_wait(bar_u_full(su), (it_g >> 1) & 1, a.budget, abort_flag, a.err, kErrWaitFull, 32))
-                        return false;
-                    if (it_g == 0 || wg.J == wg.I) {
-                        ++sg_g;
-                        if (!mbar_wait(bar_vi_full(0), sg_g & 1, a.budget, abort_flag, a.err, kErrWaitVi, 32))
-                            return false;
-                    }
-                    tc_fence_after();
-                    const uint32_t ua = smem_u32(smem + L::kVi + 2 * L::kB);
-                    const uint32_t ub = smem_u32(smem + L::kUr + su * L::kU);
-                    const uint32_t dg = tmem_acc + (uint32_t)(L::kGramCol + su * kTile);
-#pragma unroll
-                    for (int ks = 0; ks < L::kKg / 16; ++ks)
-                        mma_ss(dg, smem_desc(ua + ks * 4096, 2048, 128), smem_desc(ub + ks * 4096, 2048, 128), idg,
-                               ks == 0 ? 0u : 1u);
-                    mma_commit(bar_u_empty(su));
-                    mma_commit(bar_gram_full(su));
-                    issued = true;
-                    ++it_g;
-                    wg.next();
-                    return true;
-                };
-                // Gram tiles up to tile `limit`, stopping at a tile that opens a new row while an
-                // earlier tile (before `limit`) of the current row still needs its contraction
-                auto issue_grams = [&](int limit, int last_contracted) -> bool {
-                    while (it_g < n_it && it_g <= limit) {
-                        const bool opens_row = it_g > 0 && wg.J == wg.I;
-                        if (opens_row && it_g - 1 > last_contracted) break;
-                        if (!issue_gram()) return false;
-                    }
-                    return true;
-                };
-                bool ok = issue_grams(1, -1);
-                for (int it = 0; ok && it < n_it; ++it) {
-                    const int I = w.I;
-                    w.next();
-                    const bool seg_last = it == n_it - 1 || w.I != I;
+                for (int it = 0; it < n_it; ++it) {
                     const int s = it & 1;
-                    const int buf = it & 1;
-                    // a Gram tile held back at a row change (tile it opens the row) goes out now
-                    if (!issue_grams(it, it - 1)) break;
-                    if (it >= 2 &&
-                        !mbar_wait(bar_acc_empty(buf), ((it >> 1) - 1) & 1, a.budget, abort_flag, a.err, kErrWaitAcc, 32))
+                    const int buf = it % NB;
+                    if (it >= NB &&
+                        !mbar_wait(bar_acc_empty(buf), ((it / NB) - 1) & 1, a.budget, abort_flag, a.err, kErrWaitAcc, 32))
                         break;
                     if (!mbar_wait(bar_full(s), (it >> 1) & 1, a.budget, abort_flag, a.err, kErrWaitFull, 32)) break;
                     if (!mbar_wait(bar_ready(s), (it >> 1) & 1, a.budget, abort_flag, a.err, kErrWaitReady, 32)) break;
@@ -542,8 +525,7 @@ __global__ void __launch_bounds__(DOT ? kDotThreads : kThreads, 1)
                     }
                     mma_commit(bar_empty(s));  // V_J slot and entry buffer s (with the out_J issuer)
                     mma_commit(bar_acc_full(buf));
-                    if (seg_last) mma_commit(bar_vi_empty(0));  // U_I read by this row's Gram tiles
-                    if (!issue_grams(it + 2, it)) break;
+                    issued = true;
                 }
                 if (issued) {
                     // every MMA this thread issued has completed before the CTA frees tensor memory
@@ -626,7 +608,6 @@ __global__ void __launch_bounds__(DOT ? kDotThreads : kThreads, 1)
             const int q = warp & 3, cb = warp >> 2;
             const int rloc = 32 * q + lane;
             const uint32_t taddr = tmem_acc + ((uint32_t)(32 * q) << 16) + (uint32_t)(L::kGramCol + 32 * cb);
-            const float2 m1 = make_float2(-1.0f, -1.0f);
             const float ls2 = a.log2s2;
             float ci = 0.0f;
             for (int it = 0; it < n_it; ++it, w.next()) {
@@ -641,24 +622,20 @@ __global__ void __launch_bounds__(DOT ? kDotThreads : kThreads, 1)
                 uint32_t g[32];
                 tmem_ld<32>(taddr + (uint32_t)((it & 1) * kTile), g);
                 tmem_wait_ld();
-                // the MMA thread reuses this Gram buffer after this tile's ready arrival below, which
-                // follows the fence
+                // the Gram buffer may be rewritten once every generation warp holds its part
                 tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(bar_gram_empty(it & 1));
                 const int s = it & 1;
                 uint8_t *st = smem + L::kK + s * 2 * L::kA;  // entry buffer s: [hi | lo]
                 const float2 c2 = make_float2(ci, ci);
-    #pragma unroll
+#pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     uint32_t h[4], l[4];
-    #pragma unroll
+#pragma unroll
                     for (int v = 0; v < 4; ++v) {
                         const float2 dv = make_float2(__uint_as_float(g[8 * u + 2 * v]), __uint_as_float(g[8 * u + 2 * v + 1]));
-                        const float2 kv = DotEntry2<KIND>::k(dv, c2, ls2);
-                        h[v] = tc::pack2<FMT>(kv.x, kv.y);
-                        float h0, h1;
-                        tc::unpack2<FMT>(h[v], h0, h1);
-                        const float2 lo = __ffma2_rn(make_float2(h0, h1), m1, kv);
-                        l[v] = tc::pack2<FMT>(lo.x, lo.y);
+                        split_pair<FMT>(DotEntry2<KIND>::k(dv, c2, ls2), h[v], l[v]);
                     }
                     // columns j = 32 cb + 8 u .. +7 of row rloc: one 16-byte row of core matrix (rg, kg)
                     const int off = ((4 * cb + u) * 16 + (rloc >> 3)) * 128 + (rloc & 7) * 16;
@@ -771,9 +748,9 @@ __global__ void __launch_bounds__(DOT ? kDotThreads : kThreads, 1)
                     const bool seg_last = it == n_it - 1 || w.I != I;
                     if (seg_first) ++sg;
                     const int s = it & 1;
-                    const int buf = it & 1;
-                    if (it >= 2 &&
-                        !mbar_wait(bar_acc_empty(buf), ((it >> 1) - 1) & 1, a.budget, abort_flag, a.err, kErrWaitAcc, 32))
+                    const int buf = it % NB;
+                    if (it >= NB &&
+                        !mbar_wait(bar_acc_empty(buf), ((it / NB) - 1) & 1, a.budget, abort_flag, a.err, kErrWaitAcc, 32))
                         break;
                     if (seg_first && !mbar_wait(bar_vi_full(0), sg & 1, a.budget, abort_flag, a.err, kErrWaitVi, 32)) break;
                     if (!mbar_wait(bar_ready(s), (it >> 1) & 1, a.budget, abort_flag, a.err, kErrWaitReady, 32)) break;
@@ -801,6 +778,47 @@ __global__ void __launch_bounds__(DOT ? kDotThreads : kThreads, 1)
                     mma_commit(bar_fin_j);
                     volatile int no_abort = 0;
                     mbar_wait(bar_fin_j, 0, kDrainBudget, &no_abort, a.err, 0);
+                }
+            }
+        }
+    } else if (warp == kGramWarp) {
+        if constexpr (DOT) {
+            // -------------------------------------------------------- MMA issuer (Gram tiles), dot form
+            // Gram tile k into tensor-memory buffer k & 1 (A = the tile-row operand U_I, B = U_J from
+            // the ring) as soon as the generation warps have read Gram tile k - 2 out of that buffer.
+            if (lane == 0) {
+                const uint32_t idg = tc::instr_desc<kTile, kFmtF16>();  // M = N = 128, float16
+                bool issued = false;
+                int sg = -1;
+                for (int k = 0; k < n_it; ++k) {
+                    const bool seg_first = k == 0 || w.J == w.I;
+                    const int I = w.I;
+                    w.next();
+                    const bool seg_last = k == n_it - 1 || w.I != I;
+                    if (seg_first) ++sg;
+                    const int b = k & 1;  // Gram buffer and U_J ring slot
+                    if (k >= 2 &&
+                        !mbar_wait(bar_gram_empty(b), ((k >> 1) - 1) & 1, a.budget, abort_flag, a.err, kErrWaitGram, 32))
+                        break;
+                    if (!mbar_wait(bar_u_full(b), (k >> 1) & 1, a.budget, abort_flag, a.err, kErrWaitFull, 32)) break;
+                    if (seg_first && !mbar_wait(bar_vi_full(0), sg & 1, a.budget, abort_flag, a.err, kErrWaitVi, 32)) break;
+                    tc_fence_after();
+                    const uint32_t ua = smem_u32(smem + L::kVi + 2 * L::kB);
+                    const uint32_t ub = smem_u32(smem + L::kUr + b * L::kU);
+                    const uint32_t dg = tmem_acc + (uint32_t)(L::kGramCol + b * kTile);
+#pragma unroll
+                    for (int ks = 0; ks < L::kKg / 16; ++ks)
+                        mma_ss(dg, smem_desc(ua + ks * 4096, 2048, 128), smem_desc(ub + ks * 4096, 2048, 128), idg,
+                               ks == 0 ? 0u : 1u);
+                    mma_commit(bar_u_empty(b));
+                    mma_commit(bar_gram_full(b));
+                    if (seg_last) mma_commit(bar_vi_empty(0));  // U_I of this row
+                    issued = true;
+                }
+                if (issued) {
+                    mma_commit(bar_fin_g);
+                    volatile int no_abort = 0;
+                    mbar_wait(bar_fin_g, 0, kDrainBudget, &no_abort, a.err, 0);
                 }
             }
         }
@@ -834,25 +852,28 @@ __global__ void __launch_bounds__(DOT ? kDotThreads : kThreads, 1)
             const int I = w.I, J = w.J;
             w.next();
             const bool seg_last = it == n_it - 1 || w.I != I;
-            const int buf = it & 1;
-            const bool got = mbar_wait(bar_acc_full(buf), (it >> 1) & 1, a.budget, abort_flag, a.err, kErrWaitAcc, 128);
+            const int buf = it % NB;
+            const bool got = mbar_wait(bar_acc_full(buf), (it / NB) & 1, a.budget, abort_flag, a.err, kErrWaitAcc, 128);
             if (!drain_all(got)) break;
             tc_fence_after();
             const uint32_t base = tmem_acc + (uint32_t)(buf * L::kAccStride) + ((uint32_t)(32 * quarter) << 16);
             // blocks of each accumulator: K_hi V_hi at +0, K_hi V_lo at +t, K_lo V_hi at +2t (or, merged,
-            // added onto the +t block by the tensor pipe); 8 columns of each block per round (one wait)
+            // added onto the +t block by the tensor pipe); GW columns of each block per round, one wait
+            // per round (16 for two blocks of out_I, else 8: out_J's rounds also hold the staged values)
+            constexpr int GW = L::kMerged ? 16 : 8;
+            constexpr int GWJ = 8;
 #pragma unroll
-            for (int g = 0; g < T / 8; ++g) {
-                uint32_t v0[8], v1[8], v2[8];
-                tmem_ld<8>(base + (uint32_t)(8 * g), v0);
-                tmem_ld<8>(base + (uint32_t)(T + 8 * g), v1);
-                if constexpr (!L::kMerged) tmem_ld<8>(base + (uint32_t)(2 * T + 8 * g), v2);
+            for (int g = 0; g < T / GW; ++g) {
+                uint32_t v0[GW], v1[GW], v2[GW];
+                tmem_ld<GW>(base + (uint32_t)(GW * g), v0);
+                tmem_ld<GW>(base + (uint32_t)(T + GW * g), v1);
+                if constexpr (!L::kMerged) tmem_ld<GW>(base + (uint32_t)(2 * T + GW * g), v2);
                 tmem_wait_ld();
 #pragma unroll
-                for (int c = 0; c < 8; ++c) {
+                for (int c = 0; c < GW; ++c) {
                     float v = __uint_as_float(v0[c]) + __uint_as_float(v1[c]);
                     if constexpr (!L::kMerged) v += __uint_as_float(v2[c]);
-                    sum_i[8 * g + c] += v;
+                    sum_i[GW * g + c] += v;
                 }
             }
             const bool tma = a.add_mode == kAddTma;
@@ -860,26 +881,26 @@ __global__ void __launch_bounds__(DOT ? kDotThreads : kThreads, 1)
                 if (tma) staging_free();
                 const int64_t j = (int64_t)J * kTile + row;
 #pragma unroll
-                for (int g = 0; g < T / 8; ++g) {
-                    uint32_t v0[8], v1[8], v2[8];
-                    tmem_ld<8>(base + L::kAccJ + (uint32_t)(8 * g), v0);
-                    tmem_ld<8>(base + L::kAccJ + (uint32_t)(T + 8 * g), v1);
-                    if constexpr (!L::kMerged) tmem_ld<8>(base + L::kAccJ + (uint32_t)(2 * T + 8 * g), v2);
+                for (int g = 0; g < T / GWJ; ++g) {
+                    uint32_t v0[GWJ], v1[GWJ], v2[GWJ];
+                    tmem_ld<GWJ>(base + L::kAccJ + (uint32_t)(GWJ * g), v0);
+                    tmem_ld<GWJ>(base + L::kAccJ + (uint32_t)(T + GWJ * g), v1);
+                    if constexpr (!L::kMerged) tmem_ld<GWJ>(base + L::kAccJ + (uint32_t)(2 * T + GWJ * g), v2);
                     tmem_wait_ld();
-                    float sj[8];
+                    float sj[GWJ];
 #pragma unroll
-                    for (int c = 0; c < 8; ++c) {
+                    for (int c = 0; c < GWJ; ++c) {
                         sj[c] = __uint_as_float(v0[c]) + __uint_as_float(v1[c]);
                         if constexpr (!L::kMerged) sj[c] += __uint_as_float(v2[c]);
-                        if (a.col_scale) sj[c] *= a.col_scale[8 * g + c];
+                        if (a.col_scale) sj[c] *= col_scale[GWJ * g + c];
                     }
                     if (tma) {
-                        *reinterpret_cast<float4 *>(staging + staging_off<T>(row, 2 * g)) =
-                            make_float4(sj[0], sj[1], sj[2], sj[3]);
-                        *reinterpret_cast<float4 *>(staging + staging_off<T>(row, 2 * g + 1)) =
-                            make_float4(sj[4], sj[5], sj[6], sj[7]);
+#pragma unroll
+                        for (int q = 0; q < GWJ / 4; ++q)
+                            *reinterpret_cast<float4 *>(staging + staging_off<T>(row, (GWJ / 4) * g + q)) =
+                                make_float4(sj[4 * q], sj[4 * q + 1], sj[4 * q + 2], sj[4 * q + 3]);
                     } else if (j < a.N) {
-                        red_row<8>(a.out + j * a.ldo + 8 * g, sj, nullptr, a.add_mode == kAddVec4);
+                        red_row<GWJ>(a.out + j * a.ldo + GWJ * g, sj, nullptr, a.add_mode == kAddVec4);
                     }
                 }
             }
@@ -891,7 +912,7 @@ __global__ void __launch_bounds__(DOT ? kDotThreads : kThreads, 1)
             if (seg_last) {
                 if (a.col_scale) {
 #pragma unroll
-                    for (int c = 0; c < T; ++c) sum_i[c] *= a.col_scale[c];
+                    for (int c = 0; c < T; ++c) sum_i[c] *= col_scale[c];
                 }
                 if (tma) {
                     staging_free();
