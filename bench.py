@@ -36,11 +36,12 @@ METRIC = "matvec pair·RHS evals/s and LML+grad time, N=100k t=32, vs plain FP32
 # `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum` capture (profiles/), valid only for the
 # kernel source it was taken on: the bench reports null once a header of that kernel changes.
 TRAFFIC = {"mv_tc_kernel": {"bytes": None, "source_sha256_16": None},
-           "mv_tcs_kernel": {"bytes": 32.07e6, "source_sha256_16": "c92c1796b459881f"}}
+           "mv_tcs_kernel": {"bytes": 39.05e6, "source_sha256_16": "9261b1c732a80bce"}}
 KERNEL_SOURCES = {"mv_tc_kernel": ["mv_tc.cuh"], "mv_tcs_kernel": ["mv_tcs.cuh", "mv_tc.cuh"]}
 UNIT = "pair*RHS/s"
 SM_COUNT_NOMINAL = 152
 FP32_LANES_PER_SM = 128
+MUFU_EX2_PER_SM = 32
 MAX_SM_MHZ_NOMINAL = 2070.0
 
 
@@ -210,20 +211,26 @@ def flush_l2(buf):
     buf.add_(1.0)
 
 
-def per_pair_ops(kind: int, D: int, split: bool, t: int) -> tuple[float, dict]:
+def per_pair_ops(kind: int, D: int, split: bool, t: int, dot: bool = False) -> tuple[float, dict]:
     """Algorithmic FP32-pipe operations and MUFU operations per generated entry k(x_i, x_j).
 
     Difference form: D subtractions + D multiply-adds for r^2 (RBF starts the
     accumulation at -log2 s^2, so its exponent costs nothing more); Matern-5/2:
     exponent multiply-add, polynomial multiply-add, final multiply-add. Split
     (tensor-core) path: 2 per entry (the lo subtraction and two half-width roundings
-    counted as half an op each); the contraction runs on the tensor pipe. FP32 SIMT
-    path: t multiply-adds. MUFU: RBF one ex2; Matern-5/2 one sqrt and one ex2.
+    counted as half an op each); the contraction runs on the tensor pipe. Dot form:
+    r^2 = a_i - d from the tensor-core Gram value (1 add), the kernel value as above,
+    and the float32 hi/lo split (3 for the rounding, 1 for lo). FP32 SIMT path: t
+    multiply-adds. MUFU: RBF one ex2; the Matern forms one sqrt and one ex2.
     """
     # kernel value beyond the squared distance: RBF 0, M52 3, M12 1 (the exponent), M32 2
-    gen = 2 * D + {0: 0, 1: 3, 2: 1, 3: 2}[kind]
+    kval = {0: 0, 1: 3, 2: 1, 3: 2}[kind]
     mufu = {"ex2": 1.0, "sqrt": 0.0 if kind == 0 else 1.0}
-    return (gen + 2.0, mufu) if split else (gen + t, mufu)
+    if not split:
+        return 2 * D + kval + t, mufu
+    if dot:
+        return 1.0 + kval + 4.0, mufu
+    return 2 * D + kval + 2.0, mufu
 
 
 def run_cpu_baseline(p, t, seconds, seed=0):
@@ -372,33 +379,51 @@ def main():
     mv_ms = statistics.mean(a.elapsed_time(b) for a, b in kev)
     split = kprec in (lgp.LGP_PREC_SPLIT_BF16, lgp.LGP_PREC_SPLIT_F16)
     symmetric = split and ctx.tc_kernel_choice(p.N, p.D, p.kind, args.t, kprec) == lgp.LGP_TC_SYMMETRIC
+    form, norm_max = ctx.tc_distance_form() if symmetric else (lgp.LGP_DIST_NONE, -1.0)
+    dot = form == lgp.LGP_DIST_DOT
     kname = "mv_tcs_kernel" if symmetric else ("mv_tc_kernel" if split else "mv_simt_kernel")
-    ops_pair, mufu_pair = per_pair_ops(p.kind, p.D, split, args.t)
+    ops_pair, mufu_pair = per_pair_ops(p.kind, p.D, split, args.t, dot)
     pairs = float(p.N) ** 2
     # entries the kernel must generate: the symmetric kernel needs each unordered pair once
     entries = float(p.N) * (p.N + 1) / 2 if symmetric else pairs
-    achieved_tops = entries * ops_pair / (mv_ms / 1e3) / 1e12
+    mv_s = mv_ms / 1e3
     props = torch.cuda.get_device_properties(local)
     n_sm = props.multi_processor_count
-    # peak from unit counts and the maximum SM clock: SMs x 128 FP32 lanes x 2070 MHz
-    peak_tops = n_sm * FP32_LANES_PER_SM * MAX_SM_MHZ_NOMINAL * 1e6 / 1e12
     peaks = measured_peaks()
     meas = {name: lgp.lgp_measure_pipe_peak(i) for i, name in
             enumerate(["ffma", "ffma2_fmas", "mufu_ex2", "mufu_sqrt"])}
-    mufu_time = entries * (mufu_pair["ex2"] / meas["mufu_ex2"] + mufu_pair["sqrt"] / meas["mufu_sqrt"])
-    roofline = {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "Tops/s (FP32 pipe)",
-                "frac": achieved_tops / peak_tops,
+    # peaks from unit counts and the maximum SM clock: 128 FP32 lanes, 32 ex2 per SM per cycle (sqrt
+    # at half that rate; both confirmed by the pipe microbenchmarks in measured_pipe_peaks_per_s)
+    fp32_peak = n_sm * FP32_LANES_PER_SM * MAX_SM_MHZ_NOMINAL * 1e6
+    ex2_peak = n_sm * MUFU_EX2_PER_SM * MAX_SM_MHZ_NOMINAL * 1e6
+    mufu_work = entries * (mufu_pair["ex2"] + 2.0 * mufu_pair["sqrt"])  # in ex2 slots
+    kg = 16 if p.D <= 4 else 32
+    tensor_flops = (pairs * 6 * args.t + (entries * 2 * kg if dot else 0.0)) if split else 0.0
+    bf16_peak = peaks["bf16_tflops"] * 1e12
+    t_fp32 = entries * ops_pair / fp32_peak
+    t_mufu = mufu_work / ex2_peak
+    t_tensor = tensor_flops / bf16_peak
+    binding = max([("fp32", t_fp32), ("mufu", t_mufu), ("tensor", t_tensor)], key=lambda x: x[1])[0]
+    if binding == "fp32":
+        achieved, peak, unit = entries * ops_pair / mv_s / 1e12, fp32_peak / 1e12, "Tops/s (FP32 pipe)"
+        psrc = f"{n_sm} SMs x 128 FP32 lanes x 2070 MHz (unit counts and max clock)"
+    elif binding == "mufu":
+        achieved, peak, unit = mufu_work / mv_s / 1e12, ex2_peak / 1e12, "T ex2-slots/s (MUFU; sqrt = 2 slots)"
+        psrc = f"{n_sm} SMs x 32 ex2/cycle x 2070 MHz (unit counts and max clock)"
+    else:
+        achieved, peak, unit = tensor_flops / mv_s / 1e12, bf16_peak / 1e12, "TFLOP/s (tensor, f16/bf16)"
+        psrc = peaks["source"] + " bf16 burst (f16 dense rate = bf16)"
+    roofline = {"bound": "tensor" if binding == "tensor" else "alu", "achieved": achieved, "peak": peak,
+                "unit": unit, "frac": achieved / peak,
                 "traffic": kernel_traffic(kname) if split and p.N == 100000 and args.t == 32 else None,
-                "kernel": kname,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2070 MHz (unit counts and max clock)",
-                "per_entry_ops": ops_pair, "mufu_per_entry": mufu_pair, "matvec_ms": mv_ms,
+                "kernel": kname, "binding_pipe": binding, "peak_source": psrc,
+                "distance_form": {lgp.LGP_DIST_DOT: "dot", lgp.LGP_DIST_DIFF: "difference"}.get(form, None),
+                "centred_norm_max": norm_max if dot else None,
+                "per_entry_fp32_ops": ops_pair, "mufu_per_entry": mufu_pair, "matvec_ms": mv_ms,
                 "entries_per_launch": entries, "pairs_per_launch": pairs, "sm_count": n_sm,
+                "tensor_flops_per_launch": tensor_flops,
+                "pipe_fracs": {"fp32": t_fp32 / mv_s, "mufu": t_mufu / mv_s, "tensor": t_tensor / mv_s},
                 "measured_pipe_peaks_per_s": meas,
-                "frac_of_measured_ffma": achieved_tops * 1e12 / meas["ffma"],
-                "mufu_frac": mufu_time / (mv_ms / 1e3),
-                "tensor_flops_per_launch": pairs * 6 * args.t if split else 0.0,
-                "tensor_frac_of_bf16_burst": (pairs * 6 * args.t / (mv_ms / 1e3)) / (peaks["bf16_tflops"] * 1e12)
-                if split else 0.0,
                 "tensor_peak_source": peaks["source"] + " bf16 burst (f16 dense rate = bf16)"}
 
     # ---------------- end to end through the public API with host buffers

@@ -59,6 +59,11 @@ struct lgp_ctx {
     // the last symmetric-tile product: its kind, padded rows and columns (for the distance-form query)
     int sym_kind = -1, sym_D = 0, sym_t = 0;
     int64_t sym_Np = 0;
+    // prepare_x calls so far; the dot-form operands in vsplit belong to prepared X number dot_version
+    // (built for t columns at workspace address dot_buf), 0 = none
+    uint64_t prep_version = 0, dot_version = 0;
+    int dot_t = 0;
+    void *dot_buf = nullptr;
 };
 
 namespace {
@@ -186,6 +191,7 @@ struct Prepared {
     KernelParams kp;
     int64_t N, Np;
     float *xs;
+    uint64_t version;  // distinguishes successive preparations of the context's xs buffer
 };
 
 lgp_status prepare_x(lgp_ctx *ctx, const lgp_hyper *hyp, const float *X, int64_t N, cudaStream_t st, Prepared *pp) {
@@ -199,6 +205,7 @@ lgp_status prepare_x(lgp_ctx *ctx, const lgp_hyper *hyp, const float *X, int64_t
     s = ensure(ctx, ctx->flags, 64);
     if (s != LGP_OK) return s;
     pp->xs = (float *)ctx->xs.p;
+    pp->version = ++ctx->prep_version;
     launch_prep_x(X, N, pp->kp.D, pp->kp.dpad, pp->kp.scale, pp->xs, pp->Np, (int *)ctx->flags.p, st);
     LGP_CUDA(cudaGetLastError());
     return LGP_OK;
@@ -325,6 +332,26 @@ lgp_status autotune_tc(lgp_ctx *ctx, const Prepared &pp, const float *V, int64_t
     return LGP_OK;
 }
 
+// Whether the dot-form operands of prepared X are in the context's V-split workspace for t columns.
+bool dot_operands_valid(const lgp_ctx *ctx, const Prepared &pp, int t) {
+    return ctx->dot_version == pp.version && ctx->dot_t == t && ctx->dot_buf == ctx->vsplit.p;
+}
+
+// Builds the symmetric product's dot-form operands of prepared X once (not inside the products of a
+// solve, where X does not change); a no-op when the product would not use them.
+lgp_status ensure_dot_operands(lgp_ctx *ctx, const Prepared &pp, int t, int prec, cudaStream_t st) {
+    if (!is_tc(prec) || tc_splits_for(ctx, pp, t, prec) != kTcSymmetric || !dot_form_allowed(pp.kp.kind, pp.kp.D) ||
+        dot_operands_valid(ctx, pp, t))
+        return LGP_OK;
+    lgp_status s = ensure(ctx, ctx->vsplit, (size_t)tc_vsplit_bytes(pp.Np, t));
+    if (s != LGP_OK) return s;
+    LGP_CUDA(launch_dot_operands(pp.kp, pp.xs, pp.N, pp.Np, t, ctx->vsplit.p, nullptr, st));
+    ctx->dot_version = pp.version;
+    ctx->dot_t = t;
+    ctx->dot_buf = ctx->vsplit.p;
+    return LGP_OK;
+}
+
 // K_y V for prepared X. V has row stride ldv; out has row stride ldo.
 lgp_status matvec_prepared(lgp_ctx *ctx, const Prepared &pp, const float *V, int64_t ldv, float *out, int64_t ldo,
                            int t, int prec, const int *skip, cudaStream_t st) {
@@ -335,10 +362,11 @@ lgp_status matvec_prepared(lgp_ctx *ctx, const Prepared &pp, const float *V, int
         const int64_t pf = mv_tc_partial_floats(pp.Np, t, ctx->num_sms, forced);
         s = ensure(ctx, ctx->mv_partial, (size_t)std::max<int64_t>(pf, 1) * sizeof(float));
         if (s != LGP_OK) return s;
+        if ((s = ensure_dot_operands(ctx, pp, t, prec, st)) != LGP_OK) return s;
         LGP_CUDA(launch_mv_tc(pp.kp, pp.xs, pp.N, pp.Np, V, ldv, out, ldo, t, tc_fmt(prec), ctx->vsplit.p,
                               (float *)ctx->mv_partial.p,
                               (int64_t)(ctx->mv_partial.bytes / sizeof(float)), skip, (int *)ctx->flags.p + 1,
-                              ctx->wait_budget, ctx->num_sms, st, forced));
+                              ctx->wait_budget, ctx->num_sms, st, forced, dot_operands_valid(ctx, pp, t)));
         if (forced == kTcSymmetric) {
             ctx->sym_kind = pp.kp.kind;
             ctx->sym_D = pp.kp.D;
@@ -504,7 +532,7 @@ lgp_status build_precond(lgp_ctx *ctx, const lgp_hyper *hyp, const float *X, con
 // Run CG on the internal stream: init, then replay a captured chunk of iterations until done.
 int matvec_launches(const lgp_ctx *ctx, const Prepared &pp, int t, int prec) {
     return is_tc(prec) ? mv_tc_launches(pp.Np, t, ctx->num_sms, tc_fmt(prec), tc_splits_for(ctx, pp, t, prec), pp.kp.kind,
-                                        pp.kp.D)
+                                        pp.kp.D, dot_operands_valid(ctx, pp, t))
                        : mv_simt_launches(pp.N, pp.Np, t, ctx->num_sms);
 }
 
@@ -532,6 +560,8 @@ lgp_status run_cg(lgp_ctx *ctx, const Prepared &pp, const float *B, int64_t ldb,
         const int64_t pf = mv_simt_partial_floats(pp.N, pp.Np, t, ctx->num_sms);
         if ((s = ensure(ctx, ctx->mv_partial, (size_t)std::max<int64_t>(pf, 1) * sizeof(float))) != LGP_OK) return s;
     }
+    // the dot-form operands of X, once for the whole solve (outside the captured loop)
+    if ((s = ensure_dot_operands(ctx, pp, t, prec, st)) != LGP_OK) return s;
     // cg_buffers/ensure may have moved memory: re-read pointers
     s = cg_buffers(ctx, pp.N, pp.Np, t, hist_len, &b);
     if (s != LGP_OK) return s;

@@ -206,15 +206,22 @@ int64_t tc_vsplit_bytes(int64_t Np, int t);
 // forced_splits > 0 overrides the column-split count (the autotuner's choice); 0 = wave-efficiency heuristic;
 // kTcSymmetric = the symmetric-tile kernel (mv_tcs.cuh), which adds onto out instead of writing partials.
 constexpr int kTcSymmetric = -1;
+// dot_operands_ready: the symmetric product's dot-form operands of this Xs are already in vsplit
+// (launch_dot_operands, once per prepared X); otherwise the product builds them first.
 cudaError_t launch_mv_tc(const KernelParams &kp, const float *Xs, int64_t N, int64_t Np, const float *V, int64_t ldv,
                          float *out, int64_t ldo, int t, int fmt, void *vsplit, float *partial, int64_t partial_cap,
                          const int *skip, int *err_flag, long long wait_budget, int num_sms, cudaStream_t st,
-                         int forced_splits = 0);
+                         int forced_splits = 0, bool dot_operands_ready = false);
+// The dot-form distance data of the symmetric product (box, centred split operands, squared norms,
+// the gate word) for prescaled Xs, into the t-column V-split workspace.
+cudaError_t launch_dot_operands(const KernelParams &kp, const float *Xs, int64_t N, int64_t Np, int t, void *vsplit,
+                                const int *skip, cudaStream_t st);
 int64_t mv_tc_partial_floats(int64_t Np, int t, int num_sms);
 int64_t mv_tc_partial_floats(int64_t Np, int t, int num_sms, int forced_splits);
 // Kernels one split tensor-core product launches (the symmetric product with the dot form runs
 // its operand kernels and both gated instances).
-int mv_tc_launches(int64_t Np, int t, int num_sms, int fmt, int forced_splits = 0, int kind = -1, int D = 0);
+int mv_tc_launches(int64_t Np, int t, int num_sms, int fmt, int forced_splits = 0, int kind = -1, int D = 0,
+                   bool dot_operands_ready = false);
 // Up to four kernel choices worth timing: kTcSymmetric (when tc_symmetric_ok) and the three most
 // wave-efficient split counts.
 void tc_split_candidates(int64_t Np, int num_sms, int *cand, int *n);

@@ -114,15 +114,21 @@ __global__ void dot_bbox_kernel(const float *__restrict__ Xs, int64_t N, int dpa
             }
         }
     }
+    // warp, then block, then one global atomic per word and block
+    __shared__ unsigned int blk[16];
+    if (threadIdx.x < 16) blk[threadIdx.x] = 0u;
+    __syncthreads();
 #pragma unroll
     for (int d = 0; d < 8; ++d) {
         const unsigned int h = __reduce_max_sync(0xffffffffu, hi[d]);
         const unsigned int l = __reduce_max_sync(0xffffffffu, lo[d]);
         if ((threadIdx.x & 31) == 0 && d < dpad) {
-            atomicMax(words + d, h);
-            atomicMax(words + 8 + d, l);
+            atomicMax(blk + d, h);
+            atomicMax(blk + 8 + d, l);
         }
     }
+    __syncthreads();
+    if (threadIdx.x < 16 && (threadIdx.x & 7) < dpad) atomicMax(words + threadIdx.x, blk[threadIdx.x]);
 }
 
 // Dot-form distance, step 2: per row j, the centred coordinates u = x - c (c the box centre)
@@ -370,15 +376,33 @@ void tc_split_candidates(int64_t Np, int num_sms, int *cand, int *n) {
     }
 }
 
-int mv_tc_launches(int64_t Np, int t, int num_sms, int fmt, int forced_splits, int kind, int D) {
-    const int dot = forced_splits == kTcSymmetric && dot_form_allowed(kind, D) ? 3 : 0;
+int mv_tc_launches(int64_t Np, int t, int num_sms, int fmt, int forced_splits, int kind, int D, bool dot_operands_ready) {
+    const int dot = forced_splits == kTcSymmetric && dot_form_allowed(kind, D) ? (dot_operands_ready ? 1 : 3) : 0;
     return (mv_tc_partial_floats(Np, t, num_sms, forced_splits) > 0 ? 4 : 3) + (fmt == kFmtF16 ? 1 : 0) + dot;
+}
+
+cudaError_t launch_dot_operands(const KernelParams &kp, const float *Xs, int64_t N, int64_t Np, int t, void *vsplit,
+                                const int *skip, cudaStream_t st) {
+    unsigned int *words = (unsigned int *)((uint8_t *)vsplit + tc_dot_gate_offset(Np, t) - 16 * 4);
+    float *arow = (float *)(words + 32);
+    uint8_t *ua = (uint8_t *)(arow + Np);
+    uint8_t *ub = ua + Np * 64;
+    cudaError_t e = cudaMemsetAsync(words, 0, 32 * sizeof(unsigned int), st);
+    if (e != cudaSuccess) return e;
+    const int bb = (int)std::min<int64_t>((N + 255) / 256, 1024);
+    dot_bbox_kernel<<<bb, 256, 0, st>>>(Xs, N, kp.dpad, words, skip);
+    const int ob = (int)std::min<int64_t>((Np + 255) / 256, 4096);
+    if (kp.dpad <= 4)
+        dot_operands_kernel<4><<<ob, 256, 0, st>>>(Xs, N, Np, words, arow, (uint4 *)ua, (uint4 *)ub, skip);
+    else
+        dot_operands_kernel<8><<<ob, 256, 0, st>>>(Xs, N, Np, words, arow, (uint4 *)ua, (uint4 *)ub, skip);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_mv_tc(const KernelParams &kp, const float *Xs, int64_t N, int64_t Np, const float *V, int64_t ldv,
                          float *out, int64_t ldo, int t, int fmt, void *vsplit, float *partial, int64_t partial_cap,
                          const int *skip, int *err_flag, long long wait_budget, int num_sms, cudaStream_t st,
-                         int forced_splits) {
+                         int forced_splits, bool dot_operands_ready) {
     if (!(t == 16 || t == 32) || Np % 256 != 0) return cudaErrorInvalidValue;
     uint16_t *vs = (uint16_t *)vsplit;  // stacked [V_hi; V_lo], 2 * Np * t entries
     unsigned int *vmax = (unsigned int *)(vs + 2 * Np * t);
@@ -452,22 +476,14 @@ cudaError_t launch_mv_tc(const KernelParams &kp, const float *Xs, int64_t N, int
                                   : tcs::dispatch_bf16(kp.kind, kp.D, t, grid, mx, mv, mo, a, st);
         };
         if (!dot_form_allowed(kp.kind, kp.D)) return launch();
-        // dot form: operands, then both instances; the gate word lets exactly one of them work
+        // dot form: operands (unless the caller built them for this X), then both instances; the gate
+        // word lets exactly one of them work
+        if (!dot_operands_ready && (e = launch_dot_operands(kp, Xs, N, Np, t, vsplit, skip, st)) != cudaSuccess)
+            return e;
         unsigned int *words = (unsigned int *)(XsT + 8 * Np);
         float *arow = (float *)(words + 32);
         uint8_t *ua = (uint8_t *)(arow + Np);
         uint8_t *ub = ua + Np * 64;
-        e = cudaMemsetAsync(words, 0, 32 * sizeof(unsigned int), st);
-        if (e != cudaSuccess) return e;
-        const int bb = (int)std::min<int64_t>((N + 255) / 256, 1024);
-        dot_bbox_kernel<<<bb, 256, 0, st>>>(Xs, N, kp.dpad, words, skip);
-        const int ob = (int)std::min<int64_t>((Np + 255) / 256, 4096);
-        if (kp.dpad <= 4)
-            dot_operands_kernel<4><<<ob, 256, 0, st>>>(Xs, N, Np, words, arow, (uint4 *)ua, (uint4 *)ub, skip);
-        else
-            dot_operands_kernel<8><<<ob, 256, 0, st>>>(Xs, N, Np, words, arow, (uint4 *)ua, (uint4 *)ub, skip);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
         a.gate = words + 16;
         a.gate_lim = dot_gate_limit(kp.kind);
         a.arow = arow;

@@ -165,3 +165,28 @@ def test_dot_form_cg_solve(lgp, sym, kind):
     err = np.linalg.norm(x.cpu().numpy() - ref, axis=0) / np.linalg.norm(ref, axis=0)
     print(f"kind={kind}: iterations {iters.max()}, err {err.max():.2e}")
     assert err.max() <= 1e-4
+
+
+def test_operands_follow_each_new_x(lgp, sym):
+    """The dot-form operands are built once per prepared X and reused by the products of a solve:
+    problems that alternate on one context (one workspace) must never see each other's operands,
+    in single products and in solves (stale operands would give errors of order one)."""
+    import torch
+    probs = [wl.random_problem(2000, 6, wl.MATERN52, seed=seed, lo=0.3, log_noise=math.log(0.1)) for seed in (401, 402)]
+    for p in probs + probs:
+        V = wl.rhs_block(p.N, 32, seed=7)
+        ref = go.matvec(p.X, V, go.hyper_of(p))
+        err = _colerr(_run(lgp, sym, p, V, lgp.LGP_PREC_SPLIT_F16), ref).max()
+        assert sym.tc_distance_form()[0] == lgp.LGP_DIST_DOT
+        assert err <= TOL
+        B = V[:, :16].copy()
+        Ky = go.noisy_kernel_matrix(p.X, go.hyper_of(p))
+        ev = np.linalg.eigvalsh(Ky)
+        gate = max(1e-4, 2e-8 * ev[-1] / ev[0])
+        refx = go.cholesky_solve(Ky, B.astype(np.float64))
+        x, it, rel, s = lgp.lgp_cg_solve(torch.as_tensor(p.X, device="cuda"), p, torch.as_tensor(B, device="cuda"),
+                                         tol=1e-6, max_iter=3000, prec=lgp.LGP_PREC_SPLIT_F16, ctx=sym)
+        assert s == lgp.LGP_OK
+        errx = (np.linalg.norm(x.cpu().numpy() - refx, axis=0) / np.linalg.norm(refx, axis=0)).max()
+        print(f"product err {err:.2e}; solve err {errx:.2e} (gate {gate:.1e}, iterations {it.max()})")
+        assert errx <= gate
