@@ -138,7 +138,7 @@ int32_t lgp_version(void);
 /* Human-readable name of a status code (static storage). */
 const char *lgp_status_string(int32_t status);
 
-/* Environment variables read by a context (none changes results beyond float32 rounding order):
+/* Environment variables read by a context (none changes results beyond float32 rounding):
  *   LGP_AUTOTUNE=0      the tensor-core product keeps the row kernel with its wave-efficiency
  *                       column split instead of timing the candidate kernels on first use of
  *                       a shape;
@@ -149,7 +149,10 @@ const char *lgp_status_string(int32_t status);
  *                       shape, appended after tuning), so later processes skip the timing runs;
  *   LGP_CG_GRAPH=0      run the CG iteration loop from the host (one launch per kernel, the
  *                       done flag read back every 8 iterations) instead of one CUDA graph with
- *                       a device-side while loop; meant for profilers. */
+ *                       a device-side while loop; meant for profilers;
+ *   LGP_DISTANCE=diff   keep the symmetric-tile kernel on the difference form of the squared
+ *                       distance (see lgp_tc_distance_form); its results then differ from the
+ *                       default dot form by that form's rounding (column errors of a few 1e-6). */
 
 /* Create a context bound to CUDA device `device` (its workspace starts empty).
  * Returns LGP_ERR_INVALID_ARG for a NULL ctx or a device that does not exist,

@@ -21,14 +21,30 @@
 // are not 16-byte aligned take per-thread red.global.add instead.) The order of the additions
 // across CTAs is not fixed, so the result can differ between runs in the last bits.
 //
-// CTA structure (one CTA per SM: 22 warps, ~205 KB shared memory, all 512 tensor-memory columns):
+// Two forms of the squared distance, one kernel template (DOT):
+//
+// Difference form (DOT = false; every kernel and D). CTA: one per SM, 22 warps, ~226 KB shared
+// memory, all 512 tensor-memory columns:
 //   warps 0-15  generation: each thread computes 2 rows x 16 columns of the tile (two 8-column
-//               passes) and stores the hi/lo halves;
+//               passes, r^2 from 2D float32 operations on a transposed x_J tile) and stores the
+//               hi/lo halves;
 //   warp 16     producer: TMA of x_J (transposed, two 64-column boxes) and V_J [hi; lo] per
 //               tile into a 2-stage ring, and of V_I once per tile row into a 2-slot buffer;
 //   warp 17     tensor-memory allocation and the MMA issuer (16 or 32 MMAs per tile);
 //   warps 18-21 drain: tensor memory -> registers -> staging tile -> TMA reduce-add.
 // Accumulators: two buffers of [out_I (128 columns) | out_J (128 columns)].
+//
+// Dot form (DOT = true; RBF, Matern-3/2, Matern-5/2 at D >= 3, when the data's spread allows):
+// r^2 = a_i + a_j - 2 u_i . u_j for the box-centred coordinates u, the inner products as one
+// 128 x 128 tensor-core Gram tile per tile (float16 hi/lo operands built once per X by
+// mv_tc.cu), so an entry costs one add, the kernel value and the split. CTA: 24 warps:
+//   warps 0-15  generation from the Gram tile (one row x 32 columns per thread);
+//   warp 16     producer (lane 0: V_J ring and the tile-row slot [V_I | U_I]; lane 1: U_J ring);
+//   warp 17     tensor-memory allocation and the out_I MMAs;  warp 22  the out_J MMAs;
+//   warp 23     the Gram MMAs (two buffers, issued as soon as the generation has read one);
+//   warps 18-21 drain, as above.
+// Both instances are launched; a device word (max |u|^2, written by the operand kernel) makes
+// exactly one of them work.
 // Waits are bounded and abort the CTA as in mv_tc.cuh.
 #pragma once
 
