@@ -1057,8 +1057,10 @@ lgp_status lgp_lml_and_grad(lgp_ctx *ctx, const lgp_hyper *hyp, const float *X, 
         // float32 copy), the P-distributed probes, and P^{-1} of the probe block with the y copy
         const int pc_iter = k > 0 ? 3 : 0;
         const int pc_once = k > 0 ? (2 * k + 3) + 3 + 1 + 4 : 0;
+        // the symmetric product's dot-form operands, built once before the loop (box, operands)
+        const int dot_once = dot_operands_valid(ctx, pp, t) ? 2 : 0;
         info->launches = 3 + 2 + ran * (kChunk * (cg_iteration_launches(ctx, pp, t, prec) + pc_iter) + 1) + 2 + 1 +
-                         (grad ? 3 : 0) + pc_once;
+                         (grad ? 3 : 0) + pc_once + dot_once;
     }
     return cs;
 }
