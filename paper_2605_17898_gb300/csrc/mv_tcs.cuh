@@ -320,6 +320,11 @@ __device__ __forceinline__ void split_pair(float2 k, uint32_t &h, uint32_t &l) {
     l = tc::pack2<FMT>(lo.x, lo.y);
 }
 
+// The dot form's MMA-issue loops over K steps stay rolled (#pragma unroll 1): one issue costs ~100
+// cycles whatever the loop overhead, and the unrolled issue code competes for the instruction cache
+// with the generation warps (measured: the dot-form product is ~25% faster rolled). The difference
+// form's single issuer runs both directions and stays unrolled (rolled, it measured ~6% slower).
+//
 // DOT selects the dot form of the squared distance (D is then 4 or 8, the padded width DP).
 template <int KIND, int D, int T, int FMT, bool DOT = false>
 __global__ void __launch_bounds__(DOT ? kDotThreads : kThreads, 1)
@@ -531,7 +536,7 @@ __global__ void __launch_bounds__(DOT ? kDotThreads : kThreads, 1)
                     const uint32_t ka = smem_u32(smem + L::kK + s * 2 * L::kA);
                     const uint32_t b_vj = smem_u32(smem + L::kV + s * 2 * L::kB);
                     // descriptors as in the difference form (entry buffer ka in place of the stage)
-#pragma unroll
+#pragma unroll 1
                     for (int ks = 0; ks < kTile / 16; ++ks) {
                         const uint32_t first = ks == 0 ? 0u : 1u;
                         const uint64_t dbv = smem_desc(b_vj + ks * 2 * (2 * T) * 16, 2 * T * 16, 128);
@@ -775,7 +780,7 @@ __global__ void __launch_bounds__(DOT ? kDotThreads : kThreads, 1)
                         const uint32_t acc_j = tmem_acc + (uint32_t)(buf * L::kAccStride + L::kAccJ);
                         const uint32_t ka = smem_u32(smem + L::kK + s * 2 * L::kA);
                         const uint32_t b_vi = smem_u32(smem + L::kVi);
-#pragma unroll
+#pragma unroll 1
                         for (int ks = 0; ks < kTile / 16; ++ks) {
                             const uint32_t first = ks == 0 ? 0u : 1u;
                             const uint64_t dbv = smem_desc(b_vi + ks * 2 * (2 * T) * 16, 2 * T * 16, 128);
