@@ -64,6 +64,7 @@ struct lgp_ctx {
     uint64_t prep_version = 0, dot_version = 0;
     int dot_t = 0;
     void *dot_buf = nullptr;
+    size_t dot_buf_bytes = 0;  // with dot_buf: the workspace allocation the operands were written to
 };
 
 namespace {
@@ -334,7 +335,8 @@ lgp_status autotune_tc(lgp_ctx *ctx, const Prepared &pp, const float *V, int64_t
 
 // Whether the dot-form operands of prepared X are in the context's V-split workspace for t columns.
 bool dot_operands_valid(const lgp_ctx *ctx, const Prepared &pp, int t) {
-    return ctx->dot_version == pp.version && ctx->dot_t == t && ctx->dot_buf == ctx->vsplit.p;
+    return ctx->dot_version == pp.version && ctx->dot_t == t && ctx->dot_buf == ctx->vsplit.p &&
+           ctx->dot_buf_bytes == ctx->vsplit.bytes;
 }
 
 // Builds the symmetric product's dot-form operands of prepared X once (not inside the products of a
@@ -349,6 +351,7 @@ lgp_status ensure_dot_operands(lgp_ctx *ctx, const Prepared &pp, int t, int prec
     ctx->dot_version = pp.version;
     ctx->dot_t = t;
     ctx->dot_buf = ctx->vsplit.p;
+    ctx->dot_buf_bytes = ctx->vsplit.bytes;
     return LGP_OK;
 }
 
