@@ -233,6 +233,32 @@ def per_pair_ops(kind: int, D: int, split: bool, t: int, dot: bool = False) -> t
     return 2 * D + kval + 2.0, mufu
 
 
+def binding_pipe(entries: float, pairs: float, ops_pair: float, mufu_pair: dict, t: int, D: int, split: bool,
+                 dot: bool, seconds: float, n_sm: int, bf16_tflops: float) -> dict:
+    """The product's pipe bounds and the one that binds (the largest time bound).
+
+    FP32 pipe: entries x FP32 ops over n_sm x 128 lanes x 2070 MHz. MUFU: entries x (ex2 + 2 sqrt)
+    ex2 slots over n_sm x 32 ex2/cycle x 2070 MHz (sqrt runs at half the ex2 rate). Tensor: N^2 6t
+    contraction flops (+ 2 kg per entry for the dot form's Gram tile, kg = 16 or 32) over the bf16
+    burst peak. Returns achieved and peak in the binding pipe's unit, frac = achieved / peak, and the
+    three time fractions.
+    """
+    fp32_peak = n_sm * FP32_LANES_PER_SM * MAX_SM_MHZ_NOMINAL * 1e6
+    ex2_peak = n_sm * MUFU_EX2_PER_SM * MAX_SM_MHZ_NOMINAL * 1e6
+    mufu_work = entries * (mufu_pair["ex2"] + 2.0 * mufu_pair["sqrt"])
+    kg = 16 if D <= 4 else 32
+    tensor_flops = (pairs * 6 * t + (entries * 2 * kg if dot else 0.0)) if split else 0.0
+    bf16_peak = bf16_tflops * 1e12
+    times = {"fp32": entries * ops_pair / fp32_peak, "mufu": mufu_work / ex2_peak, "tensor": tensor_flops / bf16_peak}
+    binding = max(times, key=times.get)
+    work, peak, unit = {"fp32": (entries * ops_pair, fp32_peak, "Tops/s (FP32 pipe)"),
+                        "mufu": (mufu_work, ex2_peak, "T ex2-slots/s (MUFU; sqrt = 2 slots)"),
+                        "tensor": (tensor_flops, bf16_peak, "TFLOP/s (tensor, f16/bf16)")}[binding]
+    achieved = work / seconds / 1e12
+    return {"binding": binding, "achieved": achieved, "peak": peak / 1e12, "unit": unit, "frac": achieved / (peak / 1e12),
+            "pipe_fracs": {k: v / seconds for k, v in times.items()}, "tensor_flops": tensor_flops}
+
+
 def run_cpu_baseline(p, t, seconds, seed=0):
     """The oracle's FP64 streaming product on a bounded row sample of the workload."""
     import numpy as np
@@ -394,25 +420,12 @@ def main():
             enumerate(["ffma", "ffma2_fmas", "mufu_ex2", "mufu_sqrt"])}
     # peaks from unit counts and the maximum SM clock: 128 FP32 lanes, 32 ex2 per SM per cycle (sqrt
     # at half that rate; both confirmed by the pipe microbenchmarks in measured_pipe_peaks_per_s)
-    fp32_peak = n_sm * FP32_LANES_PER_SM * MAX_SM_MHZ_NOMINAL * 1e6
-    ex2_peak = n_sm * MUFU_EX2_PER_SM * MAX_SM_MHZ_NOMINAL * 1e6
-    mufu_work = entries * (mufu_pair["ex2"] + 2.0 * mufu_pair["sqrt"])  # in ex2 slots
-    kg = 16 if p.D <= 4 else 32
-    tensor_flops = (pairs * 6 * args.t + (entries * 2 * kg if dot else 0.0)) if split else 0.0
-    bf16_peak = peaks["bf16_tflops"] * 1e12
-    t_fp32 = entries * ops_pair / fp32_peak
-    t_mufu = mufu_work / ex2_peak
-    t_tensor = tensor_flops / bf16_peak
-    binding = max([("fp32", t_fp32), ("mufu", t_mufu), ("tensor", t_tensor)], key=lambda x: x[1])[0]
-    if binding == "fp32":
-        achieved, peak, unit = entries * ops_pair / mv_s / 1e12, fp32_peak / 1e12, "Tops/s (FP32 pipe)"
-        psrc = f"{n_sm} SMs x 128 FP32 lanes x 2070 MHz (unit counts and max clock)"
-    elif binding == "mufu":
-        achieved, peak, unit = mufu_work / mv_s / 1e12, ex2_peak / 1e12, "T ex2-slots/s (MUFU; sqrt = 2 slots)"
-        psrc = f"{n_sm} SMs x 32 ex2/cycle x 2070 MHz (unit counts and max clock)"
-    else:
-        achieved, peak, unit = tensor_flops / mv_s / 1e12, bf16_peak / 1e12, "TFLOP/s (tensor, f16/bf16)"
-        psrc = peaks["source"] + " bf16 burst (f16 dense rate = bf16)"
+    bp = binding_pipe(entries, pairs, ops_pair, mufu_pair, args.t, p.D, split, dot, mv_s, n_sm, peaks["bf16_tflops"])
+    binding, achieved, peak, unit = bp["binding"], bp["achieved"], bp["peak"], bp["unit"]
+    tensor_flops = bp["tensor_flops"]
+    psrc = {"fp32": f"{n_sm} SMs x 128 FP32 lanes x 2070 MHz (unit counts and max clock)",
+            "mufu": f"{n_sm} SMs x 32 ex2/cycle x 2070 MHz (unit counts and max clock)",
+            "tensor": peaks["source"] + " bf16 burst (f16 dense rate = bf16)"}[binding]
     roofline = {"bound": "tensor" if binding == "tensor" else "alu", "achieved": achieved, "peak": peak,
                 "unit": unit, "frac": achieved / peak,
                 "traffic": kernel_traffic(kname) if split and p.N == 100000 and args.t == 32 else None,
@@ -422,7 +435,7 @@ def main():
                 "per_entry_fp32_ops": ops_pair, "mufu_per_entry": mufu_pair, "matvec_ms": mv_ms,
                 "entries_per_launch": entries, "pairs_per_launch": pairs, "sm_count": n_sm,
                 "tensor_flops_per_launch": tensor_flops,
-                "pipe_fracs": {"fp32": t_fp32 / mv_s, "mufu": t_mufu / mv_s, "tensor": t_tensor / mv_s},
+                "pipe_fracs": bp["pipe_fracs"],
                 "measured_pipe_peaks_per_s": meas,
                 "tensor_peak_source": peaks["source"] + " bf16 burst (f16 dense rate = bf16)"}
 
