@@ -4,7 +4,10 @@ One step = one log-marginal-likelihood + gradient evaluation (the path of the
 C ABI entry point lgp_lml_and_grad) on the mBCG workload: N=100,000 points in
 D=8 (X ~ U[-1,1]^8), Matern-5/2 with ARD lengthscales log-spaced over [0.3, 2],
 t=32 right-hand sides (y plus 31 Rademacher probes), 50 Lanczos steps, batched
-CG with the split-BF16 tensor-core product, then the adjoint gradient pass.
+CG (tolerance 1e-3) with the split tensor-core product, then the adjoint gradient pass.
+The line also records how far that step's LML and gradient are from a tighter solve,
+the plain FP32 single-column path timed in full at N=20,000 beside the batched path,
+and the device memory the library holds.
 
 value = pair-RHS evaluations per second over the step: every product of the
 step contributes N^2 * t (the CG products and the adjoint pass). ms_per_step is
@@ -54,18 +57,29 @@ def parse():
     ap.add_argument("--N", type=int, default=100000)
     ap.add_argument("--t", type=int, default=32)
     ap.add_argument("--lanczos", type=int, default=50)
-    ap.add_argument("--tol", type=float, default=1e-2)
+    # CG tolerance of the step: at 1e-3 the step's LML and gradient stay within 1e-3 (measured: 3e-4 and 1.2e-4)
+    # of a tol-1e-6 solve on the same draw and probes, which the line's accuracy record re-measures each run
+    ap.add_argument("--tol", type=float, default=1e-3)
     ap.add_argument("--max-iter", type=int, default=1000)
     ap.add_argument("--prec", choices=["auto", "fp32", "split_bf16", "split_f16"], default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--plain", action="store_true", help="also time the plain FP32 single-RHS path")
-    ap.add_argument("--mode", choices=["lml", "matvec", "predict", "batch"], default="lml",
+    ap.add_argument("--mode", choices=["lml", "matvec", "predict", "batch", "memory"], default="lml",
                     help="lml: the LML+grad step (default); matvec: only the product, for kernel profiling; "
                          "predict: posterior mean and variance at --M test points; "
-                         "batch: the 64 uneven GPs of the batch workload in one call vs one call each")
+                         "batch: the 64 uneven GPs of the batch workload in one call vs one call each; "
+                         "memory: device memory of the LML+grad call for N in 1e3..5e5")
     ap.add_argument("--precond-rank", type=int, default=0,
                     help="pivoted-Cholesky preconditioner rank of the CG solves (0: the paper's plain CG)")
+    ap.add_argument("--workload", choices=["cfg3", "cfg4"], default="cfg3",
+                    help="--mode lml problem: cfg3 (N=100000, D=8, Matern-5/2, t=32; the default) or cfg4 "
+                         "(N=50000, D=8, RBF, t=16, 10 hyperparameters; the line adds the adjoint pass's own time)")
+    ap.add_argument("--ref-tol", type=float, default=1e-6,
+                    help="tolerance of the tight solve the timed step's LML and gradient are compared with")
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the accuracy record of the timed step")
+    ap.add_argument("--plain-N", type=int, default=20000,
+                    help="N at which the plain FP32 single-column path is timed in full beside the batched path")
     ap.add_argument("--M", type=int, default=10000, help="test points of --mode predict")
     ap.add_argument("--var-probes", type=int, default=31,
                     help="--mode predict: probes of the variance estimate (0: exact per-point variance)")
@@ -330,8 +344,19 @@ def main():
     prec = {"auto": lgp.LGP_PREC_AUTO, "fp32": lgp.LGP_PREC_FP32, "split_bf16": lgp.LGP_PREC_SPLIT_BF16,
             "split_f16": lgp.LGP_PREC_SPLIT_F16}[args.prec]
 
-    p = wl.cfg3(N=args.N, t=args.t)
+    if args.workload == "cfg4":
+        if args.N == 100000:
+            args.N = 50000
+        if args.t == 32:
+            args.t = 16
+        p = wl.cfg4(N=args.N, t=args.t)
+    else:
+        p = wl.cfg3(N=args.N, t=args.t)
+    kernel_name = {wl.RBF: "rbf", wl.MATERN52: "matern52"}.get(p.kind, str(p.kind))
     m = args.t - 1
+    if args.mode == "memory":
+        bench_memory(lgp, args, dev, prec, rank)
+        return
     if args.mode == "matvec":
         bench_matvec_only(lgp, ctx, p, args, dev, prec, rank)
         return
@@ -439,6 +464,14 @@ def main():
                 "measured_pipe_peaks_per_s": meas,
                 "tensor_peak_source": peaks["source"] + " bf16 burst (f16 dense rate = bf16)"}
 
+    # ---------------- device memory of the step (the library allocates only its O(N) workspace)
+    free_b, total_b = torch.cuda.mem_get_info(dev)
+    memory = {"lgp_workspace_bytes": int(ctx.workspace_bytes),
+              "torch_max_allocated_bytes": int(torch.cuda.max_memory_allocated(dev)),
+              "device_used_bytes": int(total_b - free_b),
+              "note": "workspace: the library's own device buffers (O(N)); torch: the caller's inputs, the "
+                      "kernel-timing blocks and the 256 MB L2-flush buffer; device_used includes the CUDA context"}
+
     # ---------------- end to end through the public API with host buffers
     Xh = torch.as_tensor(p.X).pin_memory()
     yh = torch.as_tensor(p.y).pin_memory()
@@ -467,9 +500,16 @@ def main():
     e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(Xh.numel() * 4 + yh.numel() * 4),
            "d2h_bytes_per_step": int(d2h), "ms_per_step": statistics.mean(e2e_ms)}
 
+    adjoint = None
+    if args.workload == "cfg4":
+        adjoint = time_adjoint(lgp, ctx, p, X, y, args, dev, prec, rank, flush_buf)
+    accuracy = None
+    if not args.no_accuracy:
+        accuracy = bench_accuracy(lgp, ctx, p, X, y, args, prec, 1234 + rank, lml, grad)
     plain = estimate_plain(lgp, ctx, p, X, y, args, dev, iters, ms_per_step)
+    plain["measured_equal_accuracy"] = bench_plain_equal(lgp, args, dev, prec, 1234 + rank)
     if args.plain:
-        plain["measured"] = bench_plain(lgp, ctx, p, X, y, args, dev)
+        plain["measured_full_size"] = bench_plain(lgp, ctx, p, X, y, args, dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -482,7 +522,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": ("f32+f16x3" if kprec == lgp.LGP_PREC_SPLIT_F16 else "f32+bf16x3") if split else "f32",
             "data": "synthetic",
-            "config": {"workload": p.name, "N": p.N, "D": p.D, "t": args.t, "kernel": "matern52",
+            "config": {"workload": p.name, "N": p.N, "D": p.D, "t": args.t, "kernel": kernel_name,
                        "tc_kernel": kname,
                        "lanczos_steps": args.lanczos, "tol": args.tol, "max_iter": args.max_iter,
                        "precond_rank": args.precond_rank,
@@ -491,8 +531,10 @@ def main():
                        "l2": "flushed between steps (256 MB write outside the step events)",
                        "parallelism": f"replicas{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
-            "lml": lml, "grad": [float(g) for g in grad],
+            "lml": lml, "grad": [float(g) for g in grad], "memory": memory, "accuracy": accuracy,
         }
+        if adjoint is not None:
+            line["adjoint"] = adjoint
         if plain is not None:
             line["plain_fp32"] = plain
         print(json.dumps(line), flush=True)
@@ -653,33 +695,151 @@ def estimate_plain(lgp, ctx, p, X, y, args, dev, iters, ms_per_step):
     est = ms[0] + ms[1] * (args.t - 1) + args.t * mv1
     return {"ms_solve_y": ms[0], "ms_solve_probe": ms[1], "iters_y": its[0], "iters_probe": its[1],
             "ms_single_column_product": mv1, "est_ms_per_step": est, "batched_ms_per_step": ms_per_step,
-            "speedup_batched_over_plain": est / ms_per_step,
+            "speedup_batched_over_plain_est": est / ms_per_step,
             "note": "plain = t single-RHS FP32 CG solves (t=1 SIMT product) at the same tol + t single-column "
                     "products for the gradient; y and one probe solve timed, the other probes counted at the "
                     "probe's time"}
 
 
 def bench_plain(lgp, ctx, p, X, y, args, dev):
-    """The plain FP32 path: single-RHS SIMT products, one CG solve per right-hand side."""
-    import numpy as np
+    """The plain FP32 path at the bench's own size: the whole LML+grad step with every column solved on its
+    own (lgp_lml_and_grad with LGP_OPT_SINGLE_RHS), one timed step."""
     import torch
-    from oracle import gp_oracle as go  # probes from the same generator definition (host side only)
-    m = args.t - 1
-    Z = lgp.lgp_rademacher_probes(1234, p.N, m, device=dev.index, ctx=ctx)
-    cols = [y.reshape(-1, 1)] + [Z[:, c:c + 1].contiguous() for c in range(m)]
     torch.cuda.synchronize()
     a = torch.cuda.Event(enable_timing=True)
     b = torch.cuda.Event(enable_timing=True)
     a.record()
-    iters = []
-    for c in cols:
-        _, it, _, _ = lgp.lgp_cg_solve(X, p, c, tol=args.tol, max_iter=args.max_iter, prec=lgp.LGP_PREC_FP32,
-                                       ctx=ctx)
-        iters.append(int(it[0]))
+    lml, grad, info = lgp.lgp_lml_and_grad(X, y, p, n_probes=args.t - 1, lanczos_steps=args.lanczos, seed=1234,
+                                           tol=args.tol, max_iter=args.max_iter, ctx=ctx, single_rhs=True)
     b.record()
     torch.cuda.synchronize()
-    ms = a.elapsed_time(b)
-    return {"ms_solves": ms, "iters": iters, "note": "t single-RHS FP32 CG solves (no adjoint pass)"}
+    return {"ms_per_step": a.elapsed_time(b), "iters_max": info["iters_max"], "lml": lml,
+            "note": "t single-column FP32 CG solves and t single-column adjoint passes, measured"}
+
+
+def bench_plain_equal(lgp, args, dev, prec, seed):
+    """Both paths on the same problem, probes, tolerance and Lanczos length, each timed in full: the batched
+    split-F16 mBCG step and the plain FP32 single-column step (LGP_OPT_SINGLE_RHS), at --plain-N points of
+    the bench workload's distribution (the plain path at N=100000 takes minutes), with the two paths' LML
+    and gradient differences."""
+    import numpy as np
+    import torch
+    import workloads as wl
+    q = wl.cfg4(N=args.plain_N, t=args.t) if args.workload == "cfg4" else wl.cfg3(N=args.plain_N, t=args.t)
+    X = torch.as_tensor(q.X, device=dev)
+    y = torch.as_tensor(q.y, device=dev)
+    ctx = lgp.Context(dev.index or 0)
+    out = {"N": q.N, "workload": q.name, "tol": args.tol, "lanczos_steps": args.lanczos}
+    res = {}
+    for name, single in (("batched", False), ("plain_fp32", True)):
+        def step():
+            return lgp.lgp_lml_and_grad(X, y, q, n_probes=args.t - 1, lanczos_steps=args.lanczos, seed=seed,
+                                        tol=args.tol, max_iter=args.max_iter, prec=prec, ctx=ctx, single_rhs=single)
+        step()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(2):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            lml, grad, info = step()
+            b.record()
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        res[name] = (lml, np.asarray(grad), info)
+        out[name] = {"ms_per_step": statistics.mean(ms), "iters_max": info["iters_max"], "lml": lml,
+                     "precision": {1: "fp32", 2: "split_bf16", 3: "split_f16"}.get(info["prec_used"])}
+    ctx.close()
+    (l0, g0, _), (l1, g1, _) = res["batched"], res["plain_fp32"]
+    gs = np.maximum(np.abs(g1), 1e-2 * np.abs(g1).max())
+    out["lml_rel_diff"] = abs(l0 - l1) / abs(l1)
+    out["grad_rel_diff_max"] = float((np.abs(g0 - g1) / gs).max())
+    out["speedup_batched_over_plain"] = out["plain_fp32"]["ms_per_step"] / out["batched"]["ms_per_step"]
+    return out
+
+
+def bench_accuracy(lgp, ctx, p, X, y, args, prec, seed, lml, grad):
+    """How accurate the timed step is, on the same draw and probes: the true residual of the block solve
+    at the step's tolerance (recomputed with the float32 product, whose own error is ~1e-7), its
+    componentwise backward error, and the LML and gradient shift against a solve at --ref-tol."""
+    import numpy as np
+    import torch
+    m = args.t - 1
+    Z = lgp.lgp_rademacher_probes(seed, p.N, m, device=X.device.index or 0, ctx=ctx)
+    B = torch.cat([y.reshape(-1, 1), Z], dim=1).contiguous()
+    x, iters, rel, _ = lgp.lgp_cg_solve(X, p, B, tol=args.tol, max_iter=args.max_iter, prec=prec, ctx=ctx)
+    Kx = lgp.lgp_kernel_matvec(X, p, x, prec=lgp.LGP_PREC_FP32, ctx=ctx)
+    Kabs = lgp.lgp_kernel_matvec(X, p, x.abs().contiguous(), prec=lgp.LGP_PREC_FP32, ctx=ctx)
+    R = B.double() - Kx.double()
+    res = (torch.linalg.norm(R, dim=0) / torch.linalg.norm(B.double(), dim=0)).cpu().numpy()
+    berr = float((R.abs() / (Kabs.double() + B.double().abs())).max().item())
+    t0 = time.perf_counter()
+    lml_ref, grad_ref, info_ref = lgp.lgp_lml_and_grad(X, y, p, n_probes=m, lanczos_steps=args.lanczos, seed=seed,
+                                                       tol=args.ref_tol, max_iter=20000, prec=prec, ctx=ctx,
+                                                       precond_rank=args.precond_rank)
+    ref_s = time.perf_counter() - t0
+    g = np.asarray(grad)
+    gr = np.asarray(grad_ref)
+    gs = np.maximum(np.abs(gr), 1e-2 * np.abs(gr).max())
+    return {"tol": args.tol, "true_rel_residual_y": float(res[0]), "true_rel_residual_max": float(res.max()),
+            "recursive_rel_residual_max": float(np.max(rel)), "backward_error_max": berr,
+            "ref_tol": args.ref_tol, "ref_iters_max": info_ref["iters_max"], "ref_seconds": ref_s,
+            "lml_ref": lml_ref, "lml_rel_shift": abs(lml - lml_ref) / abs(lml_ref),
+            "grad_rel_shift_max": float((np.abs(g - gr) / gs).max()),
+            "note": "residuals of [y | probes] solved at tol with the step's product, recomputed with the FP32 "
+                    "product over all rows; shifts = |step - tight solve| on the same probes (gradient relative "
+                    "to max(|g_p|, 1e-2 max|g|))"}
+
+
+def time_adjoint(lgp, ctx, p, X, y, args, dev, prec, rank, flush_buf):
+    """The LML call with and without the gradient (the adjoint pass is the difference), 3 timed calls each."""
+    import torch
+    out = {}
+    for name, want in (("lml_only", False), ("lml_and_grad", True)):
+        ms = []
+        for _ in range(3):
+            flush_l2(flush_buf)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            lgp.lgp_lml_and_grad(X, y, p, n_probes=args.t - 1, lanczos_steps=args.lanczos, seed=1234 + rank,
+                                 tol=args.tol, max_iter=args.max_iter, prec=prec, ctx=ctx, want_grad=want)
+            b.record()
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        out[name + "_ms"] = statistics.median(ms)
+    out["adjoint_ms"] = out["lml_and_grad_ms"] - out["lml_only_ms"]
+    out["hyperparameters"] = p.D + 2
+    return out
+
+
+def bench_memory(lgp, args, dev, prec, rank):
+    """Device memory of one LML+grad call (16 CG iterations; the workspace does not depend on the iteration
+    count) on the bench workload's distribution at N = 1e3, 1e4, 1e5, 5e5: the library's workspace grows as
+    O(N) (Sec. 4.4 reports the matrix-free CG path's peak memory flat in N for its single column)."""
+    import torch
+    import workloads as wl
+    rows = []
+    for N in (1000, 10000, 100000, 500000):
+        q = wl.cfg3(N=N, t=args.t)
+        X = torch.as_tensor(q.X, device=dev)
+        y = torch.as_tensor(q.y, device=dev)
+        ctx = lgp.Context(dev.index or 0)
+        torch.cuda.synchronize()
+        free0, _ = torch.cuda.mem_get_info(dev)
+        lgp.lgp_lml_and_grad(X, y, q, n_probes=args.t - 1, lanczos_steps=args.lanczos, seed=1, tol=1e-30,
+                             max_iter=16, prec=prec, ctx=ctx)
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info(dev)
+        ws = ctx.workspace_bytes
+        rows.append({"N": N, "lgp_workspace_bytes": int(ws), "workspace_bytes_per_point": ws / N,
+                     "device_bytes_taken_by_call": int(free0 - free1),
+                     "input_bytes": int(X.numel() * 4 + y.numel() * 4)})
+        ctx.close()
+        del X, y
+    if rank == 0:
+        print(json.dumps({"mode": "memory", "workload": f"cfg3 distribution, D=8, t={args.t}", "rows": rows}),
+              flush=True)
 
 
 if __name__ == "__main__":

@@ -102,10 +102,16 @@ typedef struct {
     int32_t flags;           /* LGP_OPT_* bits, 0 for the defaults */
 } lgp_options;
 
-/* lgp_options.flags: lgp_cg_solve starts from the initial guess held in Xsol on entry instead of
- * x0 = 0 (a warm start, e.g. from the previous optimiser step's solution); columns whose initial
- * residual already meets tol take no iteration. Ignored by the other entry points. */
-enum { LGP_OPT_WARM_START = 1 };
+/* lgp_options.flags:
+ * LGP_OPT_WARM_START: lgp_cg_solve starts from the initial guess held in Xsol on entry instead of
+ *   x0 = 0 (a warm start, e.g. from the previous optimiser step's solution); columns whose initial
+ *   residual already meets tol take no iteration. Ignored by the other entry points.
+ * LGP_OPT_SINGLE_RHS: lgp_lml_and_grad solves the t = 1 + n_probes columns one at a time, each by
+ *   its own CG run with the float32 one-column product, and computes the gradient with one adjoint
+ *   pass per column: the paper's plain single-right-hand-side CG path (Sec. 5), kept as the
+ *   comparison for the batched path. Same estimator and results up to float32 rounding; prec is
+ *   ignored (always FP32); precond_rank must be 0. Ignored by the other entry points. */
+enum { LGP_OPT_WARM_START = 1, LGP_OPT_SINGLE_RHS = 2 };
 
 typedef struct {
     double lml;              /* log marginal likelihood estimate */
@@ -313,12 +319,13 @@ lgp_status lgp_batch_cg_solve(lgp_ctx *ctx, int32_t n_gp, const lgp_hyper *hyp, 
 lgp_status lgp_measure_pipe_peak(int32_t which, double *ops_per_s, lgp_stream stream);
 
 /*
- * Allocation-free K_y V for callers that cannot allocate device memory: code
- * running while a stream is captured into a CUDA graph (allocation calls are not
- * allowed there), programs whose device memory belongs to another allocator, and
- * latency-critical loops where cudaMalloc/cudaFree could synchronise the device.
- * The paper has no counterpart of this entry point; it is a deployment variant of
- * lgp_kernel_matvec's tensor-core path.
+ * Allocation-free K_y V for callers that cannot allocate device memory: programs whose
+ * device memory belongs to another allocator (a framework's caching pool, a fixed arena
+ * sized at start-up) and must not have a library allocate behind their back; services
+ * under a fixed device-memory budget, where an allocation failing mid-request cannot be
+ * retried; and latency-critical loops, where cudaMalloc/cudaFree could synchronise the
+ * device. The paper has no counterpart of this entry point; it is a deployment variant
+ * of lgp_kernel_matvec's tensor-core path (the row kernel).
  *
  * Same arguments and result as lgp_kernel_matvec with prec in {AUTO, SPLIT_F16,
  * SPLIT_BF16} (AUTO = SPLIT_F16), but no context: it works on the current CUDA
@@ -332,12 +339,25 @@ lgp_status lgp_measure_pipe_peak(int32_t which, double *ops_per_s, lgp_stream st
  *   - Every call shares the one array: calls whose work overlaps on the GPU (on
  *     different streams, or from several threads) race and corrupt each other.
  *     Order them on one stream.
- *   - Asynchronous on `stream`; no error word is read back (a NaN/Inf in X or V
- *     propagates to out). Returns LGP_ERR_INVALID_ARG for bad pointers or values,
- *     LGP_ERR_CUDA if a launch fails.
+ *   - Asynchronous on `stream`. The call itself returns LGP_ERR_INVALID_ARG for bad
+ *     pointers or values and LGP_ERR_CUDA if a launch fails; it reads nothing back, so
+ *     LGP_OK does not mean the device work succeeded. If a bounded device-side wait of
+ *     the product runs out, the kernel returns early and `out` is left partly written
+ *     (undefined); a NaN/Inf in X or V propagates to out. Both conditions are recorded
+ *     in status words of the scratch array: see lgp_kernel_matvec_noalloc_status.
  */
 lgp_status lgp_kernel_matvec_noalloc(const lgp_hyper *hyp, const float *X, const float *V, float *out,
                                      int64_t N, int32_t t, int32_t prec, lgp_stream stream);
+
+/*
+ * Status of the allocation-free product calls on the current device since the last
+ * status read (no counterpart in the paper): synchronises `stream`, reads and clears the
+ * scratch array's status words. Returns LGP_ERR_TIMEOUT if a bounded wait ran out in one
+ * of those calls (its `out` is undefined), else LGP_ERR_NONFINITE if one of them had a
+ * NaN/Inf in X, else LGP_OK; LGP_ERR_CUDA if the read fails. Allocates nothing. Work of
+ * those calls still running on other streams must be finished by the caller first.
+ */
+lgp_status lgp_kernel_matvec_noalloc_status(lgp_stream stream);
 
 #ifdef __cplusplus
 }

@@ -53,6 +53,7 @@ EXPORTED = [
     "lgp_kernel_matvec", "lgp_kernel_matvec_grad", "lgp_cg_solve", "lgp_lml_and_grad",
     "lgp_rademacher_probes", "lgp_batch_cg_solve", "lgp_kernel_matvec_noalloc",
     "lgp_measure_pipe_peak", "lgp_tc_kernel_choice", "lgp_predict", "lgp_tc_distance_form",
+    "lgp_kernel_matvec_noalloc_status",
 ]
 
 
@@ -125,6 +126,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
                                     c.POINTER(lgp_options), vp, vp, c.POINTER(lgp_predict_info), vp]),
         "lgp_kernel_matvec_noalloc": (c.c_int32, [c.POINTER(lgp_hyper), vp, vp, vp, c.c_int64, c.c_int32, c.c_int32,
                                                   vp]),
+        "lgp_kernel_matvec_noalloc_status": (c.c_int32, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -267,9 +269,11 @@ def lgp_kernel_matvec(X, hyp, V, prec: int = LGP_PREC_AUTO, out=None, ctx: Conte
 def lgp_kernel_matvec_noalloc(X, hyp, V, out, prec: int = LGP_PREC_AUTO, stream=None) -> int:
     """K_y V into a caller-provided `out` with no device allocation (N <= 8192, t in {16, 32}).
 
-    For callers that cannot allocate device memory (stream capture, foreign allocators,
-    latency-critical loops). Returns the lgp_status; the scratch is a fixed array inside
-    the library, so overlapping calls on different streams race.
+    For callers that cannot allocate device memory (programs whose device memory belongs to
+    another allocator, services under a fixed memory budget, latency-critical loops). Returns
+    the lgp_status of the launch; device-side failures are read with
+    lgp_kernel_matvec_noalloc_status. The scratch is a fixed array inside the library, so
+    overlapping calls on different streams race.
     """
     N, t = V.shape
     h, keep = Hyper.of(hyp).to_c()
@@ -277,6 +281,12 @@ def lgp_kernel_matvec_noalloc(X, hyp, V, out, prec: int = LGP_PREC_AUTO, stream=
                                          _stream_ptr(stream))
     del keep
     return int(s)
+
+
+def lgp_kernel_matvec_noalloc_status(stream=None) -> int:
+    """Synchronise `stream`, then read and clear the status words of the allocation-free product
+    calls on the current device: LGP_OK, LGP_ERR_TIMEOUT or LGP_ERR_NONFINITE."""
+    return int(load().lgp_kernel_matvec_noalloc_status(_stream_ptr(stream)))
 
 
 PIPE_FFMA, PIPE_FFMA2, PIPE_MUFU_EX2, PIPE_MUFU_SQRT = 0, 1, 2, 3
@@ -307,6 +317,7 @@ def lgp_kernel_matvec_grad(X, hyp, W, ctx: Context | None = None, stream=None):
 
 
 LGP_OPT_WARM_START = 1
+LGP_OPT_SINGLE_RHS = 2
 
 
 def _options(tol, max_iter, lanczos_steps=0, n_probes=0, prec=LGP_PREC_AUTO, seed=0, precond_rank=0,
@@ -342,8 +353,9 @@ def lgp_cg_solve(X, hyp, B, tol: float = 1e-6, max_iter: int = 1000, prec: int =
 
 def lgp_lml_and_grad(X, y, hyp, n_probes: int = 15, lanczos_steps: int = 50, seed: int = 0, tol: float = 1e-4,
                      max_iter: int = 1000, prec: int = LGP_PREC_AUTO, want_grad: bool = True,
-                     ctx: Context | None = None, stream=None, precond_rank: int = 0):
-    """LML estimate, its gradient [D+2] (or None) and an info dict."""
+                     ctx: Context | None = None, stream=None, precond_rank: int = 0, single_rhs: bool = False):
+    """LML estimate, its gradient [D+2] (or None) and an info dict. single_rhs=True: the plain path that
+    solves the columns one at a time with the float32 one-column product (LGP_OPT_SINGLE_RHS)."""
     ctx = ctx or default_context(X.device.index or 0)
     N = int(y.shape[0])
     D = int(X.shape[1])
@@ -351,7 +363,8 @@ def lgp_lml_and_grad(X, y, hyp, n_probes: int = 15, lanczos_steps: int = 50, see
     grad = np.zeros(D + 2, dtype=np.float64)
     info = lgp_lml_info()
     h, keep = Hyper.of(hyp).to_c()
-    o = _options(tol, max_iter, lanczos_steps, n_probes, prec, seed, precond_rank)
+    o = _options(tol, max_iter, lanczos_steps, n_probes, prec, seed, precond_rank,
+                 flags=LGP_OPT_SINGLE_RHS if single_rhs else 0)
     s = ctx._check(ctx.lib.lgp_lml_and_grad(ctx.h, ctypes.byref(h), _ptr(X), _ptr(y), N, ctypes.byref(o),
                                             ctypes.byref(lml), grad.ctypes.data_as(ctypes.c_void_p) if want_grad
                                             else None, ctypes.byref(info), _stream_ptr(stream)))

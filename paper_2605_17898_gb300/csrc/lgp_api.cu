@@ -44,6 +44,7 @@ struct lgp_ctx {
     // workspace
     DevBuf xs, mv_partial, cg_vec, cg_partial, cg_state, cg_hist, scal, rhs, adj_b, adj_partial, vsplit, flags;
     DevBuf batch_meta, batch_part, pred_xs, pred_z, pred_q;
+    DevBuf sr_x, sr_state, sr_hist, sr_tmp;  // single-column solves assembled into t columns
     DevBuf pc_l64, pc_l32, pc_d, pc_info, pc_part, pc_u, pc_cinv, pc_gram, pc_e, pc_rhs;
     int64_t ws_bytes = 0;
     // pinned host mirrors
@@ -59,12 +60,15 @@ struct lgp_ctx {
     // the last symmetric-tile product: its kind, padded rows and columns (for the distance-form query)
     int sym_kind = -1, sym_D = 0, sym_t = 0;
     int64_t sym_Np = 0;
-    // prepare_x calls so far; the dot-form operands in vsplit belong to prepared X number dot_version
-    // (built for t columns at workspace address dot_buf), 0 = none
-    uint64_t prep_version = 0, dot_version = 0;
-    int dot_t = 0;
-    void *dot_buf = nullptr;
-    size_t dot_buf_bytes = 0;  // with dot_buf: the workspace allocation the operands were written to
+    // prepare_x calls so far; the X-only operands of the tensor-core products in vsplit (transposed X,
+    // with opnd_dot also the dot-form distance operands) belong to prepared X number opnd_version (built for
+    // opnd_t columns at workspace address opnd_buf), 0 = none
+    uint64_t prep_version = 0, opnd_version = 0;
+    int opnd_t = 0;
+    bool opnd_dot = false;
+    void *opnd_buf = nullptr;
+    size_t opnd_buf_bytes = 0;  // with opnd_buf: the workspace allocation the operands were written to
+    int cg_dist_form = -1;      // distance form baked into the last CG graph (-1: both instances launch)
 };
 
 namespace {
@@ -333,31 +337,39 @@ lgp_status autotune_tc(lgp_ctx *ctx, const Prepared &pp, const float *V, int64_t
     return LGP_OK;
 }
 
-// Whether the dot-form operands of prepared X are in the context's V-split workspace for t columns.
-bool dot_operands_valid(const lgp_ctx *ctx, const Prepared &pp, int t) {
-    return ctx->dot_version == pp.version && ctx->dot_t == t && ctx->dot_buf == ctx->vsplit.p &&
-           ctx->dot_buf_bytes == ctx->vsplit.bytes;
+// Whether the symmetric product of this shape may take the dot form (and so needs its operands).
+bool needs_dot(const lgp_ctx *ctx, const Prepared &pp, int t, int prec) {
+    return is_tc(prec) && tc_splits_for(ctx, pp, t, prec) == kTcSymmetric && dot_form_allowed(pp.kp.kind, pp.kp.D);
 }
 
-// Builds the symmetric product's dot-form operands of prepared X once (not inside the products of a
-// solve, where X does not change); a no-op when the product would not use them.
-lgp_status ensure_dot_operands(lgp_ctx *ctx, const Prepared &pp, int t, int prec, cudaStream_t st) {
-    if (!is_tc(prec) || tc_splits_for(ctx, pp, t, prec) != kTcSymmetric || !dot_form_allowed(pp.kp.kind, pp.kp.D) ||
-        dot_operands_valid(ctx, pp, t))
-        return LGP_OK;
+// Whether the X-only operands of prepared X (for a product of this shape) are in the context's V-split
+// workspace for t columns.
+bool tc_operands_valid(const lgp_ctx *ctx, const Prepared &pp, int t, int prec) {
+    return ctx->opnd_version == pp.version && ctx->opnd_t == t && ctx->opnd_buf == ctx->vsplit.p &&
+           ctx->opnd_buf_bytes == ctx->vsplit.bytes && (ctx->opnd_dot || !needs_dot(ctx, pp, t, prec));
+}
+
+// Builds the X-only operands of the tensor-core products of prepared X once (not inside the products of a
+// solve, where X does not change): the transposed X and, for a symmetric product that may take the dot
+// form, its distance operands.
+lgp_status ensure_tc_operands(lgp_ctx *ctx, const Prepared &pp, int t, int prec, cudaStream_t st) {
+    if (!is_tc(prec) || tc_operands_valid(ctx, pp, t, prec)) return LGP_OK;
     lgp_status s = ensure(ctx, ctx->vsplit, (size_t)tc_vsplit_bytes(pp.Np, t));
     if (s != LGP_OK) return s;
-    LGP_CUDA(launch_dot_operands(pp.kp, pp.xs, pp.N, pp.Np, t, ctx->vsplit.p, nullptr, st));
-    ctx->dot_version = pp.version;
-    ctx->dot_t = t;
-    ctx->dot_buf = ctx->vsplit.p;
-    ctx->dot_buf_bytes = ctx->vsplit.bytes;
+    const bool dot = needs_dot(ctx, pp, t, prec);
+    LGP_CUDA(launch_tc_operands(pp.kp, pp.xs, pp.N, pp.Np, t, ctx->vsplit.p, dot, st));
+    ctx->opnd_version = pp.version;
+    ctx->opnd_t = t;
+    ctx->opnd_dot = dot;
+    ctx->opnd_buf = ctx->vsplit.p;
+    ctx->opnd_buf_bytes = ctx->vsplit.bytes;
     return LGP_OK;
 }
 
 // K_y V for prepared X. V has row stride ldv; out has row stride ldo.
+// dist_form: see launch_mv_tc (-1 unless the caller read the dot-form gate word of this X).
 lgp_status matvec_prepared(lgp_ctx *ctx, const Prepared &pp, const float *V, int64_t ldv, float *out, int64_t ldo,
-                           int t, int prec, const int *skip, cudaStream_t st) {
+                           int t, int prec, const int *skip, cudaStream_t st, int dist_form = -1) {
     if (is_tc(prec)) {
         lgp_status s = ensure(ctx, ctx->vsplit, (size_t)tc_vsplit_bytes(pp.Np, t));
         if (s != LGP_OK) return s;
@@ -365,11 +377,12 @@ lgp_status matvec_prepared(lgp_ctx *ctx, const Prepared &pp, const float *V, int
         const int64_t pf = mv_tc_partial_floats(pp.Np, t, ctx->num_sms, forced);
         s = ensure(ctx, ctx->mv_partial, (size_t)std::max<int64_t>(pf, 1) * sizeof(float));
         if (s != LGP_OK) return s;
-        if ((s = ensure_dot_operands(ctx, pp, t, prec, st)) != LGP_OK) return s;
+        if ((s = ensure_tc_operands(ctx, pp, t, prec, st)) != LGP_OK) return s;
         LGP_CUDA(launch_mv_tc(pp.kp, pp.xs, pp.N, pp.Np, V, ldv, out, ldo, t, tc_fmt(prec), ctx->vsplit.p,
                               (float *)ctx->mv_partial.p,
                               (int64_t)(ctx->mv_partial.bytes / sizeof(float)), skip, (int *)ctx->flags.p + 1,
-                              ctx->wait_budget, ctx->num_sms, st, forced, dot_operands_valid(ctx, pp, t)));
+                              ctx->wait_budget, ctx->num_sms, st, forced, tc_operands_valid(ctx, pp, t, prec),
+                              dist_form));
         if (forced == kTcSymmetric) {
             ctx->sym_kind = pp.kp.kind;
             ctx->sym_D = pp.kp.D;
@@ -533,15 +546,15 @@ lgp_status build_precond(lgp_ctx *ctx, const lgp_hyper *hyp, const float *X, con
 }
 
 // Run CG on the internal stream: init, then replay a captured chunk of iterations until done.
-int matvec_launches(const lgp_ctx *ctx, const Prepared &pp, int t, int prec) {
+int matvec_launches(const lgp_ctx *ctx, const Prepared &pp, int t, int prec, int dist_form = -1) {
     return is_tc(prec) ? mv_tc_launches(pp.Np, t, ctx->num_sms, tc_fmt(prec), tc_splits_for(ctx, pp, t, prec), pp.kp.kind,
-                                        pp.kp.D, dot_operands_valid(ctx, pp, t))
+                                        pp.kp.D, tc_operands_valid(ctx, pp, t, prec), dist_form)
                        : mv_simt_launches(pp.N, pp.Np, t, ctx->num_sms);
 }
 
 // Kernel launches of one CG iteration (the product plus the five vector/scalar kernels).
-int cg_iteration_launches(const lgp_ctx *ctx, const Prepared &pp, int t, int prec) {
-    return matvec_launches(ctx, pp, t, prec) + 5;
+int cg_iteration_launches(const lgp_ctx *ctx, const Prepared &pp, int t, int prec, int dist_form = -1) {
+    return matvec_launches(ctx, pp, t, prec, dist_form) + 5;
 }
 
 lgp_status run_cg(lgp_ctx *ctx, const Prepared &pp, const float *B, int64_t ldb, int t, const lgp_options *opt,
@@ -563,8 +576,21 @@ lgp_status run_cg(lgp_ctx *ctx, const Prepared &pp, const float *B, int64_t ldb,
         const int64_t pf = mv_simt_partial_floats(pp.N, pp.Np, t, ctx->num_sms);
         if ((s = ensure(ctx, ctx->mv_partial, (size_t)std::max<int64_t>(pf, 1) * sizeof(float))) != LGP_OK) return s;
     }
-    // the dot-form operands of X, once for the whole solve (outside the captured loop)
-    if ((s = ensure_dot_operands(ctx, pp, t, prec, st)) != LGP_OK) return s;
+    // the X-only operands of the products, once for the whole solve (outside the captured loop)
+    if ((s = ensure_tc_operands(ctx, pp, t, prec, st)) != LGP_OK) return s;
+    // the symmetric product's distance form, read once per solve from the gate word those operands hold,
+    // so that only the instance of that form is launched in the loop
+    int dist_form = -1;
+    if (needs_dot(ctx, pp, t, prec) && tc_operands_valid(ctx, pp, t, prec)) {
+        unsigned int bits = 0;
+        LGP_CUDA(cudaMemcpyAsync(&bits, (const char *)ctx->vsplit.p + tc_dot_gate_offset(pp.Np, t), sizeof bits,
+                                 cudaMemcpyDeviceToHost, st));
+        LGP_CUDA(cudaStreamSynchronize(st));
+        float amax;
+        std::memcpy(&amax, &bits, sizeof amax);
+        dist_form = amax <= dot_gate_limit(pp.kp.kind) ? 1 : 0;
+    }
+    ctx->cg_dist_form = dist_form;
     // cg_buffers/ensure may have moved memory: re-read pointers
     s = cg_buffers(ctx, pp.N, pp.Np, t, hist_len, &b);
     if (s != LGP_OK) return s;
@@ -572,7 +598,7 @@ lgp_status run_cg(lgp_ctx *ctx, const Prepared &pp, const float *B, int64_t ldb,
 
     if (X0) {
         // warm start: r0 = b - K_y x0 needs one product first (into Kp)
-        if ((s = matvec_prepared(ctx, pp, X0, t, b.Kp, t, t, prec, nullptr, st)) != LGP_OK) return s;
+        if ((s = matvec_prepared(ctx, pp, X0, t, b.Kp, t, t, prec, nullptr, st, dist_form)) != LGP_OK) return s;
     }
     launch_cg_init(B, ldb, pp.N, pp.Np, t, b, opt->tol, opt->max_iter, hist_len, st, X0, t);
     LGP_CUDA(cudaGetLastError());
@@ -584,7 +610,8 @@ lgp_status run_cg(lgp_ctx *ctx, const Prepared &pp, const float *B, int64_t ldb,
         int launched = 0;
         while (true) {
             for (int k = 0; k < kChunk; ++k) {
-                if ((s = matvec_prepared(ctx, pp, b.p, t, b.Kp, t, t, prec, &b.state->done, st)) != LGP_OK) return s;
+                if ((s = matvec_prepared(ctx, pp, b.p, t, b.Kp, t, t, prec, &b.state->done, st, dist_form)) != LGP_OK)
+                    return s;
                 launch_cg_after_matvec(pp.N, pp.Np, t, b, st);
             }
             launch_cg_chunk_tally(b.state, st);
@@ -609,6 +636,7 @@ lgp_status run_cg(lgp_ctx *ctx, const Prepared &pp, const float *B, int64_t ldb,
     put(&pp.xs, sizeof pp.xs);
     put(&t, sizeof t);
     put(&prec, sizeof prec);
+    put(&dist_form, sizeof dist_form);
     // the buffers field by field (the structs have padding bytes)
     const void *ptrs[] = {b.x, b.r, b.p, b.Kp, b.z, b.partial, b.state, b.hist_alpha, b.hist_beta,
                           b.pc.L64, b.pc.L32, b.pc.Cinv, b.pc.part, b.pc.U};
@@ -654,7 +682,7 @@ lgp_status run_cg(lgp_ctx *ctx, const Prepared &pp, const float *B, int64_t ldb,
         }
         lgp_status cs = LGP_OK;
         for (int k = 0; k < kChunk && cs == LGP_OK; ++k) {
-            cs = matvec_prepared(ctx, pp, b.p, t, b.Kp, t, t, prec, &b.state->done, st);
+            cs = matvec_prepared(ctx, pp, b.p, t, b.Kp, t, t, prec, &b.state->done, st, dist_form);
             if (cs == LGP_OK) launch_cg_after_matvec(pp.N, pp.Np, t, b, st);
         }
         if (cs == LGP_OK) launch_cg_loop_condition(h, b.state, st);
@@ -681,6 +709,52 @@ lgp_status run_cg(lgp_ctx *ctx, const Prepared &pp, const float *B, int64_t ldb,
     LGP_CUDA(cudaMemcpyAsync(ctx->h_state, b.state, sizeof(CgState), cudaMemcpyDeviceToHost, st));
     *bout = b;
     if (chunks_run) *chunks_run = launched;
+    return LGP_OK;
+}
+
+// The single-column path of lgp_lml_and_grad (LGP_OPT_SINGLE_RHS): each of the t columns of B is
+// solved by its own CG run with the float32 one-column product, as the paper's plain CG loop does
+// (Sec. 5), and the runs are assembled into t-column results (solutions, CG state, Lanczos history) for
+// the same quadrature and adjoint kernels as the batched path.
+lgp_status run_cg_columns(lgp_ctx *ctx, const Prepared &pp, const float *B, int t, const lgp_options *opt,
+                          int hist_len, CgBuffers *bout, int *chunks_run) {
+    NvtxRange nvtx_range("lgp.cg_columns");
+    cudaStream_t st = ctx->work;
+    const int Gt = cg_num_blocks(pp.N, t, ctx->num_sms);
+    lgp_status s;
+    // every t-column buffer exists before the first solve, so nothing moves between the column runs
+    if ((s = ensure(ctx, ctx->cg_partial, (size_t)Gt * 3 * t * sizeof(double))) != LGP_OK ||
+        (s = ensure(ctx, ctx->sr_x, (size_t)pp.Np * t * sizeof(float))) != LGP_OK ||
+        (s = ensure(ctx, ctx->sr_state, sizeof(CgState))) != LGP_OK ||
+        (s = ensure(ctx, ctx->sr_hist, (size_t)2 * std::max(hist_len, 1) * t * sizeof(double))) != LGP_OK)
+        return s;
+    CgState *dst = (CgState *)ctx->sr_state.p;
+    double *dst_alpha = (double *)ctx->sr_hist.p;
+    double *dst_beta = dst_alpha + (size_t)std::max(hist_len, 1) * t;
+    float *xs = (float *)ctx->sr_x.p;
+    LGP_CUDA(cudaMemsetAsync(dst, 0, sizeof(CgState), st));
+    int chunks = 0;
+    for (int c = 0; c < t; ++c) {
+        CgBuffers b1;
+        int ran = 0;
+        if ((s = run_cg(ctx, pp, B + c, t, 1, opt, hist_len, LGP_PREC_FP32, &b1, &ran)) != LGP_OK) return s;
+        launch_copy_cols(b1.x, 1, xs, t, pp.N, 1, c, st);
+        launch_cg_gather_column(b1, hist_len, dst, dst_alpha, dst_beta, t, c, st);
+        LGP_CUDA(cudaGetLastError());
+        chunks += ran;
+    }
+    CgBuffers b;
+    b.x = xs;
+    b.r = b.p = b.Kp = b.z = nullptr;
+    b.partial = (double *)ctx->cg_partial.p;
+    b.G = Gt;
+    b.state = dst;
+    b.hist_alpha = dst_alpha;
+    b.hist_beta = dst_beta;
+    b.pc = Precond();
+    LGP_CUDA(cudaMemcpyAsync(ctx->h_state, dst, sizeof(CgState), cudaMemcpyDeviceToHost, st));
+    *bout = b;
+    if (chunks_run) *chunks_run = chunks;
     return LGP_OK;
 }
 
@@ -787,7 +861,8 @@ void lgp_destroy(lgp_ctx *ctx) {
                       &ctx->batch_part, &ctx->pred_xs,  &ctx->pred_z,    &ctx->pred_q,     &ctx->xs,
                       &ctx->mv_partial, &ctx->cg_vec,   &ctx->cg_partial, &ctx->cg_state,  &ctx->cg_hist,
                       &ctx->scal,       &ctx->rhs,      &ctx->adj_b,     &ctx->adj_partial, &ctx->vsplit,
-                      &ctx->flags,      &ctx->batch_meta};
+                      &ctx->flags,      &ctx->batch_meta, &ctx->sr_x,      &ctx->sr_state,   &ctx->sr_hist,
+                      &ctx->sr_tmp};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (ctx->h_state) cudaFreeHost(ctx->h_state);
@@ -969,7 +1044,10 @@ lgp_status lgp_lml_and_grad(lgp_ctx *ctx, const lgp_hyper *hyp, const float *X, 
     if ((s = check_dev_ptr(ctx, X, "X")) || (s = check_dev_ptr(ctx, y, "y"))) return s;
     const int t = opt->n_probes + 1;
     const int L = opt->lanczos_steps;
-    const int prec = resolve_prec(t, opt->prec);
+    const bool single = (opt->flags & LGP_OPT_SINGLE_RHS) != 0;
+    if (single && opt->precond_rank > 0)
+        return fail(ctx, LGP_ERR_UNSUPPORTED, "the single-column path runs without a preconditioner");
+    const int prec = single ? (int)LGP_PREC_FP32 : resolve_prec(t, opt->prec);
     if (prec < 0) return fail(ctx, (lgp_status)prec, "precision %d unsupported for t=%d", opt->prec, t);
     cudaStream_t user = (cudaStream_t)stream;
     if ((s = enter(ctx, user)) != LGP_OK) return s;
@@ -996,7 +1074,11 @@ lgp_status lgp_lml_and_grad(lgp_ctx *ctx, const lgp_hyper *hyp, const float *X, 
     LGP_CUDA(cudaGetLastError());
     CgBuffers b;
     int chunks = 0;
-    if ((s = run_cg(ctx, pp, rhs, t, t, opt, L, prec, &b, &chunks, k > 0 ? &pc : nullptr)) != LGP_OK) return s;
+    if (single) {
+        if ((s = run_cg_columns(ctx, pp, rhs, t, opt, L, &b, &chunks)) != LGP_OK) return s;
+    } else if ((s = run_cg(ctx, pp, rhs, t, t, opt, L, prec, &b, &chunks, k > 0 ? &pc : nullptr)) != LGP_OK) {
+        return s;
+    }
     // the probe side of the trace terms: P^{-1} z_c (z_c itself without a preconditioner); column 0 stays y
     const float *rhs_t = rhs;
     if (k > 0) {
@@ -1016,7 +1098,7 @@ lgp_status lgp_lml_and_grad(lgp_ctx *ctx, const lgp_hyper *hyp, const float *X, 
     launch_col_dots(b.x, rhs_t, N, t, b.partial, G, dots, st);
     launch_slq_lml(b, t, L, dots, N, slq, st);
     LGP_CUDA(cudaGetLastError());
-    if (grad) {
+    if (grad && !single) {
         if ((s = ensure(ctx, ctx->adj_b, (size_t)pp.Np * t * sizeof(float))) != LGP_OK) return s;
         const int64_t pd = adjoint_partial_doubles(N, t, pp.kp.D, ctx->num_sms);
         if ((s = ensure(ctx, ctx->adj_partial, (size_t)pd * sizeof(double))) != LGP_OK) return s;
@@ -1025,6 +1107,26 @@ lgp_status lgp_lml_and_grad(lgp_ctx *ctx, const lgp_hyper *hyp, const float *X, 
         LGP_CUDA(launch_adjoint_bilinear(pp.kp, pp.xs, N, pp.Np, b.x, (const float *)ctx->adj_b.p, t,
                                          (double *)ctx->adj_partial.p, pd, &nblk, ctx->num_sms, st));
         launch_grad_finalize((const double *)ctx->adj_partial.p, nblk, pp.kp.D, dots, t, pp.kp.noise, gdev, st);
+        LGP_CUDA(cudaGetLastError());
+    } else if (grad) {
+        // single-column path: one adjoint pass per column (its solution against its right-hand side), the
+        // block partials of column c in region c; the finalisation sums all regions
+        if ((s = ensure(ctx, ctx->adj_b, (size_t)pp.Np * t * sizeof(float))) != LGP_OK) return s;
+        const int64_t pd = adjoint_partial_doubles(N, 1, pp.kp.D, ctx->num_sms);
+        if ((s = ensure(ctx, ctx->adj_partial, (size_t)pd * t * sizeof(double))) != LGP_OK) return s;
+        if ((s = ensure(ctx, ctx->sr_tmp, (size_t)2 * pp.Np * sizeof(float))) != LGP_OK) return s;
+        float *adj_b = (float *)ctx->adj_b.p, *ta = (float *)ctx->sr_tmp.p, *tb = ta + pp.Np;
+        launch_adjoint_rhs(b.x, rhs_t, N, t, adj_b, st);
+        int nblk = 0;
+        for (int c = 0; c < t; ++c) {
+            launch_copy_cols(b.x + c, t, ta, 1, N, 1, 0, st);
+            launch_copy_cols(adj_b + c, t, tb, 1, N, 1, 0, st);
+            LGP_CUDA(launch_adjoint_bilinear(pp.kp, pp.xs, N, pp.Np, ta, tb, 1, (double *)ctx->adj_partial.p + c * pd,
+                                             pd, &nblk, ctx->num_sms, st));
+        }
+        if ((int64_t)nblk * (pp.kp.D + 1) != pd)
+            return fail(ctx, LGP_ERR_CUDA, "adjoint partial layout mismatch (%d blocks)", nblk);
+        launch_grad_finalize((const double *)ctx->adj_partial.p, nblk * t, pp.kp.D, dots, t, pp.kp.noise, gdev, st);
         LGP_CUDA(cudaGetLastError());
     }
     LGP_CUDA(cudaMemcpyAsync(ctx->h_scal, dots, (size_t)(2 * kMaxT + 4 + kMaxD + 2) * sizeof(double),
@@ -1055,15 +1157,23 @@ lgp_status lgp_lml_and_grad(lgp_ctx *ctx, const lgp_hyper *hyp, const float *X, 
         info->cg_chunks = ran;
         info->logdet_precond = k > 0 ? pc.logdet : 0.0;
         (void)chunks;
-        // prep_x, y copy, probes, CG init (2), the loop's chunks, column dots (2), SLQ, adjoint (3)
+        // prep_x, y copy, probes, CG init (2), the loop's chunks, column dots (2), SLQ (2), adjoint (3)
         // preconditioned: 3 more launches per iteration and in the CG init; the build (init, 2 per rank step, Gram,
         // float32 copy), the P-distributed probes, and P^{-1} of the probe block with the y copy
         const int pc_iter = k > 0 ? 3 : 0;
         const int pc_once = k > 0 ? (2 * k + 3) + 3 + 1 + 4 : 0;
-        // the symmetric product's dot-form operands, built once before the loop (box, operands)
-        const int dot_once = dot_operands_valid(ctx, pp, t) ? 2 : 0;
-        info->launches = 3 + 2 + ran * (kChunk * (cg_iteration_launches(ctx, pp, t, prec) + pc_iter) + 1) + 2 + 1 +
-                         (grad ? 3 : 0) + pc_once + dot_once;
+        // the products' X-only operands, built once before the loop (transpose; box and operands of the dot form)
+        const int opnd_once = is_tc(prec) && tc_operands_valid(ctx, pp, t, prec) ? (ctx->opnd_dot ? 3 : 1) : 0;
+        if (!single) {
+            info->launches = 3 + 2 +
+                             ran * (kChunk * (cg_iteration_launches(ctx, pp, t, prec, ctx->cg_dist_form) + pc_iter) + 1) +
+                             2 + 2 + (grad ? 3 : 0) + pc_once + opnd_once;
+        } else {
+            // per column: CG init (2), copy and gather (2); the chunks of all columns; per column in the
+            // gradient: two column copies and one adjoint pass
+            info->launches = 3 + 4 * t + ran * (kChunk * (mv_simt_launches(pp.N, pp.Np, 1, ctx->num_sms) + 5) + 1) +
+                             2 + 2 + (grad ? 2 + 3 * t : 0);
+        }
     }
     return cs;
 }

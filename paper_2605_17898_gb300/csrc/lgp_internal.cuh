@@ -206,22 +206,26 @@ int64_t tc_vsplit_bytes(int64_t Np, int t);
 // forced_splits > 0 overrides the column-split count (the autotuner's choice); 0 = wave-efficiency heuristic;
 // kTcSymmetric = the symmetric-tile kernel (mv_tcs.cuh), which adds onto out instead of writing partials.
 constexpr int kTcSymmetric = -1;
-// dot_operands_ready: the symmetric product's dot-form operands of this Xs are already in vsplit
-// (launch_dot_operands, once per prepared X); otherwise the product builds them first.
+// operands_ready: the operands that depend on X alone are already in vsplit (launch_tc_operands, once
+// per prepared X): the transposed X and, where the symmetric product may take the dot form, its
+// distance operands; otherwise the product builds them first.
+// dist_form (symmetric product with the dot form allowed): -1 = not known on the host, so both distance
+// instances launch and the device gate word lets one of them work; 0 / 1 = only the difference / dot
+// instance launches (the caller read the gate word, which must then give the same answer).
 cudaError_t launch_mv_tc(const KernelParams &kp, const float *Xs, int64_t N, int64_t Np, const float *V, int64_t ldv,
                          float *out, int64_t ldo, int t, int fmt, void *vsplit, float *partial, int64_t partial_cap,
                          const int *skip, int *err_flag, long long wait_budget, int num_sms, cudaStream_t st,
-                         int forced_splits = 0, bool dot_operands_ready = false);
-// The dot-form distance data of the symmetric product (box, centred split operands, squared norms,
-// the gate word) for prescaled Xs, into the t-column V-split workspace.
-cudaError_t launch_dot_operands(const KernelParams &kp, const float *Xs, int64_t N, int64_t Np, int t, void *vsplit,
-                                const int *skip, cudaStream_t st);
+                         int forced_splits = 0, bool operands_ready = false, int dist_form = -1);
+// The operands of the tensor-core products that depend on X alone, into the t-column V-split workspace:
+// the transposed prescaled X, and with dot = true the dot-form distance data of the symmetric product
+// (box, centred split operands, squared norms, the gate word).
+cudaError_t launch_tc_operands(const KernelParams &kp, const float *Xs, int64_t N, int64_t Np, int t, void *vsplit,
+                               bool dot, cudaStream_t st);
 int64_t mv_tc_partial_floats(int64_t Np, int t, int num_sms);
 int64_t mv_tc_partial_floats(int64_t Np, int t, int num_sms, int forced_splits);
-// Kernels one split tensor-core product launches (the symmetric product with the dot form runs
-// its operand kernels and both gated instances).
+// Kernels one split tensor-core product launches (arguments as launch_mv_tc).
 int mv_tc_launches(int64_t Np, int t, int num_sms, int fmt, int forced_splits = 0, int kind = -1, int D = 0,
-                   bool dot_operands_ready = false);
+                   bool operands_ready = false, int dist_form = -1);
 // Up to four kernel choices worth timing: kTcSymmetric (when tc_symmetric_ok) and the three most
 // wave-efficient split counts.
 void tc_split_candidates(int64_t Np, int num_sms, int *cand, int *n);
@@ -277,6 +281,10 @@ void launch_cg_init(const float *B, int64_t ldb, int64_t N, int64_t Np, int t, c
                     int max_iter, int hist_len, cudaStream_t st, const float *X0 = nullptr, int64_t ldx0 = 0);
 void launch_cg_after_matvec(int64_t N, int64_t Np, int t, const CgBuffers &b, cudaStream_t st);
 void launch_cg_copy_out(const CgBuffers &b, int64_t N, int t, float *Xsol, int64_t ldx, cudaStream_t st);
+// Column 0 of the single-column run b1 (state, first hist_len Lanczos coefficients) into column c of a
+// t-column state and history; dst->loop_chunks accumulates.
+void launch_cg_gather_column(const CgBuffers &b1, int hist_len, CgState *dst, double *dst_alpha, double *dst_beta,
+                             int t, int c, cudaStream_t st);
 // Body tail of the device-side CG loop: sets the while-node condition to "not done and under the chunk cap".
 void launch_cg_loop_condition(cudaGraphConditionalHandle h, CgState *state, cudaStream_t st);
 // Host-driven loop (LGP_CG_GRAPH=0): counts one chunk in state->loop_chunks.

@@ -376,10 +376,17 @@ void tc_split_candidates(int64_t Np, int num_sms, int *cand, int *n) {
     }
 }
 
-int mv_tc_launches(int64_t Np, int t, int num_sms, int fmt, int forced_splits, int kind, int D, bool dot_operands_ready) {
-    const int dot = forced_splits == kTcSymmetric && dot_form_allowed(kind, D) ? (dot_operands_ready ? 1 : 3) : 0;
-    return (mv_tc_partial_floats(Np, t, num_sms, forced_splits) > 0 ? 4 : 3) + (fmt == kFmtF16 ? 1 : 0) + dot;
+int mv_tc_launches(int64_t Np, int t, int num_sms, int fmt, int forced_splits, int kind, int D, bool operands_ready,
+                   int dist_form) {
+    // split V (+ column maxima for F16), transpose X unless ready, the product, the split reduction
+    int n = 2 + (operands_ready ? 0 : 1) + (mv_tc_partial_floats(Np, t, num_sms, forced_splits) > 0 ? 1 : 0) +
+            (fmt == kFmtF16 ? 1 : 0);
+    if (forced_splits == kTcSymmetric && dot_form_allowed(kind, D))
+        n += (operands_ready ? 0 : 2) + (dist_form < 0 ? 1 : 0);  // operand kernels, the second instance
+    return n;
 }
+
+namespace {
 
 cudaError_t launch_dot_operands(const KernelParams &kp, const float *Xs, int64_t N, int64_t Np, int t, void *vsplit,
                                 const int *skip, cudaStream_t st) {
@@ -399,10 +406,27 @@ cudaError_t launch_dot_operands(const KernelParams &kp, const float *Xs, int64_t
     return cudaGetLastError();
 }
 
+void launch_transpose_x(const KernelParams &kp, const float *Xs, int64_t Np, void *vsplit, int t, const int *skip,
+                        cudaStream_t st) {
+    float *XsT = (float *)((uint8_t *)vsplit + 2 * Np * t * 2 + 2 * 64 * 4);
+    transpose_x_kernel<<<(int)std::min<int64_t>((Np * kp.dpad + 255) / 256, 4096), 256, 0, st>>>(Xs, Np, kp.dpad,
+                                                                                              XsT, skip);
+}
+
+}  // namespace
+
+cudaError_t launch_tc_operands(const KernelParams &kp, const float *Xs, int64_t N, int64_t Np, int t, void *vsplit,
+                               bool dot, cudaStream_t st) {
+    launch_transpose_x(kp, Xs, Np, vsplit, t, nullptr, st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !dot) return e;
+    return launch_dot_operands(kp, Xs, N, Np, t, vsplit, nullptr, st);
+}
+
 cudaError_t launch_mv_tc(const KernelParams &kp, const float *Xs, int64_t N, int64_t Np, const float *V, int64_t ldv,
                          float *out, int64_t ldo, int t, int fmt, void *vsplit, float *partial, int64_t partial_cap,
                          const int *skip, int *err_flag, long long wait_budget, int num_sms, cudaStream_t st,
-                         int forced_splits, bool dot_operands_ready) {
+                         int forced_splits, bool operands_ready, int dist_form) {
     if (!(t == 16 || t == 32) || Np % 256 != 0) return cudaErrorInvalidValue;
     uint16_t *vs = (uint16_t *)vsplit;  // stacked [V_hi; V_lo], 2 * Np * t entries
     unsigned int *vmax = (unsigned int *)(vs + 2 * Np * t);
@@ -431,8 +455,7 @@ cudaError_t launch_mv_tc(const KernelParams &kp, const float *Xs, int64_t N, int
             split_v_kernel<32, kFmtBF16><<<blocks, 256, 0, st>>>(V, ldv, N, Np, vs, vmax, col_scale, kp.s2, out_init,
                                                               ldo, kp.noise, skip);
     }
-    transpose_x_kernel<<<(int)std::min<int64_t>((Np * kp.dpad + 255) / 256, 4096), 256, 0, st>>>(Xs, Np, kp.dpad,
-                                                                                              XsT, skip);
+    if (!operands_ready) launch_transpose_x(kp, Xs, Np, vsplit, t, skip, st);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
 
@@ -476,9 +499,9 @@ cudaError_t launch_mv_tc(const KernelParams &kp, const float *Xs, int64_t N, int
                                   : tcs::dispatch_bf16(kp.kind, kp.D, t, grid, mx, mv, mo, a, st);
         };
         if (!dot_form_allowed(kp.kind, kp.D)) return launch();
-        // dot form: operands (unless the caller built them for this X), then both instances; the gate
-        // word lets exactly one of them work
-        if (!dot_operands_ready && (e = launch_dot_operands(kp, Xs, N, Np, t, vsplit, skip, st)) != cudaSuccess)
+        // dot form: operands (unless the caller built them for this X), then the instance of the known
+        // distance form, or both instances, of which the gate word lets exactly one work
+        if (!operands_ready && (e = launch_dot_operands(kp, Xs, N, Np, t, vsplit, skip, st)) != cudaSuccess)
             return e;
         unsigned int *words = (unsigned int *)(XsT + 8 * Np);
         float *arow = (float *)(words + 32);
@@ -489,8 +512,11 @@ cudaError_t launch_mv_tc(const KernelParams &kp, const float *Xs, int64_t N, int
         a.arow = arow;
         a.ua = ua;
         a.ub = ub;
-        a.dot = 1;
-        if ((e = launch()) != cudaSuccess) return e;
+        if (dist_form != 0) {
+            a.dot = 1;
+            if ((e = launch()) != cudaSuccess) return e;
+        }
+        if (dist_form == 1) return cudaSuccess;
         a.dot = 0;
         return launch();
     }

@@ -2,15 +2,17 @@
 // allocate device memory.
 //
 // Some callers cannot call cudaMalloc:
-//   - code that runs while a CUDA stream is being captured into a graph, where
-//     allocation calls are not permitted;
 //   - programs whose device memory is owned by another allocator (a framework's
-//     caching pool, a fixed arena);
+//     caching pool, a fixed arena sized at start-up), which must not see a library
+//     take memory behind their back;
+//   - services that run under a fixed device-memory budget, where an allocation
+//     that fails in the middle of a request cannot be retried;
 //   - latency-critical loops, where cudaMalloc/cudaFree can synchronise the device.
 // For them this entry point takes no context and allocates nothing. Its scratch
-// (prescaled X, the split copies of V and the split-column partial sums) is one
-// file-scope __device__ array, held by every GPU that loads the library until the
-// process exits.
+// (prescaled X, the split copies of V, the split-column partial sums and two status
+// words) is one file-scope __device__ array, held by every GPU that loads the
+// library until the process exits. lgp_kernel_matvec_noalloc_status reads the
+// status words back.
 //
 // Limits: N <= 8192, t in {16, 32}, D <= 8.
 #include <cuda_runtime.h>
@@ -126,14 +128,28 @@ extern "C" lgp_status lgp_kernel_matvec_noalloc(const lgp_hyper *hyp, const floa
     int *flags = (int *)(base + kOffFlags);
     cudaStream_t st = (cudaStream_t)stream;
 
-    // The array keeps the previous call's contents: the flag words must start at zero
-    // (the product clears its own column maxima; every other region is fully rewritten).
-    if (cudaMemsetAsync(flags, 0, 2 * sizeof(int), st) != cudaSuccess) return LGP_ERR_CUDA;
+    // The array keeps the previous call's contents. Every region the product reads is rewritten
+    // first (the product clears its own column maxima); the two status words (flags[0]: NaN or
+    // Inf in X, flags[1]: a bounded wait ran out) are only ever OR-ed into, so they accumulate
+    // over calls until lgp_kernel_matvec_noalloc_status reads and clears them.
     launch_prep_x(X, N, kp.D, kp.dpad, kp.scale, xs, Np, flags, st);
     if (cudaGetLastError() != cudaSuccess) return LGP_ERR_CUDA;
     const int fmt = prec == LGP_PREC_SPLIT_BF16 ? 0 : 1;
     if (launch_mv_tc(kp, xs, N, Np, V, t, out, t, t, fmt, vsplit, partial, (int64_t)(kPartialBytes / sizeof(float)),
                      nullptr, flags + 1, 4000000000LL, sms, st) != cudaSuccess)
         return LGP_ERR_CUDA;
+    return LGP_OK;
+}
+
+extern "C" lgp_status lgp_kernel_matvec_noalloc_status(lgp_stream stream) {
+    unsigned char *base = nullptr;
+    if (scratch_for_current_device(&base) != cudaSuccess) return LGP_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    int words[2] = {0, 0};
+    if (cudaStreamSynchronize(st) != cudaSuccess) return LGP_ERR_CUDA;
+    if (cudaMemcpy(words, base + kOffFlags, sizeof words, cudaMemcpyDeviceToHost) != cudaSuccess) return LGP_ERR_CUDA;
+    if (cudaMemset(base + kOffFlags, 0, sizeof words) != cudaSuccess) return LGP_ERR_CUDA;
+    if (words[1]) return LGP_ERR_TIMEOUT;
+    if (words[0]) return LGP_ERR_NONFINITE;
     return LGP_OK;
 }

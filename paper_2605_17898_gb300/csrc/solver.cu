@@ -258,6 +258,32 @@ __global__ void cg_loop_condition_kernel(cudaGraphConditionalHandle h, CgState *
 // Host-driven form of the loop tail (no graph): only counts the chunk.
 __global__ void cg_chunk_tally_kernel(CgState *st) { st->loop_chunks += 1; }
 
+// Single-column solves assembled into one t-column result: column 0 of a t = 1 CG run (its state
+// and the first hist_len Lanczos coefficients) becomes column c of dst; chunk counts add up.
+__global__ void cg_gather_column_kernel(const CgState *__restrict__ src, const double *__restrict__ src_alpha,
+                                        const double *__restrict__ src_beta, int hist_len, CgState *dst,
+                                        double *__restrict__ dst_alpha, double *__restrict__ dst_beta, int t, int c) {
+    for (int k = threadIdx.x; k < hist_len; k += blockDim.x) {
+        dst_alpha[(int64_t)k * t + c] = src_alpha[k];
+        dst_beta[(int64_t)k * t + c] = src_beta[k];
+    }
+    if (threadIdx.x == 0) {
+        dst->active[c] = src->active[0];
+        dst->iters[c] = src->iters[0];
+        dst->bnorm2[c] = src->bnorm2[0];
+        dst->rr[c] = src->rr[0];
+        dst->rz[c] = src->rz[0];
+        dst->w0[c] = src->w0[0];
+        dst->alpha[c] = src->alpha[0];
+        dst->beta[c] = src->beta[0];
+        dst->loop_chunks += src->loop_chunks;
+        dst->iter = max(dst->iter, src->iter);
+        if (src->status != 0 && dst->status == 0) dst->status = src->status;
+        dst->t = t;
+        dst->hist_len = hist_len;
+    }
+}
+
 __global__ void copy_out_kernel(const float *__restrict__ x, int64_t N, int t, float *__restrict__ out, int64_t ldo) {
     const int64_t total = N * t;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
@@ -292,107 +318,155 @@ __global__ void col_dots_final_kernel(const double *__restrict__ partial, int G,
     out[c] = s;
 }
 
-// e_1^T log(T) e_1 for the symmetric tridiagonal T (diagonal a[0..m), off-diagonal b[0..m-1)),
-// by implicit symmetric QR steps with a Wilkinson shift (Golub & Van Loan, Sec. 8.3),
-// carrying u = W e_1 where W is the product of all Givens rotations (so that
-// e_1^T f(T) e_1 = sum_j u_j^2 f(lambda_j)). Arrays are overwritten.
-__device__ double tridiag_e1_log_e1(double *a, double *b, double *u, int m, int *nonpos) {
-    for (int k = 0; k < m; ++k) u[k] = (k == 0) ? 1.0 : 0.0;
-    int hi = m - 1;
-    int steps = 0;
-    const int max_steps = 60 * m + 60;
-    while (hi > 0 && steps < max_steps) {
-        for (int k = 0; k < hi; ++k)
-            if (fabs(b[k]) <= 2.220446049250313e-16 * (fabs(a[k]) + fabs(a[k + 1]))) b[k] = 0.0;
-        if (b[hi - 1] == 0.0) {
-            --hi;
-            continue;
-        }
-        int lo = hi - 1;
-        while (lo > 0 && b[lo - 1] != 0.0) --lo;
-        ++steps;
-        const double dlt = 0.5 * (a[hi - 1] - a[hi]);
-        const double bb = b[hi - 1];
-        const double den = dlt + copysign(hypot(dlt, bb), dlt);
-        const double mu = a[hi] - bb * bb / den;
-        double x = a[lo] - mu;
-        double z = b[lo];
-        for (int k = lo; k < hi; ++k) {
-            const double rr = hypot(x, z);
-            double c = 1.0, s = 0.0;
-            if (rr > 0.0) {
-                c = x / rr;
-                s = z / rr;
-            }
-            if (k > lo) b[k - 1] = rr;
-            const double p = a[k], q = b[k], w = a[k + 1];
-            a[k] = c * c * p + 2.0 * c * s * q + s * s * w;
-            a[k + 1] = s * s * p - 2.0 * c * s * q + c * c * w;
-            b[k] = c * s * (w - p) + (c * c - s * s) * q;
-            if (k + 1 < hi) {
-                z = s * b[k + 1];
-                b[k + 1] = c * b[k + 1];
-                x = b[k];
-            }
-            const double uk = u[k], uk1 = u[k + 1];
-            u[k] = c * uk + s * uk1;
-            u[k + 1] = -s * uk + c * uk1;
-        }
-    }
-    double sum = 0.0;
-    for (int k = 0; k < m; ++k) {
-        if (!(a[k] > 0.0)) {
-            *nonpos = 1;
-            continue;
-        }
-        sum += u[k] * u[k] * log(a[k]);
-    }
-    if (hi > 0) *nonpos = 1;
-    return sum;
+// e_1^T log(T) e_1 of each probe's Lanczos tridiagonal, the Gauss quadrature of the stochastic
+// log-determinant (Sec. 3 "Inference"), without an eigendecomposition of T. For lambda > 0,
+//   log lambda = int_R [s(v) - s(v - log lambda)] dv,   s(v) = 1 / (1 + e^-v),
+// so with x = e^v and g(x) = e_1^T (T + x I)^{-1} e_1 = sum_j u_1j^2 / (lambda_j + x),
+//   e_1^T log(T) e_1 = int_R [x / (1 + x) - x g(x)] dv.
+// The integrand is a sum of differences of logistic functions: analytic in the strip |Im v| < pi
+// and decaying like e^-|v| outside [log lambda_min, log lambda_max], so the trapezoidal rule with
+// step h on [log lambda_lo - 36, log lambda_hi + 36] has discretisation error ~exp(-2 pi^2 / h)
+// (8e-18 at h = 0.5) and truncation error ~e^-36 (Trefethen & Weideman, "The exponentially
+// convergent trapezoidal rule", SIAM Review 2014). Bounds: lambda_max <= the Gershgorin bound of T;
+// lambda_min >= 1 / tr(T^-1), where T = L D L^T with D = diag(1/alpha_k) and unit lower bidiagonal L
+// of subdiagonal sqrt(beta_k) (the CG-Lanczos factorisation), which gives
+// tr(T^-1) = sum_i alpha_i s_i, s_0 = 1, s_i = 1 + beta_{i-1} s_{i-1}.
+// At each node g(x) = P_2 / P_1 with the trailing minors P_k = det((T + x I)[k:m, k:m]) from the
+// division-free recurrence P_k = (a_k + x) P_{k+1} - b_k^2 P_{k+2}, rescaled by powers of two, and
+//   x / (1 + x) - x P_2 / P_1 = x ((a_1 - 1) P_2 - b_1^2 P_3) / ((1 + x) P_1)
+// (P_1 expanded along its first row), which has no cancellation between the two terms. All of it is
+// float64: every thread of the block evaluates its own nodes, so each float64 instruction does the
+// work of all its lanes on a part whose float64 rate is low.
+constexpr int kSlqThreads = 256;
+constexpr double kSlqStep = 0.5;   // h
+constexpr double kSlqTail = 36.0;  // trapezoidal range beyond the spectrum bounds, in log units
+
+// (p0, p1, p2) scaled by the power of two that brings max(|p0|, |p1|) into [1, 2): exact.
+__device__ __forceinline__ void rescale_pow2(double &p0, double &p1, double &p2) {
+    const double mx = fmax(fabs(p0), fabs(p1));
+    if (!(mx > 0.0) || !isfinite(mx)) return;
+    const int e = ((__double2hiint(mx) >> 20) & 0x7ff) - 1023;
+    if (e <= -1022 || e >= 1023) return;
+    const double sc = __hiloint2double((1023 - e) << 20, 0);
+    p0 *= sc;
+    p1 *= sc;
+    p2 *= sc;
 }
 
-// One thread per probe column c = 1..t-1: T_c from the CG coefficients
-// (T[k,k] = 1/alpha_k + beta_{k-1}/alpha_{k-1}, T[k,k+1] = sqrt(beta_k)/alpha_k),
-// gamma_c = w_c e_1^T log(T_c) e_1 with w_c = z_c^T P^{-1} z_c (||z_c||^2 without a preconditioner);
-// logdet = logdet_P + mean_c gamma_c (Sec. 3 "Inference"; logdet_P = log|P|, 0 without one).
-__global__ void slq_lml_kernel(const CgState *st, const double *__restrict__ hist_alpha,
-                               const double *__restrict__ hist_beta, int t, int hist_len,
-                               const double *__restrict__ dots, int64_t N, double logdet_p, double *out) {
-    __shared__ double gam[kMaxT];
-    __shared__ int flag[kMaxT];
-    const int c = threadIdx.x;
-    if (c >= 1 && c < t) {
-        double a[kMaxLanczos], b[kMaxLanczos], u[kMaxLanczos];
-        const int m = min(hist_len, st->iters[c]);
-        int nonpos = 0;
-        double g = 0.0;
-        if (m > 0) {
-            for (int k = 0; k < m; ++k) {
-                const double al = hist_alpha[(int64_t)k * t + c];
-                a[k] = 1.0 / al;
-                if (k > 0) a[k] += hist_beta[(int64_t)(k - 1) * t + c] / hist_alpha[(int64_t)(k - 1) * t + c];
-                if (k + 1 < m) b[k] = sqrt(hist_beta[(int64_t)k * t + c]) / al;
-            }
-            g = st->w0[c] * tridiag_e1_log_e1(a, b, u, m, &nonpos);
+// One block per probe column c = blockIdx.x + 1: gamma_c = w_c e_1^T log(T_c) e_1 with
+// w_c = z_c^T P^{-1} z_c (||z_c||^2 without a preconditioner), T_c from the first
+// m = min(L, iterations of c) CG coefficients: T[k,k] = 1/alpha_k + beta_{k-1}/alpha_{k-1},
+// T[k,k+1] = sqrt(beta_k)/alpha_k. Writes gamma[c] and bad[c] (1 if T_c is not positive definite
+// or a value is not finite). Summation order is fixed.
+__global__ void __launch_bounds__(kSlqThreads) slq_quad_kernel(const CgState *st, const double *__restrict__ hist_alpha,
+                                                               const double *__restrict__ hist_beta, int t,
+                                                               int hist_len, double *__restrict__ gamma,
+                                                               double *__restrict__ bad) {
+    __shared__ double sa[kMaxLanczos], sbb[kMaxLanczos], sal[kMaxLanczos], sbe[kMaxLanczos];
+    __shared__ double red[kSlqThreads];
+    __shared__ double s_vlo;
+    __shared__ int s_nodes, s_bad;
+    const int c = blockIdx.x + 1;
+    const int tid = threadIdx.x;
+    const int m = min(hist_len, st->iters[c]);
+    if (m <= 0) {
+        if (tid == 0) {
+            gamma[c] = 0.0;
+            bad[c] = 0.0;
         }
-        gam[c] = g;
-        flag[c] = nonpos;
+        return;
+    }
+    if (tid == 0) s_bad = 0;
+    __syncthreads();
+    if (tid < m) {
+        const double al = hist_alpha[(int64_t)tid * t + c];
+        const double be = hist_beta[(int64_t)tid * t + c];
+        sal[tid] = al;
+        sbe[tid] = be;
+        if (!(al > 0.0) || !isfinite(al) || (tid + 1 < m && (!(be >= 0.0) || !isfinite(be)))) atomicOr(&s_bad, 1);
     }
     __syncthreads();
-    if (c == 0) {
-        double s = 0.0;
-        int bad = 0;
-        for (int k = 1; k < t; ++k) {
-            s += gam[k];
-            bad |= flag[k];
-        }
-        const double logdet = logdet_p + (t > 1 ? s / (t - 1) : 0.0);
-        const double quad = dots[0];
-        out[0] = -0.5 * (quad + logdet + (double)N * 1.8378770664093453);  // log(2 pi)
-        out[1] = quad;
-        out[2] = logdet;
-        out[3] = bad ? 1.0 : 0.0;
+    if (tid < m) {
+        double a = 1.0 / sal[tid];
+        if (tid > 0) a += sbe[tid - 1] / sal[tid - 1];
+        sa[tid] = a;
+        sbb[tid] = tid + 1 < m ? sbe[tid] / (sal[tid] * sal[tid]) : 0.0;  // b_k^2
     }
+    __syncthreads();
+    // Gershgorin upper bound of the spectrum (max reduction over the rows)
+    double g = 0.0;
+    if (tid < m) {
+        g = sa[tid];
+        if (tid > 0) g += sqrt(sbb[tid - 1]);
+        if (tid + 1 < m) g += sqrt(sbb[tid]);
+    }
+    red[tid] = g;
+    __syncthreads();
+    for (int s = kSlqThreads / 2; s > 0; s >>= 1) {
+        if (tid < s) red[tid] = fmax(red[tid], red[tid + s]);
+        __syncthreads();
+    }
+    if (tid == 0) {
+        const double lam_hi = red[0];
+        double sk = 1.0, tr = sal[0];
+        for (int i = 1; i < m; ++i) {
+            sk = fma(sbe[i - 1], sk, 1.0);
+            tr = fma(sal[i], sk, tr);
+        }
+        const double lam_lo = 1.0 / tr;
+        if (!(lam_hi > 0.0) || !isfinite(lam_hi) || !(lam_lo > 0.0) || !isfinite(tr)) s_bad = 1;
+        const double vlo = log(lam_lo) - kSlqTail;
+        const double vhi = log(lam_hi) + kSlqTail;
+        s_vlo = vlo;
+        s_nodes = s_bad ? 0 : (int)ceil((vhi - vlo) / kSlqStep) + 1;
+    }
+    __syncthreads();
+    const int nodes = s_nodes;
+    const double a1m1 = sa[0] - 1.0, b1sq = sbb[0];
+    double acc = 0.0;
+    int nonpos = 0;
+    for (int n = tid; n < nodes; n += kSlqThreads) {
+        const double x = exp(s_vlo + n * kSlqStep);
+        double p0 = sa[m - 1] + x, p1 = 1.0, p2 = 0.0;  // (P_k, P_{k+1}, P_{k+2}) at k = m
+        for (int k = m - 2, q = 0; k >= 0; --k, ++q) {
+            p2 = p1;
+            p1 = p0;
+            p0 = fma(sa[k] + x, p1, -sbb[k] * p2);
+            if ((q & 3) == 3) rescale_pow2(p0, p1, p2);
+        }
+        if (!(p0 > 0.0)) nonpos = 1;  // T + x I positive definite: every trailing minor is positive
+        acc += x * fma(a1m1, p1, -b1sq * p2) / ((1.0 + x) * p0);
+    }
+    if (nonpos) atomicOr(&s_bad, 1);
+    red[tid] = acc;
+    __syncthreads();
+    for (int s = kSlqThreads / 2; s > 0; s >>= 1) {
+        if (tid < s) red[tid] += red[tid + s];
+        __syncthreads();
+    }
+    if (tid == 0) {
+        const double v = st->w0[c] * kSlqStep * red[0];
+        gamma[c] = v;
+        bad[c] = (s_bad || !isfinite(v)) ? 1.0 : 0.0;
+    }
+}
+
+// logdet = logdet_P + mean_c gamma_c (logdet_P = log|P|, 0 without a preconditioner);
+// LML = -1/2 (y^T K_y^{-1} y + logdet + N log 2 pi). Sums in column order.
+__global__ void slq_lml_finish_kernel(const double *__restrict__ gamma, const double *__restrict__ bad, int t,
+                                      const double *__restrict__ dots, int64_t N, double logdet_p, double *out) {
+    double s = 0.0;
+    int any_bad = 0;
+    for (int k = 1; k < t; ++k) {
+        s += gamma[k];
+        any_bad |= bad[k] != 0.0;
+    }
+    const double logdet = logdet_p + (t > 1 ? s / (t - 1) : 0.0);
+    const double quad = dots[0];
+    out[0] = -0.5 * (quad + logdet + (double)N * 1.8378770664093453);  // log(2 pi)
+    out[1] = quad;
+    out[2] = logdet;
+    out[3] = any_bad ? 1.0 : 0.0;
 }
 
 __global__ void adjoint_rhs_kernel(const float *__restrict__ A, const float *__restrict__ RHS, int64_t N, int t,
@@ -479,6 +553,12 @@ void launch_cg_loop_condition(cudaGraphConditionalHandle h, CgState *state, cuda
 
 void launch_cg_chunk_tally(CgState *state, cudaStream_t st) { cg_chunk_tally_kernel<<<1, 1, 0, st>>>(state); }
 
+void launch_cg_gather_column(const CgBuffers &b1, int hist_len, CgState *dst, double *dst_alpha, double *dst_beta,
+                             int t, int c, cudaStream_t st) {
+    cg_gather_column_kernel<<<1, 64, 0, st>>>(b1.state, b1.hist_alpha, b1.hist_beta, hist_len, dst, dst_alpha,
+                                              dst_beta, t, c);
+}
+
 void launch_cg_copy_out(const CgBuffers &b, int64_t N, int t, float *Xsol, int64_t ldx, cudaStream_t st) {
     copy_out_kernel<<<grid_for(N * t), 256, 0, st>>>(b.x, N, t, Xsol, ldx);
 }
@@ -491,8 +571,13 @@ void launch_col_dots(const float *A, const float *B, int64_t N, int t, double *p
 
 void launch_slq_lml(const CgBuffers &b, int t, int hist_len, const double *dots, int64_t N, double *out,
                     cudaStream_t st) {
-    slq_lml_kernel<<<1, kMaxT, 0, st>>>(b.state, b.hist_alpha, b.hist_beta, t, hist_len, dots, N,
-                                        b.pc.k > 0 ? b.pc.logdet : 0.0, out);
+    // per-column gamma and bad flags in the CG partial-sum buffer (3 G t >= 2 t doubles, free after
+    // the column dots have been reduced)
+    double *gamma = b.partial;
+    double *bad = b.partial + t;
+    if (t > 1)
+        slq_quad_kernel<<<t - 1, kSlqThreads, 0, st>>>(b.state, b.hist_alpha, b.hist_beta, t, hist_len, gamma, bad);
+    slq_lml_finish_kernel<<<1, 1, 0, st>>>(gamma, bad, t, dots, N, b.pc.k > 0 ? b.pc.logdet : 0.0, out);
 }
 
 void launch_adjoint_rhs(const float *A, const float *RHS, int64_t N, int t, float *Bp, cudaStream_t st) {

@@ -130,6 +130,60 @@ def test_lml_and_grad_against_oracle(lgp, case):
     assert _grad_err(grad, est["grad"]).max() <= 1e-3
 
 
+@pytest.mark.parametrize("n,L", [(24, 64), (40, 64), (200, 3)])
+def test_slq_quadrature_against_probe_targets(lgp, n, L):
+    """The log-determinant quadrature, pinned tighter than the LML gate.
+
+    With CG run until its Krylov space holds every probe (N <= L), Gauss quadrature on the Lanczos
+    tridiagonal is exact: mean_i ||z_i||^2 e_1^T log(T_i) e_1 = mean_i z_i^T log(K_y) z_i, the oracle's
+    probe-conditioned log-determinant (eigh of K_y), up to float32 CG rounding. With L = 3 steps on a
+    larger problem the quadrature is the FP64 estimator's own truncated one, compared at its gate."""
+    p = wl.random_problem(n, 2, wl.RBF, seed=21 + n, log_noise=math.log(0.1))
+    hyp = go.hyper_of(p)
+    m, seed = 7, 5
+    lml, _, info = lgp.lgp_lml_and_grad(_dev(p.X), _dev(p.y), p, n_probes=m, lanczos_steps=L, seed=seed,
+                                        tol=1e-7, max_iter=400, want_grad=False)
+    if n <= L:
+        tg = go.probe_conditioned_targets(p.X, p.y, hyp, go.rademacher(seed, n, m))
+        assert info["logdet"] == pytest.approx(tg["logdet"], rel=1e-5, abs=1e-5)
+    else:
+        est = go.estimator_fp64(p.X, p.y, hyp, n_probes=m, lanczos_steps=L, seed=seed, tol=1e-7, max_iter=400)
+        assert info["logdet"] == pytest.approx(est["logdet"], rel=1e-4)
+
+
+def test_single_column_path_and_batched_path_meet_the_same_gate(lgp):
+    """Equal accuracy of the two paths the bench compares, on the mBCG workload's distribution at N=3000:
+    the batched split-F16 mBCG step and the plain FP32 single-column step (every column its own CG run
+    with the one-column product, one adjoint pass per column) use the same probes, tolerance and Lanczos
+    length, and each meets the 1e-3 LML and gradient gates against the FP64 estimator and the
+    probe-conditioned targets."""
+    p, m = wl.cfg3(N=3000, t=32), 31
+    hyp = go.hyper_of(p)
+    L, seed, tol = 50, 77, 1e-6
+    est = go.estimator_fp64(p.X, p.y, hyp, n_probes=m, lanczos_steps=L, seed=seed, tol=tol, max_iter=3000)
+    tg = go.probe_conditioned_targets(p.X, p.y, hyp, est["Z"])
+    X, y = _dev(p.X), _dev(p.y)
+    for single in (False, True):
+        lml, grad, info = lgp.lgp_lml_and_grad(X, y, p, n_probes=m, lanczos_steps=L, seed=seed, tol=tol,
+                                               max_iter=3000, single_rhs=single)
+        label = "single-column FP32" if single else "batched"
+        print(f"{label}: lml {lml:.6f} (fp64 estimator {est['lml']:.6f}), iterations "
+              f"{info['iters_min']}..{info['iters_max']}, launches {info['launches']}")
+        assert info["prec_used"] == (lgp.LGP_PREC_FP32 if single else lgp.LGP_PREC_SPLIT_F16)
+        assert info["t"] == m + 1
+        assert lml == pytest.approx(est["lml"], rel=1e-3)
+        assert info["quad"] == pytest.approx(tg["quad"], rel=1e-4)
+        assert _grad_err(grad, est["grad"]).max() <= 1e-3
+        assert _grad_err(grad, tg["grad"]).max() <= 1e-3
+
+
+def test_single_column_path_rejects_a_preconditioner(lgp):
+    p = wl.cfg3(N=500, t=8)
+    with pytest.raises(lgp.LGPError) as e:
+        lgp.lgp_lml_and_grad(_dev(p.X), _dev(p.y), p, n_probes=7, single_rhs=True, precond_rank=4)
+    assert e.value.status == lgp.LGP_ERR_UNSUPPORTED
+
+
 def test_lml_gradient_matches_finite_differences_of_exact_lml(lgp):
     """cfg4-shaped check: the analytic gradient estimate against central FD (h=1e-3) of the exact LML.
 

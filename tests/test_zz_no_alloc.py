@@ -1,15 +1,18 @@
-"""The allocation-free product against the allocating one (collected last on purpose).
+"""The allocation-free product against the allocating one and the FP64 oracle (collected last on
+purpose, so that a failure here leaves every other test already run).
 
-lgp_kernel_matvec_noalloc serves callers that cannot allocate device memory (code
-under stream capture, programs with their own allocator, latency-critical loops):
-it uses a fixed scratch array inside the library instead of a context workspace.
-Two calls in a row, with different shapes, must each match lgp_kernel_matvec
-within the product tolerance, and a repeated call must not change the device's
-free memory.
+lgp_kernel_matvec_noalloc serves callers that cannot allocate device memory: programs whose
+device memory belongs to another allocator, services under a fixed memory budget, and
+latency-critical loops where cudaMalloc/cudaFree could synchronise the device. It uses a fixed
+scratch array inside the library instead of a context workspace. Two calls in a row, with
+different shapes, must each match lgp_kernel_matvec and the FP64 oracle within the product
+tolerance, the status words must read back clean, and a repeated call must not change the
+device's free memory.
 """
 import numpy as np
 import pytest
 
+from oracle import gp_oracle as go
 import workloads as wl
 
 pytestmark = pytest.mark.gpu
@@ -18,26 +21,29 @@ TOL = 1e-5
 
 
 def _colerr(a, b):
-    a = a.double()
-    b = b.double()
-    import torch
-    return (torch.linalg.norm(a - b, dim=0) / torch.linalg.norm(b, dim=0)).max().item()
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return (np.linalg.norm(a - b, axis=0) / np.linalg.norm(b, axis=0)).max()
 
 
-def test_noalloc_matches_allocating_entry_on_two_calls(lgp):
+def test_noalloc_matches_allocating_entry_and_oracle_on_two_calls(lgp):
     import torch
     cases = [(wl.random_problem(8000, 5, wl.MATERN52, seed=101), 32),
              (wl.random_problem(3001, 2, wl.RBF, seed=102), 16)]
     for p, t in cases:
+        Vh = wl.rhs_block(p.N, t, seed=t)
         X = torch.as_tensor(p.X, device="cuda")
-        V = torch.as_tensor(wl.rhs_block(p.N, t, seed=t), device="cuda")
+        V = torch.as_tensor(Vh, device="cuda")
         out = torch.full((p.N, t), float("nan"), device="cuda")
         s = lgp.lgp_kernel_matvec_noalloc(X, p, V, out)
         assert s == lgp.LGP_OK
+        assert lgp.lgp_kernel_matvec_noalloc_status() == lgp.LGP_OK
         ref = lgp.lgp_kernel_matvec(X, p, V, prec=lgp.LGP_PREC_SPLIT_F16)
         torch.cuda.synchronize()
-        assert torch.isfinite(out).all()
-        assert _colerr(out, ref) <= TOL
+        got = out.cpu().numpy()
+        assert np.isfinite(got).all()
+        assert _colerr(got, ref.cpu().numpy()) <= TOL
+        assert _colerr(got, go.matvec(p.X, Vh, go.hyper_of(p))) <= TOL
 
 
 def test_noalloc_repeated_call_allocates_nothing(lgp):
@@ -51,6 +57,7 @@ def test_noalloc_repeated_call_allocates_nothing(lgp):
     free0, _ = torch.cuda.mem_get_info()
     for _ in range(3):
         assert lgp.lgp_kernel_matvec_noalloc(X, p, V, out) == lgp.LGP_OK
+    assert lgp.lgp_kernel_matvec_noalloc_status() == lgp.LGP_OK
     torch.cuda.synchronize()
     free1, _ = torch.cuda.mem_get_info()
     assert free1 == free0
