@@ -598,9 +598,25 @@ def _bench_batch_set(lgp, ctx, args, dev, label, probs):
         else:
             res[name]["iters_max"] = max(out)
     pairs = sum(float(q.N) ** 2 for q in probs)
+    _, it_b, _, _ = batched()
+    # useful work of the batched call: each problem's products (one per iteration of its slowest column,
+    # plus the initial one) over the call's time; and the FP32-pipe operations the same products cost on
+    # the float32 route (2D + kernel value + t per entry), against the FP32 peak, as the persistent
+    # product's pipe fraction (tensor-route problems counted at that float32 cost, so an upper bound)
+    kval = {wl.RBF: 0, wl.MATERN52: 3, wl.MATERN12: 1, wl.MATERN32: 2}
+    it_g = [int(it_b[g].max()) + 1 for g in range(len(probs))]
+    pr = sum(i * float(q.N) ** 2 * 8 for i, q in zip(it_g, probs)) / (res["batched"]["ms"] / 1e3)
+    ops = sum(i * float(q.N) ** 2 * (2 * q.D + kval[q.kind] + 8) for i, q in zip(it_g, probs))
+    n_sm = torch.cuda.get_device_properties(dev.index or 0).multi_processor_count
+    fp32_peak = n_sm * FP32_LANES_PER_SM * MAX_SM_MHZ_NOMINAL * 1e6
+    routes = [ctx.batch_route_choice(q.N, q.D, q.kind, 8) for q in probs]
     return {"mode": "batch", "workload": label, "n_gp": len(probs), "t": 8, "pairs_per_product": pairs,
             "N_min": min(q.N for q in probs), "N_max": max(q.N for q in probs), **res,
-            "speedup": res["one_call_per_gp"]["ms"] / res["batched"]["ms"]}
+            "speedup": res["one_call_per_gp"]["ms"] / res["batched"]["ms"],
+            "batched_pair_rhs_per_s": pr,
+            "batched_fp32_equiv_frac": ops / (res["batched"]["ms"] / 1e3) / fp32_peak,
+            "tensor_route_problems": sum(1 for r in routes if r == lgp.LGP_BATCH_TENSOR),
+            "tensor_route_N": sorted(q.N for q, r in zip(probs, routes) if r == lgp.LGP_BATCH_TENSOR)}
 
 
 def bench_predict(lgp, ctx, p, args, dev, prec, rank):

@@ -300,15 +300,30 @@ lgp_status lgp_rademacher_probes(lgp_ctx *ctx, uint64_t seed, int64_t N, int32_t
 /*
  * Many independent GP solves of uneven size in one call: for g < n_gp,
  * Xsol[g] = K_y(g)^{-1} B[g] with K_y(g) from hyp[g] and X[g] ([N[g], hyp[g].D]),
- * B[g] and Xsol[g] device [N[g], t]. All problems advance together: each CG
- * iteration is one product launch over a work list of (problem, row tile)
- * items and one launch per vector update, captured once in a CUDA graph and
- * replayed. iters (HOST [n_gp * t], may be NULL) and rel_resid (HOST
- * [n_gp * t], may be NULL) are per problem and column. Synchronises `stream`.
+ * B[g] and Xsol[g] device [N[g], t], 1 <= t <= 16. Each problem takes one of two routes,
+ * chosen per shape (padded N, D, kind, t) by timing both products once on the caller's
+ * own data (the Sec. 5 gap: no batched solves):
+ *   - the persistent batch: all such problems advance together, each CG iteration one
+ *     float32 product launch over a work list of (problem, row block, column range)
+ *     items plus one launch per vector update, the loop one CUDA graph with a
+ *     device-side while node;
+ *   - the tensor-core route (problems of at least 2048 rows whose split-F16 product with
+ *     the columns zero-padded to 16 measures at least 10% faster): its own CG solve with
+ *     that product, as lgp_cg_solve with prec = LGP_PREC_SPLIT_F16.
+ * opt->prec = LGP_PREC_FP32 keeps every problem in the persistent batch; LGP_AUTOTUNE=0
+ * too. iters (HOST [n_gp * t], may be NULL) and rel_resid (HOST [n_gp * t], may be NULL)
+ * are per problem and column. Synchronises `stream`.
  */
 lgp_status lgp_batch_cg_solve(lgp_ctx *ctx, int32_t n_gp, const lgp_hyper *hyp, const float *const *X,
                               const float *const *B, float *const *Xsol, const int64_t *N, int32_t t,
                               const lgp_options *opt, int32_t *iters, double *rel_resid, lgp_stream stream);
+
+/* Which route lgp_batch_cg_solve chose for problems of N rows, dimension D, kernel `kind`
+ * and t columns (diagnostic; no counterpart in the paper): LGP_BATCH_UNTUNED before the
+ * first batched solve with that shape, LGP_BATCH_PERSISTENT or LGP_BATCH_TENSOR; a
+ * negative lgp_status for invalid arguments. */
+enum { LGP_BATCH_UNTUNED = 0, LGP_BATCH_PERSISTENT = 1, LGP_BATCH_TENSOR = 2 };
+int32_t lgp_batch_route_choice(const lgp_ctx *ctx, int64_t N, int32_t D, int32_t kind, int32_t t);
 
 /*
  * Measurement support (no counterpart in the paper): throughput of one GPU pipe on the

@@ -46,6 +46,9 @@ LGP_TC_SYMMETRIC = 2
 LGP_DIST_NONE = -1
 LGP_DIST_DIFF = 0
 LGP_DIST_DOT = 1
+LGP_BATCH_UNTUNED = 0
+LGP_BATCH_PERSISTENT = 1
+LGP_BATCH_TENSOR = 2
 
 EXPORTED = [
     "lgp_version", "lgp_status_string", "lgp_create", "lgp_destroy", "lgp_last_error_message",
@@ -53,7 +56,7 @@ EXPORTED = [
     "lgp_kernel_matvec", "lgp_kernel_matvec_grad", "lgp_cg_solve", "lgp_lml_and_grad",
     "lgp_rademacher_probes", "lgp_batch_cg_solve", "lgp_kernel_matvec_noalloc",
     "lgp_measure_pipe_peak", "lgp_tc_kernel_choice", "lgp_predict", "lgp_tc_distance_form",
-    "lgp_kernel_matvec_noalloc_status",
+    "lgp_kernel_matvec_noalloc_status", "lgp_batch_route_choice",
 ]
 
 
@@ -127,6 +130,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "lgp_kernel_matvec_noalloc": (c.c_int32, [c.POINTER(lgp_hyper), vp, vp, vp, c.c_int64, c.c_int32, c.c_int32,
                                                   vp]),
         "lgp_kernel_matvec_noalloc_status": (c.c_int32, [vp]),
+        "lgp_batch_route_choice": (c.c_int32, [vp, c.c_int64, c.c_int32, c.c_int32, c.c_int32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -221,6 +225,10 @@ class Context:
     def tc_kernel_choice(self, N: int, D: int, kind: int, t: int, prec: int = LGP_PREC_AUTO) -> int:
         """LGP_TC_UNTUNED / LGP_TC_ROW / LGP_TC_SYMMETRIC for that product shape (or a negative status)."""
         return int(self.lib.lgp_tc_kernel_choice(self.h, int(N), int(D), int(kind), int(t), int(prec)))
+
+    def batch_route_choice(self, N: int, D: int, kind: int, t: int) -> int:
+        """LGP_BATCH_UNTUNED / LGP_BATCH_PERSISTENT / LGP_BATCH_TENSOR for that batched-problem shape."""
+        return int(self.lib.lgp_batch_route_choice(self.h, int(N), int(D), int(kind), int(t)))
 
     def tc_distance_form(self, stream=None) -> tuple[int, float]:
         """(LGP_DIST_NONE / LGP_DIST_DIFF / LGP_DIST_DOT, max |u|^2 or -1) of the last symmetric product."""

@@ -57,6 +57,9 @@ struct lgp_ctx {
     std::vector<unsigned char> cg_key;
     // autotuned column-split counts of the tensor-core product, keyed by (Np, t, fmt, D, kind)
     std::map<std::vector<int64_t>, int> tc_splits;
+    // route of a batched problem shape, keyed by (Np, D, kind, t): 0 = the persistent batch launch,
+    // 1 = its own solve with the tensor-core product (timed once per shape, batch_route)
+    std::map<std::vector<int64_t>, int> batch_routes;
     // the last symmetric-tile product: its kind, padded rows and columns (for the distance-form query)
     int sym_kind = -1, sym_D = 0, sym_t = 0;
     int64_t sym_Np = 0;
@@ -69,6 +72,7 @@ struct lgp_ctx {
     void *opnd_buf = nullptr;
     size_t opnd_buf_bytes = 0;  // with opnd_buf: the workspace allocation the operands were written to
     int cg_dist_form = -1;      // distance form baked into the last CG graph (-1: both instances launch)
+    int last_batch_tc = 0;      // problems of the last batched solve that took the tensor-core route
 };
 
 namespace {
@@ -793,6 +797,118 @@ lgp_status cg_status_of(lgp_ctx *ctx, const CgState &h, int t, int *iters, doubl
     return LGP_OK;
 }
 
+// Smallest problem the batched solver times for the tensor-core route (smaller ones stay in the batch).
+constexpr int64_t kBatchTcMinN = 2048;
+
+// Route of one problem of a batched solve with t <= 16 columns: time, on the caller's own X and
+// right-hand sides, one float32 product with t columns (the arithmetic of the persistent batch launch)
+// against one split-F16 tensor-core product with the columns zero-padded to 16 (the kernel that
+// autotune_tc picks for that shape), and keep the faster (the tensor-core one only if at least 10%
+// faster, since it carries the padding and per-problem launches). Cached per shape in the context and,
+// with LGP_AUTOTUNE_CACHE, in the same file as the product choices (key suffix |route).
+lgp_status batch_route(lgp_ctx *ctx, const lgp_hyper *h, const float *X, int64_t N, const float *B, int t,
+                       int *route) {
+    NvtxRange nvtx_range("lgp.batch_route");
+    const std::vector<int64_t> key = {pad_rows(N), (int64_t)h->D, (int64_t)h->kind, (int64_t)t};
+    auto it = ctx->batch_routes.find(key);
+    if (it != ctx->batch_routes.end()) {
+        *route = it->second;
+        return LGP_OK;
+    }
+    *route = 0;
+    const char *env = std::getenv("LGP_AUTOTUNE");
+    if (N < kBatchTcMinN || t > 16 || !tc_supported(16) || (env && env[0] == '0')) {
+        ctx->batch_routes[key] = 0;
+        return LGP_OK;
+    }
+    const char *cache_path = std::getenv("LGP_AUTOTUNE_CACHE");
+    const std::string cache_key = cache_path ? tune_cache_key(ctx, key) + "|route" : std::string();
+    int cached = 0;
+    if (cache_path && tune_cache_lookup(cache_path, cache_key, &cached) && (cached == 0 || cached == 1)) {
+        ctx->batch_routes[key] = cached;
+        *route = cached;
+        return LGP_OK;
+    }
+    cudaStream_t st = ctx->work;
+    Prepared pp;
+    lgp_status s;
+    if ((s = prepare_x(ctx, h, X, N, st, &pp)) != LGP_OK) return s;
+    constexpr int tp = 16;
+    if ((s = ensure(ctx, ctx->rhs, (size_t)pp.Np * tp * sizeof(float))) != LGP_OK ||
+        (s = ensure(ctx, ctx->sr_x, (size_t)pp.Np * tp * sizeof(float))) != LGP_OK)
+        return s;
+    float *vpad = (float *)ctx->rhs.p, *out = (float *)ctx->sr_x.p;
+    LGP_CUDA(cudaMemsetAsync(vpad, 0, (size_t)pp.Np * tp * sizeof(float), st));
+    launch_copy_cols(B, t, vpad, tp, N, t, 0, st);
+    LGP_CUDA(cudaGetLastError());
+    if ((s = autotune_tc(ctx, pp, vpad, tp, out, tp, tp, LGP_PREC_SPLIT_F16, st)) != LGP_OK) return s;
+    cudaEvent_t e0, e1;
+    LGP_CUDA(cudaEventCreate(&e0));
+    LGP_CUDA(cudaEventCreate(&e1));
+    float ms[2] = {0.0f, 0.0f};
+    for (int cand = 0; cand < 2 && s == LGP_OK; ++cand) {
+        for (int rep = 0; rep < 3 && s == LGP_OK; ++rep) {
+            cudaEventRecord(e0, st);
+            s = cand == 0 ? matvec_prepared(ctx, pp, B, t, out, t, t, LGP_PREC_FP32, nullptr, st)
+                          : matvec_prepared(ctx, pp, vpad, tp, out, tp, tp, LGP_PREC_SPLIT_F16, nullptr, st);
+            cudaEventRecord(e1, st);
+            float m = 0.0f;
+            if (s == LGP_OK && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&m, e0, e1) == cudaSuccess) {
+                if (rep > 0) ms[cand] += m;
+            } else if (s == LGP_OK) {
+                s = fail(ctx, LGP_ERR_CUDA, "batch route timing failed");
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != LGP_OK) return s;
+    *route = ms[1] < 0.9f * ms[0] ? 1 : 0;
+    ctx->batch_routes[key] = *route;
+    if (cache_path) tune_cache_store(cache_path, cache_key, *route);
+    return LGP_OK;
+}
+
+// One problem of a batched solve on the tensor-core route: its t columns zero-padded to 16 (a zero
+// column takes no iteration), one CG solve with the split-F16 product, the first t columns copied to
+// Xsol. Fills iters and rel_resid for its t columns; synchronises the internal stream.
+lgp_status batch_tc_solve(lgp_ctx *ctx, const lgp_hyper *h, const float *X, const float *B, float *Xsol, int64_t N,
+                          int t, const lgp_options *opt, int *iters, double *rel, bool *unconverged) {
+    NvtxRange nvtx_range("lgp.batch_tc_solve");
+    cudaStream_t st = ctx->work;
+    Prepared pp;
+    lgp_status s;
+    if ((s = prepare_x(ctx, h, X, N, st, &pp)) != LGP_OK) return s;
+    constexpr int tp = 16;
+    if ((s = ensure(ctx, ctx->rhs, (size_t)pp.Np * tp * sizeof(float))) != LGP_OK) return s;
+    float *bpad = (float *)ctx->rhs.p;
+    LGP_CUDA(cudaMemsetAsync(bpad, 0, (size_t)pp.Np * tp * sizeof(float), st));
+    launch_copy_cols(B, t, bpad, tp, N, t, 0, st);
+    LGP_CUDA(cudaGetLastError());
+    lgp_options o = *opt;
+    o.prec = LGP_PREC_SPLIT_F16;
+    o.precond_rank = 0;
+    o.flags = 0;
+    CgBuffers b;
+    if ((s = run_cg(ctx, pp, bpad, tp, tp, &o, 0, LGP_PREC_SPLIT_F16, &b)) != LGP_OK) return s;
+    launch_copy_cols(b.x, tp, Xsol, t, N, t, 0, st);
+    LGP_CUDA(cudaGetLastError());
+    LGP_CUDA(cudaMemcpyAsync(ctx->h_flags, ctx->flags.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    LGP_CUDA(cudaStreamSynchronize(st));
+    if (ctx->h_flags[1]) return fail(ctx, LGP_ERR_TIMEOUT, "a bounded device wait ran out (code %d)", ctx->h_flags[1]);
+    if (ctx->h_flags[0]) return fail(ctx, LGP_ERR_NONFINITE, "some X[g] contains NaN or Inf");
+    int it_all[kMaxT];
+    double rel_all[kMaxT];
+    const lgp_status cs = cg_status_of(ctx, *ctx->h_state, tp, it_all, rel_all, 0);
+    if (cs < 0) return cs;
+    for (int c = 0; c < t; ++c) {
+        iters[c] = it_all[c];
+        rel[c] = rel_all[c];
+        *unconverged |= ctx->h_state->active[c] != 0;
+    }
+    return LGP_OK;
+}
+
 }  // namespace
 
 // ============================================================================ C ABI
@@ -900,6 +1016,14 @@ int32_t lgp_tc_kernel_choice(const lgp_ctx *ctx, int64_t N, int32_t D, int32_t k
     auto it = ctx->tc_splits.find(key);
     if (it == ctx->tc_splits.end()) return LGP_TC_UNTUNED;
     return it->second == kTcSymmetric ? LGP_TC_SYMMETRIC : LGP_TC_ROW;
+}
+
+int32_t lgp_batch_route_choice(const lgp_ctx *ctx, int64_t N, int32_t D, int32_t kind, int32_t t) {
+    if (!ctx || N < 1 || D < 1 || D > kMaxD || !kind_supported(kind) || t < 1 || t > 16) return LGP_ERR_INVALID_ARG;
+    const std::vector<int64_t> key = {pad_rows(N), (int64_t)D, (int64_t)kind, (int64_t)t};
+    auto it = ctx->batch_routes.find(key);
+    if (it == ctx->batch_routes.end()) return LGP_BATCH_UNTUNED;
+    return it->second ? LGP_BATCH_TENSOR : LGP_BATCH_PERSISTENT;
 }
 
 lgp_status lgp_tc_distance_form(lgp_ctx *ctx, lgp_stream stream, int32_t *form, float *norm_max) {
@@ -1346,16 +1470,10 @@ lgp_status lgp_batch_cg_solve(lgp_ctx *ctx, int32_t n_gp, const lgp_hyper *hyp, 
     lgp_status s;
     if ((s = check_opts(ctx, opt, false)) != LGP_OK) return s;
     LGP_CUDA(cudaSetDevice(ctx->device));
-    std::vector<BatchGp> gps(n_gp);
-    std::vector<KernelParams> kps(n_gp);
-    std::vector<BatchItem> items;
-    std::vector<BatchVecBlock> vblocks;
-    const int rows_per_vblock = std::max(1, 4096 / t);
-    const int bm = batch_item_rows();
-    int64_t xs_total = 0, rows_total = 0, part_total = 0;
+    std::vector<KernelParams> kps_all(n_gp);
     for (int g = 0; g < n_gp; ++g) {
         if (N[g] < 1) return fail(ctx, LGP_ERR_INVALID_ARG, "N[%d]=%lld must be >= 1", g, (long long)N[g]);
-        if ((s = make_params(ctx, &hyp[g], &kps[g])) != LGP_OK) return s;
+        if ((s = make_params(ctx, &hyp[g], &kps_all[g])) != LGP_OK) return s;
         char nm[32];
         snprintf(nm, sizeof nm, "X[%d]", g);
         if ((s = check_dev_ptr(ctx, X[g], nm))) return s;
@@ -1364,21 +1482,62 @@ lgp_status lgp_batch_cg_solve(lgp_ctx *ctx, int32_t n_gp, const lgp_hyper *hyp, 
         snprintf(nm, sizeof nm, "Xsol[%d]", g);
         if ((s = check_dev_ptr(ctx, Xsol[g], nm))) return s;
         if ((const float *)Xsol[g] == B[g]) return fail(ctx, LGP_ERR_INVALID_ARG, "Xsol[%d] aliases B[%d]", g, g);
-        BatchGp &G = gps[g];
+    }
+    cudaStream_t user = (cudaStream_t)stream;
+    if ((s = enter(ctx, user)) != LGP_OK) return s;
+    cudaStream_t st = ctx->work;
+    LGP_CUDA(cudaMemsetAsync(ctx->flags.p, 0, 4 * sizeof(int), st));
+    // Route of each problem (timed once per shape): large problems whose tensor-core product measures
+    // faster solve on their own with it; the rest share the persistent batch launch.
+    std::vector<int> bids;  // problems of the persistent batch launch
+    std::vector<int> tc_ids;
+    for (int g = 0; g < n_gp; ++g) {
+        int route = 0;
+        if (opt->prec != LGP_PREC_FP32 && (s = batch_route(ctx, &hyp[g], X[g], N[g], B[g], t, &route)) != LGP_OK)
+            return s;
+        (route ? tc_ids : bids).push_back(g);
+    }
+    ctx->last_batch_tc = (int)tc_ids.size();
+    bool unconverged = false;
+    for (int g : tc_ids) {
+        if ((s = batch_tc_solve(ctx, &hyp[g], X[g], B[g], Xsol[g], N[g], t, opt, iters ? iters + (int64_t)g * t : nullptr,
+                                rel_resid ? rel_resid + (int64_t)g * t : nullptr, &unconverged)) != LGP_OK)
+            return s;
+    }
+    if (bids.empty()) {
+        if ((s = leave_sync(ctx, user)) != LGP_OK) return s;
+        if (unconverged) {
+            fail(ctx, LGP_WARN_NOT_CONVERGED, "some batched column reached max_iter before tol");
+            return LGP_WARN_NOT_CONVERGED;
+        }
+        return LGP_OK;
+    }
+    const int n_b = (int)bids.size();
+    std::vector<BatchGp> gps(n_b);
+    std::vector<KernelParams> kps(n_b);
+    std::vector<BatchItem> items;
+    std::vector<BatchVecBlock> vblocks;
+    const int rows_per_vblock = std::max(1, 4096 / t);
+    const int bm = batch_item_rows();
+    int64_t xs_total = 0, rows_total = 0, part_total = 0;
+    for (int q = 0; q < n_b; ++q) {
+        const int g = bids[q];
+        kps[q] = kps_all[g];
+        BatchGp &G = gps[q];
         G.N = N[g];
         G.Np = pad_rows(N[g]);
         G.xs_off = xs_total;
         G.vec_off = rows_total;
-        G.kind = kps[g].kind;
-        G.dpad = kps[g].dpad;
-        G.D = kps[g].D;
-        G.log2s2 = kps[g].log2_s2;
-        G.noise = kps[g].noise;
+        G.kind = kps[q].kind;
+        G.dpad = kps[q].dpad;
+        G.D = kps[q].D;
+        G.log2s2 = kps[q].log2_s2;
+        G.noise = kps[q].noise;
         G.B = B[g];
         G.Xsol = Xsol[g];
         G.blk0 = (int)vblocks.size();
         for (int64_t r0 = 0; r0 < G.N; r0 += rows_per_vblock)
-            vblocks.push_back({g, r0, std::min<int64_t>(G.N, r0 + rows_per_vblock)});
+            vblocks.push_back({q, r0, std::min<int64_t>(G.N, r0 + rows_per_vblock)});
         G.blk1 = (int)vblocks.size();
         // column splits so that this problem alone gives about two items per CTA slot of the persistent
         // product (its last iterations may run with no other problem left), each split a whole number
@@ -1392,7 +1551,7 @@ lgp_status lgp_batch_cg_solve(lgp_ctx *ctx, int32_t n_gp, const lgp_hyper *hyp, 
         G.part_off = part_total;
         if (G.splits > 1) part_total += (int64_t)G.splits * G.Np * t;
         for (int64_t rb = 0; rb < rb_n; ++rb)
-            for (int sp = 0; sp < G.splits; ++sp) items.push_back({g, (int)rb, sp});
+            for (int sp = 0; sp < G.splits; ++sp) items.push_back({q, (int)rb, sp});
         xs_total += G.Np * G.dpad;
         rows_total += G.Np;
     }
@@ -1400,7 +1559,7 @@ lgp_status lgp_batch_cg_solve(lgp_ctx *ctx, int32_t n_gp, const lgp_hyper *hyp, 
     std::stable_sort(items.begin(), items.end(), [&](const BatchItem &a, const BatchItem &b) {
         return std::min(gps[a.gp].N, gps[a.gp].cols_per_split) > std::min(gps[b.gp].N, gps[b.gp].cols_per_split);
     });
-    const int ng_t = n_gp * t;
+    const int ng_t = n_b * t;
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     size_t off = 0;
     const size_t o_gps = off; off = al(off + gps.size() * sizeof(BatchGp));
@@ -1408,7 +1567,7 @@ lgp_status lgp_batch_cg_solve(lgp_ctx *ctx, int32_t n_gp, const lgp_hyper *hyp, 
     const size_t o_vb = off; off = al(off + vblocks.size() * sizeof(BatchVecBlock));
     const size_t o_rr = off; off = al(off + 4 * (size_t)ng_t * sizeof(double));
     const size_t o_act = off; off = al(off + 2 * (size_t)ng_t * sizeof(int));
-    const size_t o_gpd = off; off = al(off + (size_t)n_gp * sizeof(int));
+    const size_t o_gpd = off; off = al(off + (size_t)n_b * sizeof(int));
     const size_t o_misc = off; off = al(off + 256);
     if ((s = ensure(ctx, ctx->batch_meta, off)) != LGP_OK) return s;
     if ((s = ensure(ctx, ctx->xs, (size_t)xs_total * sizeof(float))) != LGP_OK) return s;
@@ -1422,7 +1581,7 @@ lgp_status lgp_batch_cg_solve(lgp_ctx *ctx, int32_t n_gp, const lgp_hyper *hyp, 
     A.gps = (const BatchGp *)(meta + o_gps);
     A.items = (const BatchItem *)(meta + o_items);
     A.vblocks = (const BatchVecBlock *)(meta + o_vb);
-    A.n_gp = n_gp;
+    A.n_gp = n_b;
     A.n_items = (int)items.size();
     A.n_vblocks = (int)vblocks.size();
     A.t = t;
@@ -1449,18 +1608,14 @@ lgp_status lgp_batch_cg_solve(lgp_ctx *ctx, int32_t n_gp, const lgp_hyper *hyp, 
     A.item_counter = (int *)(meta + o_misc + 4);
     A.st = (BatchState *)(meta + o_misc + 64);
 
-    cudaStream_t user = (cudaStream_t)stream;
-    if ((s = enter(ctx, user)) != LGP_OK) return s;
-    cudaStream_t st = ctx->work;
-    LGP_CUDA(cudaMemsetAsync(ctx->flags.p, 0, 4 * sizeof(int), st));
     LGP_CUDA(cudaMemcpyAsync(meta + o_gps, gps.data(), gps.size() * sizeof(BatchGp), cudaMemcpyHostToDevice, st));
     LGP_CUDA(cudaMemcpyAsync(meta + o_items, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice,
                              st));
     LGP_CUDA(cudaMemcpyAsync(meta + o_vb, vblocks.data(), vblocks.size() * sizeof(BatchVecBlock),
                              cudaMemcpyHostToDevice, st));
-    for (int g = 0; g < n_gp; ++g)
-        launch_prep_x(X[g], gps[g].N, kps[g].D, kps[g].dpad, kps[g].scale, (float *)ctx->xs.p + gps[g].xs_off,
-                      gps[g].Np, (int *)ctx->flags.p, st);
+    for (int q = 0; q < n_b; ++q)
+        launch_prep_x(X[bids[q]], gps[q].N, kps[q].D, kps[q].dpad, kps[q].scale, (float *)ctx->xs.p + gps[q].xs_off,
+                      gps[q].Np, (int *)ctx->flags.p, st);
     LGP_CUDA(launch_batch_init(A, opt->tol, opt->max_iter, st));
 
     // one graph: a conditional WHILE node whose body is a chunk of iterations plus the condition kernel,
@@ -1513,10 +1668,10 @@ lgp_status lgp_batch_cg_solve(lgp_ctx *ctx, int32_t n_gp, const lgp_hyper *hyp, 
     LGP_CUDA(cudaMemcpyAsync(ctx->h_flags, ctx->flags.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
     if ((s = leave_sync(ctx, user)) != LGP_OK) return s;
     if (ctx->h_flags[0]) return fail(ctx, LGP_ERR_NONFINITE, "some X[g] contains NaN or Inf");
-    bool unconverged = false;
     for (int k = 0; k < ng_t; ++k) {
-        if (iters) iters[k] = h_it[k];
-        if (rel_resid) rel_resid[k] = h_b2[k] > 0.0 ? std::sqrt(h_rr[k] / h_b2[k]) : 0.0;
+        const int64_t dst = (int64_t)bids[k / t] * t + k % t;
+        if (iters) iters[dst] = h_it[k];
+        if (rel_resid) rel_resid[dst] = h_b2[k] > 0.0 ? std::sqrt(h_rr[k] / h_b2[k]) : 0.0;
         if (h_act[k]) unconverged = true;
     }
     if (h_st.status & 1) return fail(ctx, LGP_ERR_NONFINITE, "non-finite value in some B[g] or a CG scalar");

@@ -106,3 +106,31 @@ def test_batch_edge_cases(lgp):
     with pytest.raises(lgp.LGPError) as e:
         lgp.lgp_batch_cg_solve([_dev(q.X)], [q], [_dev(np.ones((1, 17), np.float32))])
     assert e.value.status == lgp.LGP_ERR_UNSUPPORTED
+
+
+def test_batch_routes_reach_the_same_backward_error(lgp):
+    """Problems large enough for the tensor-core route (N >= 2048): the default call, whose route per shape
+    is timed, and the same call with prec = FP32, which keeps every problem in the persistent batch launch,
+    each reach a componentwise backward error below 1e-5 on sampled rows (FP64 row oracle), and the route
+    diagnostic names a route for every shape after the call."""
+    probs = wl.cfg5_batch(n_gp=6, t=8, seed=21, n_lo=2500, n_hi=9000)
+    Bs = [_rhs(p, 8, g) for g, p in enumerate(probs)]
+    ctx = lgp.Context(0)
+    rng = np.random.default_rng(9)
+    for prec in (lgp.LGP_PREC_AUTO, lgp.LGP_PREC_FP32):
+        sols, iters, rel, s = lgp.lgp_batch_cg_solve([_dev(p.X) for p in probs], probs, [_dev(B) for B in Bs],
+                                                     tol=1e-6, max_iter=6000, prec=prec, ctx=ctx)
+        assert s == lgp.LGP_OK and (rel <= 1e-6).all()
+        worst = 0.0
+        for p, B, x in zip(probs, Bs, sols):
+            rows = rng.choice(p.N, 32, replace=False)
+            xs = x.cpu().numpy()
+            Kx, _ = oracle.kyv_rows_c(p.X, xs, go.hyper_of(p), rows=rows)
+            Kabs, _ = oracle.kyv_rows_c(p.X, np.abs(xs), go.hyper_of(p), rows=rows)
+            worst = max(worst, float((np.abs(B[rows] - Kx) / (Kabs + np.abs(B[rows]))).max()))
+        routes = [ctx.batch_route_choice(p.N, p.D, p.kind, 8) for p in probs]
+        print(f"prec {prec}: routes {routes}, iterations {iters.max()}, worst backward error {worst:.2e}")
+        assert worst <= 1e-5
+        assert all(r in (lgp.LGP_BATCH_PERSISTENT, lgp.LGP_BATCH_TENSOR) for r in routes)
+    assert ctx.batch_route_choice(100, 2, wl.RBF, 8) == lgp.LGP_BATCH_UNTUNED
+    ctx.close()

@@ -2,8 +2,9 @@
 
 The GPU forms r^2 = a_i + a_j - 2 u_i . u_j from box-centred coordinates u. It splits them as
 u = h + m in float16, takes three Gram products (h h + m h + h m) with float32 accumulation, and
-computes a_j = sum(h^2 + 2 h m) so that r^2_ii = 0 up to rounding. This model repeats those
-roundings in NumPy (float16 splits, float32 sums) on the same seeded data and compares the
+computes a_j = sum(h^2 + 2 h m) so that r^2_ii = 0 up to rounding (the Matern forms then take the
+absolute value of the rounded r^2). This model repeats those roundings in NumPy (float16 splits,
+float32 sums) on the same seeded data and compares the
 resulting entries and products with the FP64 oracle. Three properties are checked:
 
 - near each kernel's limit on max |u|^2 (RBF 97, Matern-3/2 134, Matern-5/2 403, prescaled
@@ -39,15 +40,17 @@ def _dot_form_sq_dist(xs):
     g = (h @ h.T + m @ h.T + h @ m.T).astype(np.float32)
     a = (h * h + 2 * h * m).sum(1).astype(np.float32)
     d = (np.float32(2) * g - a[None, :]).astype(np.float32)  # the Gram value 2 u_i.u_j - a_j
-    return np.maximum((a[:, None] - d).astype(np.float32), np.float32(0)), float(((xs - c).astype(np.float64) ** 2).sum(1).max())
+    return (a[:, None] - d).astype(np.float32), float(((xs - c).astype(np.float64) ** 2).sum(1).max())
 
 
 def _entries(kind, r2, s2):
-    """k from prescaled squared distances (the oracle's forms on the prescaled coordinates)."""
+    """k from prescaled squared distances (the oracle's forms on the prescaled coordinates). As on the GPU,
+    the RBF exponent takes the rounded value as it is, and the Matern forms its absolute value."""
     r2 = r2.astype(np.float64)
     if kind == wl.RBF:
         return s2 * np.exp2(-r2)
-    r = np.sqrt(r2)
+    r = np.sqrt(np.abs(r2))
+    r2 = np.abs(r2)
     if kind == wl.MATERN52:
         return s2 * (1 + r + r * r / 3) * np.exp(-r)
     if kind == wl.MATERN32:
