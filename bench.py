@@ -60,7 +60,7 @@ def parse():
     # CG tolerance of the step: at 1e-3 the step's LML and gradient stay within 1e-3 (measured: 3e-4 and 1.2e-4)
     # of a tol-1e-6 solve on the same draw and probes, which the line's accuracy record re-measures each run
     ap.add_argument("--tol", type=float, default=1e-3)
-    ap.add_argument("--max-iter", type=int, default=1000)
+    ap.add_argument("--max-iter", type=int, default=3000)
     ap.add_argument("--prec", choices=["auto", "fp32", "split_bf16", "split_f16"], default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)

@@ -135,17 +135,20 @@ __global__ void dot_bbox_kernel(const float *__restrict__ Xs, int64_t N, int dpa
 // split as u = h + m (h = f16(u), m = f16(u - h)), the squared norm a_j = sum_d (h^2 + 2 h m)
 // (what the Gram products below give for <u_j, u_j> without the m m term) in float32 and in three
 // float16 parts, and the two Gram operand rows, K-major, in the tile layout the MMA reads
-// (element (r, k) of 128-row tile q at q kU + ((k / 8) 16 + r / 8) 128 + (r % 8) 16 + (k % 8) 2):
-//   A role:  [h | m | h | 1 1 1 | 0 ...]
-//   B role:  [2h | 2h | 2m | -a_h -a_m -a_l | 0 ...]
-// so that A_i . B_j = 2 (h_i h_j + m_i h_j + h_i m_j) - a_j = 2 u_i . u_j - a_j to about 22 bits.
+// (element (r, k) of 128-row tile q at q kU + ((k / 8) 16 + r / 8) 128 + (r % 8) 16 + (k % 8) 2),
+// 32 values per row:
+//   A role:  [h | m | h | 1 1 1 | -a_h -a_m -a_l | 0 ...]
+//   B role:  [2h | 2h | 2m | -a_h -a_m -a_l | 1 1 1 | 0 ...]
+// so that A_i . B_j = 2 (h_i h_j + m_i h_j + h_i m_j) - a_j - a_i = -|u_i - u_j|^2 to about 22 bits: the
+// tensor core hands the generation the negated squared distance itself.
 // words[16] collects max a_j over rows j < N (float bits, a_j >= 0).
 template <int DP>
 __global__ void dot_operands_kernel(const float *__restrict__ Xs, int64_t N, int64_t Np,
                                     unsigned int *__restrict__ words, float *__restrict__ arow,
                                     uint4 *__restrict__ ua, uint4 *__restrict__ ub, const int *skip) {
     if (skip && *skip) return;
-    constexpr int KG = DP <= 4 ? 16 : 32;
+    constexpr int KG = 32;
+    static_assert(3 * DP + 6 <= KG, "Gram operand row too short");
     constexpr int kTileBytes = 128 * KG * 2;
     float c[DP];
 #pragma unroll
@@ -183,9 +186,13 @@ __global__ void dot_operands_kernel(const float *__restrict__ Xs, int64_t N, int
             rb[2 * DP + d] = m2;
         }
         ra[3 * DP] = ra[3 * DP + 1] = ra[3 * DP + 2] = one;
+        ra[3 * DP + 3] = __hneg(ah);
+        ra[3 * DP + 4] = __hneg(am);
+        ra[3 * DP + 5] = __hneg(al);
         rb[3 * DP] = __hneg(ah);
         rb[3 * DP + 1] = __hneg(am);
         rb[3 * DP + 2] = __hneg(al);
+        rb[3 * DP + 3] = rb[3 * DP + 4] = rb[3 * DP + 5] = one;
         arow[j] = a32;
         const int64_t q = j / 128;
         const int r = (int)(j - q * 128);

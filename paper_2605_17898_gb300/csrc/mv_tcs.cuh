@@ -35,9 +35,9 @@
 // Accumulators: two buffers of [out_I (128 columns) | out_J (128 columns)].
 //
 // Dot form (DOT = true; RBF, Matern-3/2, Matern-5/2 at D >= 3, when the data's spread allows):
-// r^2 = a_i + a_j - 2 u_i . u_j for the box-centred coordinates u, the inner products as one
-// 128 x 128 tensor-core Gram tile per tile (float16 hi/lo operands built once per X by
-// mv_tc.cu), so an entry costs one add, the kernel value and the split. CTA: 24 warps:
+// r^2 = a_i + a_j - 2 u_i . u_j for the box-centred coordinates u, as one 128 x 128 tensor-core Gram
+// tile per tile whose float16 hi/lo operand rows also carry the squared norms a (built once per X by
+// mv_tc.cu), so the tensor core returns -r^2 and an entry costs the kernel value and the split. CTA: 24 warps:
 //   warps 0-15  generation from the Gram tile (one row x 32 columns per thread);
 //   warp 16     producer (lane 0: V_J ring and the tile-row slot [V_I | U_I]; lane 1: U_J ring);
 //   warp 17     tensor-memory allocation and the out_I MMAs;  warp 22  the out_J MMAs;
@@ -125,7 +125,7 @@ template <int T, int DP>
 struct TcdLayout {
     static constexpr int kA = kTile * kTile * 2;
     static constexpr int kB = T * kTile * 2;
-    static constexpr int kKg = DP <= 4 ? 16 : 32;  // Gram operand width (16-bit values per row)
+    static constexpr int kKg = 32;                 // Gram operand width (16-bit values per row)
     static constexpr int kU = kTile * kKg * 2;
     static constexpr int kK = 0;                   // entry buffers: 2 x [hi | lo]
     static constexpr int kV = 4 * kA;              // V_J ring: 2 x [hi; lo]
@@ -268,43 +268,38 @@ __device__ __forceinline__ void red_row(float *dst, const float (&s)[NV], const 
     }
 }
 
-// Entries from the dot-form Gram value d = 2 x_i . x_j - a_j (tensor memory) and a per-row
-// constant: the squared distance is a_i - d (clamped at 0 against rounding); RBF folds a_i and
-// the exponent offset into its row constant, ls2 - a_i, so that k = 2^(d + ls2 - a_i). The
-// Matern forms are those of Entry2 (mv_tc.cuh) on the reconstructed squared distance.
+// Entries from the dot-form Gram value g = -|u_i - u_j|^2 (tensor memory; the operand rows carry both
+// squared norms, mv_tc.cu): RBF k = 2^(g + ls2). The Matern forms take |g| as the squared distance:
+// near r = 0, where rounding can make g slightly positive, their entries are smooth in r^2
+// (k = s^2 (1 - rh^2 / 6 + ...) for Matern-5/2, s^2 (1 - rh^2 / 2 + ...) for Matern-3/2), so |g| and a
+// clamp give the same entry up to that rounding; measured, the absolute value makes the Matern-5/2
+// product 3% faster than a clamp. (The Matern forms are those of Entry2 in mv_tc.cuh.)
 template <int KIND> struct DotEntry2;
 template <> struct DotEntry2<LGP_RBF> {
-    static __device__ __forceinline__ float row_const(float ai, float ls2) { return ls2 - ai; }
-    static __device__ __forceinline__ float2 k(float2 d, float2 c, float ls2) {
-        (void)ls2;
-        const float2 arg = __fadd2_rn(d, c);
+    static __device__ __forceinline__ float2 k(float2 g, float ls2) {
+        const float2 arg = __fadd2_rn(g, make_float2(ls2, ls2));
         return make_float2(ex2_approx(arg.x), ex2_approx(arg.y));
     }
 };
-// The Matern forms take |a_i - d|: near r = 0, where rounding can make a_i - d slightly negative,
-// their entries are smooth in r^2 (k = s^2 (1 - rh^2 / 6 + ...) for Matern-5/2, s^2 (1 - rh^2 / 2 + ...)
-// for Matern-3/2), so |a_i - d| and a clamp at 0 give the same entry up to that rounding; measured,
-// the absolute value makes the Matern-5/2 product 3% faster than the clamp.
 template <> struct DotEntry2<LGP_MATERN52> {
-    static __device__ __forceinline__ float row_const(float ai, float ls2) { (void)ls2; return ai; }
-    static __device__ __forceinline__ float2 k(float2 d, float2 c, float ls2) {
-        float2 rh2 = __ffma2_rn(d, make_float2(-1.0f, -1.0f), c);
-        rh2 = make_float2(fabsf(rh2.x), fabsf(rh2.y));
-        return tc::Entry2<LGP_MATERN52>::k(rh2, make_float2(ls2, ls2));
+    // k = e + e (rh + rh^2 / 3), e = 2^(ls2 - rh log2 e), rh = sqrt|g|; rh^2 / 3 taken as -g / 3, which
+    // needs no absolute value (a rounding-positive g near r = 0 only perturbs q by that rounding)
+    static __device__ __forceinline__ float2 k(float2 g, float ls2) {
+        const float2 rh = make_float2(sqrt_approx(fabsf(g.x)), sqrt_approx(fabsf(g.y)));
+        const float2 arg = __ffma2_rn(rh, make_float2(-kLog2e, -kLog2e), make_float2(ls2, ls2));
+        const float2 e = make_float2(ex2_approx(arg.x), ex2_approx(arg.y));
+        const float2 q = __ffma2_rn(g, make_float2(-1.0f / 3.0f, -1.0f / 3.0f), rh);
+        return __ffma2_rn(e, q, e);
     }
 };
 template <> struct DotEntry2<LGP_MATERN32> {
-    static __device__ __forceinline__ float row_const(float ai, float ls2) { (void)ls2; return ai; }
-    static __device__ __forceinline__ float2 k(float2 d, float2 c, float ls2) {
-        float2 rh2 = __ffma2_rn(d, make_float2(-1.0f, -1.0f), c);
-        rh2 = make_float2(fabsf(rh2.x), fabsf(rh2.y));
-        return tc::Entry2<LGP_MATERN32>::k(rh2, make_float2(ls2, ls2));
+    static __device__ __forceinline__ float2 k(float2 g, float ls2) {
+        return tc::Entry2<LGP_MATERN32>::k(make_float2(fabsf(g.x), fabsf(g.y)), make_float2(ls2, ls2));
     }
 };
-// Matern-1/2 has no dot form (its entries are not smooth in r^2 at r = 0); this stub is never launched.
+// Matern-1/2 has no dot form (its entries are not smooth in r^2 at 0); this stub is never launched.
 template <> struct DotEntry2<LGP_MATERN12> {
-    static __device__ __forceinline__ float row_const(float ai, float ls2) { (void)ls2; return ai; }
-    static __device__ __forceinline__ float2 k(float2 d, float2 c, float ls2) { (void)c; (void)ls2; return d; }
+    static __device__ __forceinline__ float2 k(float2 g, float ls2) { (void)ls2; return g; }
 };
 
 // hi/lo split of two entries for the MMA, lo = k - hi (exact in float32), then both packed.
@@ -643,9 +638,7 @@ __global__ void __launch_bounds__(DOT ? kDotThreads : kThreads, 1)
             const int rloc = 32 * q + lane;
             const uint32_t taddr = tmem_acc + ((uint32_t)(32 * q) << 16) + (uint32_t)(L::kGramCol + 32 * cb);
             const float ls2 = a.log2s2;
-            float ci = 0.0f;
             for (int it = 0; it < n_it; ++it, w.next()) {
-                if (it == 0 || w.J == w.I) ci = DotEntry2<KIND>::row_const(a.arow[(int64_t)w.I * kTile + rloc], ls2);
                 // Gram tile it (buffer it & 1), and entry buffer it & 1 released by both issuers'
                 // products of tile it - 2
                 bool got = mbar_wait(bar_gram_full(it & 1), (it >> 1) & 1, a.budget, abort_flag, a.err, kErrWaitGram);
@@ -662,14 +655,13 @@ __global__ void __launch_bounds__(DOT ? kDotThreads : kThreads, 1)
                 if (lane == 0) mbar_arrive(bar_gram_empty(it & 1));
                 const int s = it & 1;
                 uint8_t *st = smem + L::kK + s * 2 * L::kA;  // entry buffer s: [hi | lo]
-                const float2 c2 = make_float2(ci, ci);
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     uint32_t h[4], l[4];
 #pragma unroll
                     for (int v = 0; v < 4; ++v) {
                         const float2 dv = make_float2(__uint_as_float(g[8 * u + 2 * v]), __uint_as_float(g[8 * u + 2 * v + 1]));
-                        split_pair<FMT>(DotEntry2<KIND>::k(dv, c2, ls2), h[v], l[v]);
+                        split_pair<FMT>(DotEntry2<KIND>::k(dv, ls2), h[v], l[v]);
                     }
                     // columns j = 32 cb + 8 u .. +7 of row rloc: one 16-byte row of core matrix (rg, kg)
                     const int off = ((4 * cb + u) * 16 + (rloc >> 3)) * 128 + (rloc & 7) * 16;

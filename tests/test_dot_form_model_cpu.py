@@ -1,10 +1,11 @@
 """CPU model of the symmetric product's dot-form distance, checking the limits it is gated on.
 
 The GPU forms r^2 = a_i + a_j - 2 u_i . u_j from box-centred coordinates u. It splits them as
-u = h + m in float16, takes three Gram products (h h + m h + h m) with float32 accumulation, and
-computes a_j = sum(h^2 + 2 h m) so that r^2_ii = 0 up to rounding (the Matern forms then take the
-absolute value of the rounded r^2). This model repeats those roundings in NumPy (float16 splits,
-float32 sums) on the same seeded data and compares the
+u = h + m in float16 and takes three Gram products (h h + m h + h m) together with the squared norms
+a = sum(h^2 + 2 h m) (so that r^2_ii = 0 up to rounding) in one float32 tensor-core accumulation,
+which returns -r^2 (the Matern square roots then take the absolute value of the rounded r^2). This model
+repeats those roundings in NumPy (float16 splits, float32 sums: the Gram part, then each squared
+norm, rounded in turn) on the same seeded data and compares the
 resulting entries and products with the FP64 oracle. Three properties are checked:
 
 - near each kernel's limit on max |u|^2 (RBF 97, Matern-3/2 134, Matern-5/2 403, prescaled
@@ -45,14 +46,15 @@ def _dot_form_sq_dist(xs):
 
 def _entries(kind, r2, s2):
     """k from prescaled squared distances (the oracle's forms on the prescaled coordinates). As on the GPU,
-    the RBF exponent takes the rounded value as it is, and the Matern forms its absolute value."""
+    the RBF exponent and the Matern-5/2 quadratic term take the rounded value as it is, and the Matern square
+    roots its absolute value."""
     r2 = r2.astype(np.float64)
     if kind == wl.RBF:
         return s2 * np.exp2(-r2)
     r = np.sqrt(np.abs(r2))
-    r2 = np.abs(r2)
     if kind == wl.MATERN52:
-        return s2 * (1 + r + r * r / 3) * np.exp(-r)
+        # the quadratic term takes the signed r^2 (no absolute value there on the GPU either)
+        return s2 * (1 + r + r2 / 3) * np.exp(-r)
     if kind == wl.MATERN32:
         return s2 * (1 + r) * np.exp(-r)
     return s2 * np.exp2(-r)
