@@ -301,15 +301,17 @@ lgp_status lgp_rademacher_probes(lgp_ctx *ctx, uint64_t seed, int64_t N, int32_t
  * Many independent GP solves of uneven size in one call: for g < n_gp,
  * Xsol[g] = K_y(g)^{-1} B[g] with K_y(g) from hyp[g] and X[g] ([N[g], hyp[g].D]),
  * B[g] and Xsol[g] device [N[g], t], 1 <= t <= 16. Each problem takes one of two routes,
- * chosen per shape (padded N, D, kind, t) by timing both products once on the caller's
- * own data (the Sec. 5 gap: no batched solves):
+ * chosen per shape (padded N, D, kind, t) by timing, once, what a CG iteration of that
+ * problem costs on each route on the caller's own data (the Sec. 5 gap: no batched solves):
  *   - the persistent batch: all such problems advance together, each CG iteration one
  *     float32 product launch over a work list of (problem, row block, column range)
  *     items plus one launch per vector update, the loop one CUDA graph with a
- *     device-side while node;
- *   - the tensor-core route (problems of at least 2048 rows whose split-F16 product with
- *     the columns zero-padded to 16 measures at least 10% faster): its own CG solve with
- *     that product, as lgp_cg_solve with prec = LGP_PREC_SPLIT_F16.
+ *     device-side while node. A problem's cost there is its float32 product less that
+ *     product's launch floor (timed on its first 256 rows), which the batch pays once;
+ *   - the tensor-core route (problems of at least 2048 rows whose standalone CG iteration
+ *     with the split-F16 product, columns zero-padded to 16, measures at least 10% cheaper
+ *     than that marginal cost): its own CG solve with that product, as lgp_cg_solve with
+ *     prec = LGP_PREC_SPLIT_F16.
  * opt->prec = LGP_PREC_FP32 keeps every problem in the persistent batch; LGP_AUTOTUNE=0
  * too. iters (HOST [n_gp * t], may be NULL) and rel_resid (HOST [n_gp * t], may be NULL)
  * are per problem and column. Synchronises `stream`.

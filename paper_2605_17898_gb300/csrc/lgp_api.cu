@@ -800,12 +800,17 @@ lgp_status cg_status_of(lgp_ctx *ctx, const CgState &h, int t, int *iters, doubl
 // Smallest problem the batched solver times for the tensor-core route (smaller ones stay in the batch).
 constexpr int64_t kBatchTcMinN = 2048;
 
-// Route of one problem of a batched solve with t <= 16 columns: time, on the caller's own X and
-// right-hand sides, one float32 product with t columns (the arithmetic of the persistent batch launch)
-// against one split-F16 tensor-core product with the columns zero-padded to 16 (the kernel that
-// autotune_tc picks for that shape), and keep the faster (the tensor-core one only if at least 10%
-// faster, since it carries the padding and per-problem launches). Cached per shape in the context and,
-// with LGP_AUTOTUNE_CACHE, in the same file as the product choices (key suffix |route).
+// Route of one problem of a batched solve with t <= 16 columns, chosen by what each route costs per
+// CG iteration, timed on the caller's own X and right-hand sides:
+// - persistent batch launch (float32 products): the problem's marginal cost there, i.e. one float32
+//   product with its t columns minus the same product on its first 256 rows (the launch floor, which
+//   the batch launch pays once for all its problems);
+// - tensor-core route: an iteration of a standalone CG solve with the split-F16 product, its columns
+//   zero-padded to 16 (the product, the CG updates and the graph launches, all paid per problem):
+//   the difference of two short solves (1 and 3 chunks of iterations, at tol 0) over 2 chunks.
+// The tensor-core route is kept only if at least 10% cheaper. The short solves run only when the bare
+// tensor-core product already passes that test. Cached per shape in the context and, with
+// LGP_AUTOTUNE_CACHE, in the same file as the product choices (key suffix |route).
 lgp_status batch_route(lgp_ctx *ctx, const lgp_hyper *h, const float *X, int64_t N, const float *B, int t,
                        int *route) {
     NvtxRange nvtx_range("lgp.batch_route");
@@ -830,40 +835,69 @@ lgp_status batch_route(lgp_ctx *ctx, const lgp_hyper *h, const float *X, int64_t
         return LGP_OK;
     }
     cudaStream_t st = ctx->work;
-    Prepared pp;
-    lgp_status s;
-    if ((s = prepare_x(ctx, h, X, N, st, &pp)) != LGP_OK) return s;
     constexpr int tp = 16;
-    if ((s = ensure(ctx, ctx->rhs, (size_t)pp.Np * tp * sizeof(float))) != LGP_OK ||
-        (s = ensure(ctx, ctx->sr_x, (size_t)pp.Np * tp * sizeof(float))) != LGP_OK)
+    constexpr int64_t kFloorRows = 256;
+    lgp_status s;
+    if ((s = ensure(ctx, ctx->rhs, (size_t)pad_rows(N) * tp * sizeof(float))) != LGP_OK ||
+        (s = ensure(ctx, ctx->sr_x, (size_t)pad_rows(N) * tp * sizeof(float))) != LGP_OK)
         return s;
     float *vpad = (float *)ctx->rhs.p, *out = (float *)ctx->sr_x.p;
-    LGP_CUDA(cudaMemsetAsync(vpad, 0, (size_t)pp.Np * tp * sizeof(float), st));
-    launch_copy_cols(B, t, vpad, tp, N, t, 0, st);
-    LGP_CUDA(cudaGetLastError());
-    if ((s = autotune_tc(ctx, pp, vpad, tp, out, tp, tp, LGP_PREC_SPLIT_F16, st)) != LGP_OK) return s;
     cudaEvent_t e0, e1;
     LGP_CUDA(cudaEventCreate(&e0));
     LGP_CUDA(cudaEventCreate(&e1));
-    float ms[2] = {0.0f, 0.0f};
-    for (int cand = 0; cand < 2 && s == LGP_OK; ++cand) {
-        for (int rep = 0; rep < 3 && s == LGP_OK; ++rep) {
+    // mean time of fn() over `reps` calls on the stream, after one untimed call
+    auto timed = [&](auto fn, int reps, float *mean_ms) -> lgp_status {
+        *mean_ms = 0.0f;
+        for (int rep = 0; rep <= reps; ++rep) {
             cudaEventRecord(e0, st);
-            s = cand == 0 ? matvec_prepared(ctx, pp, B, t, out, t, t, LGP_PREC_FP32, nullptr, st)
-                          : matvec_prepared(ctx, pp, vpad, tp, out, tp, tp, LGP_PREC_SPLIT_F16, nullptr, st);
+            lgp_status r = fn();
             cudaEventRecord(e1, st);
+            if (r != LGP_OK) return r;
             float m = 0.0f;
-            if (s == LGP_OK && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&m, e0, e1) == cudaSuccess) {
-                if (rep > 0) ms[cand] += m;
-            } else if (s == LGP_OK) {
-                s = fail(ctx, LGP_ERR_CUDA, "batch route timing failed");
-            }
+            if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&m, e0, e1) != cudaSuccess)
+                return fail(ctx, LGP_ERR_CUDA, "batch route timing failed");
+            if (rep > 0) *mean_ms += m / reps;
         }
+        return LGP_OK;
+    };
+    float ms_floor = 0.0f, ms_fp32 = 0.0f, ms_tc = 0.0f;
+    Prepared pp;
+    // the launch floor: the float32 product of the first rows only (B is row-major, so its first rows
+    // are that problem's right-hand sides)
+    if ((s = prepare_x(ctx, h, X, kFloorRows, st, &pp)) == LGP_OK)
+        s = timed([&] { return matvec_prepared(ctx, pp, B, t, out, t, t, LGP_PREC_FP32, nullptr, st); }, 2, &ms_floor);
+    if (s == LGP_OK) s = prepare_x(ctx, h, X, N, st, &pp);
+    if (s == LGP_OK) {
+        LGP_CUDA(cudaMemsetAsync(vpad, 0, (size_t)pp.Np * tp * sizeof(float), st));
+        launch_copy_cols(B, t, vpad, tp, N, t, 0, st);
+        LGP_CUDA(cudaGetLastError());
+        s = autotune_tc(ctx, pp, vpad, tp, out, tp, tp, LGP_PREC_SPLIT_F16, st);
+    }
+    if (s == LGP_OK)
+        s = timed([&] { return matvec_prepared(ctx, pp, B, t, out, t, t, LGP_PREC_FP32, nullptr, st); }, 2, &ms_fp32);
+    if (s == LGP_OK)
+        s = timed([&] { return matvec_prepared(ctx, pp, vpad, tp, out, tp, tp, LGP_PREC_SPLIT_F16, nullptr, st); }, 2,
+                  &ms_tc);
+    const float marginal = ms_fp32 - ms_floor;
+    if (s == LGP_OK && ms_tc < 0.9f * marginal) {
+        lgp_options o = {};
+        o.tol = 0.0;  // never met: each short solve runs its whole chunk budget
+        o.prec = LGP_PREC_SPLIT_F16;
+        float ms_short[2] = {0.0f, 0.0f};
+        for (int k = 0; k < 2 && s == LGP_OK; ++k) {
+            o.max_iter = (1 + 2 * k) * kChunk;
+            s = timed(
+                [&] {
+                    CgBuffers b;
+                    return run_cg(ctx, pp, vpad, tp, tp, &o, 0, LGP_PREC_SPLIT_F16, &b);
+                },
+                2, &ms_short[k]);
+        }
+        if (s == LGP_OK) *route = (ms_short[1] - ms_short[0]) / (2 * kChunk) < 0.9f * marginal ? 1 : 0;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (s != LGP_OK) return s;
-    *route = ms[1] < 0.9f * ms[0] ? 1 : 0;
     ctx->batch_routes[key] = *route;
     if (cache_path) tune_cache_store(cache_path, cache_key, *route);
     return LGP_OK;

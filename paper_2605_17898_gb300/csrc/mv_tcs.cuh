@@ -332,6 +332,8 @@ __device__ __forceinline__ void split_pair(float2 k, uint32_t &h, uint32_t &l) {
 // cycles whatever the loop overhead, and the unrolled issue code competes for the instruction cache
 // with the generation warps (measured: the dot-form product is ~25% faster rolled). The difference
 // form's single issuer runs both directions and stays unrolled (rolled, it measured ~6% slower).
+// The dot form's three issuers poll their barriers without a back-off sleep (measured ~0.5% faster
+// than a 32 ns sleep between polls).
 //
 // DOT selects the dot form of the squared distance (D is then 4 or 8, the padded width DP).
 template <int KIND, int D, int T, int FMT, bool DOT = false>
@@ -535,10 +537,10 @@ __global__ void __launch_bounds__(DOT ? kDotThreads : kThreads, 1)
                     const int s = it & 1;
                     const int buf = it % NB;
                     if (it >= NB &&
-                        !mbar_wait(bar_acc_empty(buf), ((it / NB) - 1) & 1, a.budget, abort_flag, a.err, kErrWaitAcc, 32))
+                        !mbar_wait(bar_acc_empty(buf), ((it / NB) - 1) & 1, a.budget, abort_flag, a.err, kErrWaitAcc))
                         break;
-                    if (!mbar_wait(bar_full(s), (it >> 1) & 1, a.budget, abort_flag, a.err, kErrWaitFull, 32)) break;
-                    if (!mbar_wait(bar_ready(s), (it >> 1) & 1, a.budget, abort_flag, a.err, kErrWaitReady, 32)) break;
+                    if (!mbar_wait(bar_full(s), (it >> 1) & 1, a.budget, abort_flag, a.err, kErrWaitFull)) break;
+                    if (!mbar_wait(bar_ready(s), (it >> 1) & 1, a.budget, abort_flag, a.err, kErrWaitReady)) break;
                     tc_fence_after();
                     const uint32_t acc_i = tmem_acc + (uint32_t)(buf * L::kAccStride);
                     const uint32_t ka = smem_u32(smem + L::kK + s * 2 * L::kA);
@@ -776,10 +778,10 @@ __global__ void __launch_bounds__(DOT ? kDotThreads : kThreads, 1)
                     const int s = it & 1;
                     const int buf = it % NB;
                     if (it >= NB &&
-                        !mbar_wait(bar_acc_empty(buf), ((it / NB) - 1) & 1, a.budget, abort_flag, a.err, kErrWaitAcc, 32))
+                        !mbar_wait(bar_acc_empty(buf), ((it / NB) - 1) & 1, a.budget, abort_flag, a.err, kErrWaitAcc))
                         break;
-                    if (seg_first && !mbar_wait(bar_vi_full(0), sg & 1, a.budget, abort_flag, a.err, kErrWaitVi, 32)) break;
-                    if (!mbar_wait(bar_ready(s), (it >> 1) & 1, a.budget, abort_flag, a.err, kErrWaitReady, 32)) break;
+                    if (seg_first && !mbar_wait(bar_vi_full(0), sg & 1, a.budget, abort_flag, a.err, kErrWaitVi)) break;
+                    if (!mbar_wait(bar_ready(s), (it >> 1) & 1, a.budget, abort_flag, a.err, kErrWaitReady)) break;
                     tc_fence_after();
                     if (!diag) {
                         const uint32_t acc_j = tmem_acc + (uint32_t)(buf * L::kAccStride + L::kAccJ);
@@ -824,10 +826,10 @@ __global__ void __launch_bounds__(DOT ? kDotThreads : kThreads, 1)
                     if (seg_first) ++sg;
                     const int b = k & 1;  // Gram buffer and U_J ring slot
                     if (k >= 2 &&
-                        !mbar_wait(bar_gram_empty(b), ((k >> 1) - 1) & 1, a.budget, abort_flag, a.err, kErrWaitGram, 32))
+                        !mbar_wait(bar_gram_empty(b), ((k >> 1) - 1) & 1, a.budget, abort_flag, a.err, kErrWaitGram))
                         break;
-                    if (!mbar_wait(bar_u_full(b), (k >> 1) & 1, a.budget, abort_flag, a.err, kErrWaitFull, 32)) break;
-                    if (seg_first && !mbar_wait(bar_vi_full(0), sg & 1, a.budget, abort_flag, a.err, kErrWaitVi, 32)) break;
+                    if (!mbar_wait(bar_u_full(b), (k >> 1) & 1, a.budget, abort_flag, a.err, kErrWaitFull)) break;
+                    if (seg_first && !mbar_wait(bar_vi_full(0), sg & 1, a.budget, abort_flag, a.err, kErrWaitVi)) break;
                     tc_fence_after();
                     const uint32_t ua = smem_u32(smem + L::kVi + 2 * L::kB);
                     const uint32_t ub = smem_u32(smem + L::kUr + b * L::kU);
