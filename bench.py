@@ -794,6 +794,11 @@ def bench_accuracy(lgp, ctx, p, X, y, args, prec, seed, lml, grad):
                                                        tol=args.ref_tol, max_iter=20000, prec=prec, ctx=ctx,
                                                        precond_rank=args.precond_rank)
     ref_s = time.perf_counter() - t0
+    # the Lanczos truncation of the log-determinant: the step's tolerance and probes with the longest
+    # tridiagonal the library keeps
+    lml_lmax, _, info_lmax = lgp.lgp_lml_and_grad(X, y, p, n_probes=m, lanczos_steps=lgp.LGP_MAX_LANCZOS_STEPS,
+                                                  seed=seed, tol=args.tol, max_iter=args.max_iter, prec=prec, ctx=ctx,
+                                                  precond_rank=args.precond_rank, want_grad=False)
     g = np.asarray(grad)
     gr = np.asarray(grad_ref)
     gs = np.maximum(np.abs(gr), 1e-2 * np.abs(gr).max())
@@ -802,9 +807,12 @@ def bench_accuracy(lgp, ctx, p, X, y, args, prec, seed, lml, grad):
             "ref_tol": args.ref_tol, "ref_iters_max": info_ref["iters_max"], "ref_seconds": ref_s,
             "lml_ref": lml_ref, "lml_rel_shift": abs(lml - lml_ref) / abs(lml_ref),
             "grad_rel_shift_max": float((np.abs(g - gr) / gs).max()),
+            "lanczos_steps": args.lanczos, "lanczos_max": lgp.LGP_MAX_LANCZOS_STEPS, "lml_lanczos_max": lml_lmax,
+            "logdet_lanczos_max": info_lmax["logdet"], "lml_rel_shift_lanczos": abs(lml - lml_lmax) / abs(lml_lmax),
             "note": "residuals of [y | probes] solved at tol with the step's product, recomputed with the FP32 "
                     "product over all rows; shifts = |step - tight solve| on the same probes (gradient relative "
-                    "to max(|g_p|, 1e-2 max|g|))"}
+                    "to max(|g_p|, 1e-2 max|g|)); lml_rel_shift_lanczos = |step - the same step with "
+                    "lanczos_max Lanczos steps|, the truncation of the log-determinant quadrature"}
 
 
 def time_adjoint(lgp, ctx, p, X, y, args, dev, prec, rank, flush_buf):

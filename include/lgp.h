@@ -38,7 +38,7 @@
  *   - Errors: arguments are checked before any launch. A negative status means
  *     the outputs are undefined; a positive status means they are valid with a
  *     warning. lgp_last_error_message() describes the last failure.
- *   - Limits: 1 <= D <= 8, 1 <= t <= 64, N >= 1, 1 <= lanczos_steps <= 64.
+ *   - Limits: 1 <= D <= 8, 1 <= t <= 64, N >= 1, 1 <= lanczos_steps <= 1024.
  *   - Thread safety: a context must not be used by two host threads at once.
  */
 #ifndef LGP_H
@@ -92,7 +92,11 @@ typedef struct {
 typedef struct {
     double tol;              /* stop column c when ||r_c|| / ||b_c|| <= tol (recursive residual) */
     int32_t max_iter;        /* CG iteration cap, >= 1 */
-    int32_t lanczos_steps;   /* L: CG steps per probe kept for the Lanczos tridiagonal */
+    int32_t lanczos_steps;   /* L: CG steps per probe kept for the Lanczos tridiagonal (1..1024).
+                              * The log-determinant quadrature uses min(L, that probe's CG
+                              * iterations) steps. Too few steps bias it when K_y is badly
+                              * conditioned. With L at least the iteration count, the whole
+                              * Krylov space of the solve is used. */
     int32_t n_probes;        /* m Rademacher probes; the solve block is [y, z_1..z_m], t = m + 1 */
     int32_t prec;            /* lgp_precision of the products inside the solve */
     uint64_t seed;           /* probe seed (see lgp_rademacher_probes) */
@@ -112,6 +116,8 @@ typedef struct {
  *   comparison for the batched path. Same estimator and results up to float32 rounding; prec is
  *   ignored (always FP32); precond_rank must be 0. Ignored by the other entry points. */
 enum { LGP_OPT_WARM_START = 1, LGP_OPT_SINGLE_RHS = 2 };
+/* Largest lgp_options.lanczos_steps accepted. */
+enum { LGP_MAX_LANCZOS_STEPS = 1024 };
 
 typedef struct {
     double lml;              /* log marginal likelihood estimate */
@@ -258,7 +264,7 @@ lgp_status lgp_cg_solve(lgp_ctx *ctx, const lgp_hyper *hyp, const float *X, cons
  *            for theta = (log l_1..log l_D, log s^2, log sigma_n^2).
  * X [N, D] and y [N] are device arrays. lml (HOST, may be NULL), grad (HOST
  * [D + 2], may be NULL: the adjoint pass is then skipped), info (HOST, may be
- * NULL). n_probes >= 1 and 1 <= lanczos_steps <= 64. Synchronises `stream`.
+ * NULL). n_probes >= 1 and 1 <= lanczos_steps <= 1024. Synchronises `stream`.
  */
 lgp_status lgp_lml_and_grad(lgp_ctx *ctx, const lgp_hyper *hyp, const float *X, const float *y, int64_t N,
                             const lgp_options *opt, double *lml, double *grad, lgp_lml_info *info,

@@ -20,7 +20,9 @@ namespace lgp {
 
 constexpr int kMaxD = 8;
 constexpr int kMaxT = 64;
-constexpr int kMaxLanczos = 64;
+// Lanczos steps kept per column for the log-determinant quadrature (the quadrature kernel holds the
+// tridiagonal in shared memory: 4 x 8 bytes per step)
+constexpr int kMaxLanczos = 1024;
 constexpr int kMaxRank = 32;  // largest pivoted-Cholesky preconditioner rank
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kTwoLn2 = 1.3862943611198906f;

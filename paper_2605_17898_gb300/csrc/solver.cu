@@ -378,27 +378,28 @@ __global__ void __launch_bounds__(kSlqThreads) slq_quad_kernel(const CgState *st
     }
     if (tid == 0) s_bad = 0;
     __syncthreads();
-    if (tid < m) {
-        const double al = hist_alpha[(int64_t)tid * t + c];
-        const double be = hist_beta[(int64_t)tid * t + c];
-        sal[tid] = al;
-        sbe[tid] = be;
-        if (!(al > 0.0) || !isfinite(al) || (tid + 1 < m && (!(be >= 0.0) || !isfinite(be)))) atomicOr(&s_bad, 1);
+    for (int k = tid; k < m; k += kSlqThreads) {
+        const double al = hist_alpha[(int64_t)k * t + c];
+        const double be = hist_beta[(int64_t)k * t + c];
+        sal[k] = al;
+        sbe[k] = be;
+        if (!(al > 0.0) || !isfinite(al) || (k + 1 < m && (!(be >= 0.0) || !isfinite(be)))) atomicOr(&s_bad, 1);
     }
     __syncthreads();
-    if (tid < m) {
-        double a = 1.0 / sal[tid];
-        if (tid > 0) a += sbe[tid - 1] / sal[tid - 1];
-        sa[tid] = a;
-        sbb[tid] = tid + 1 < m ? sbe[tid] / (sal[tid] * sal[tid]) : 0.0;  // b_k^2
+    for (int k = tid; k < m; k += kSlqThreads) {
+        double a = 1.0 / sal[k];
+        if (k > 0) a += sbe[k - 1] / sal[k - 1];
+        sa[k] = a;
+        sbb[k] = k + 1 < m ? sbe[k] / (sal[k] * sal[k]) : 0.0;  // b_k^2
     }
     __syncthreads();
     // Gershgorin upper bound of the spectrum (max reduction over the rows)
     double g = 0.0;
-    if (tid < m) {
-        g = sa[tid];
-        if (tid > 0) g += sqrt(sbb[tid - 1]);
-        if (tid + 1 < m) g += sqrt(sbb[tid]);
+    for (int k = tid; k < m; k += kSlqThreads) {
+        double gk = sa[k];
+        if (k > 0) gk += sqrt(sbb[k - 1]);
+        if (k + 1 < m) gk += sqrt(sbb[k]);
+        g = fmax(g, gk);
     }
     red[tid] = g;
     __syncthreads();

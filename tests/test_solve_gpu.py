@@ -151,6 +151,30 @@ def test_slq_quadrature_against_probe_targets(lgp, n, L):
         assert info["logdet"] == pytest.approx(est["logdet"], rel=1e-4)
 
 
+@pytest.mark.parametrize("L", [512, 1024])
+def test_long_lanczos_against_oracle(lgp, L):
+    """Lanczos lengths beyond one quadrature thread per step (m > 256 steps kept), on a badly conditioned
+    problem (Matern-5/2, D=3, lengthscales in [0.3, 1], noise 1e-3, N=2000: ~840 CG iterations at tol
+    1e-6 in float64): the GPU log-determinant and LML against the FP64 estimator with the same L, probes
+    and tolerance. L = 1024 is the largest accepted; 1025 is refused."""
+    p, m = wl.random_problem(2000, 3, wl.MATERN52, seed=41, lo=0.3, hi=1.0, log_noise=math.log(1e-3)), 15
+    hyp = go.hyper_of(p)
+    seed, tol = 4321, 1e-6
+    lml, _, info = lgp.lgp_lml_and_grad(_dev(p.X), _dev(p.y), p, n_probes=m, lanczos_steps=L, seed=seed, tol=tol,
+                                        max_iter=3000, want_grad=False)
+    est = go.estimator_fp64(p.X, p.y, hyp, n_probes=m, lanczos_steps=L, seed=seed, tol=tol, max_iter=3000)
+    print(f"L={L}: logdet gpu {info['logdet']:.6f} fp64 {est['logdet']:.6f}, iterations "
+          f"{info['iters_min']}..{info['iters_max']}")
+    assert info["iters_max"] > 256  # the quadrature kernel's strided loads are exercised
+    assert info["logdet"] == pytest.approx(est["logdet"], abs=1e-3 * abs(est["lml"]))
+    assert lml == pytest.approx(est["lml"], rel=1e-3)
+    if L == 1024:
+        with pytest.raises(lgp.LGPError) as e:
+            lgp.lgp_lml_and_grad(_dev(p.X), _dev(p.y), p, n_probes=m, lanczos_steps=lgp.LGP_MAX_LANCZOS_STEPS + 1,
+                                 seed=seed, tol=tol)
+        assert e.value.status == lgp.LGP_ERR_UNSUPPORTED
+
+
 def test_single_column_path_and_batched_path_meet_the_same_gate(lgp):
     """Equal accuracy of the two paths the bench compares, on the mBCG workload's distribution at N=3000:
     the batched split-F16 mBCG step and the plain FP32 single-column step (every column its own CG run
