@@ -610,13 +610,19 @@ def _bench_batch_set(lgp, ctx, args, dev, label, probs):
     n_sm = torch.cuda.get_device_properties(dev.index or 0).multi_processor_count
     fp32_peak = n_sm * FP32_LANES_PER_SM * MAX_SM_MHZ_NOMINAL * 1e6
     routes = [ctx.batch_route_choice(q.N, q.D, q.kind, 8) for q in probs]
+    # column splits of the persistent-route problems: the timed choice against the fixed rule
+    splits = [(q.N, ctx.batch_split_choice(q.N, q.D, q.kind, 8), ctx.batch_split_rule(q.N))
+              for q, r in zip(probs, routes) if r == lgp.LGP_BATCH_PERSISTENT]
     return {"mode": "batch", "workload": label, "n_gp": len(probs), "t": 8, "pairs_per_product": pairs,
             "N_min": min(q.N for q in probs), "N_max": max(q.N for q in probs), **res,
             "speedup": res["one_call_per_gp"]["ms"] / res["batched"]["ms"],
             "batched_pair_rhs_per_s": pr,
             "batched_fp32_equiv_frac": ops / (res["batched"]["ms"] / 1e3) / fp32_peak,
             "tensor_route_problems": sum(1 for r in routes if r == lgp.LGP_BATCH_TENSOR),
-            "tensor_route_N": sorted(q.N for q, r in zip(probs, routes) if r == lgp.LGP_BATCH_TENSOR)}
+            "tensor_route_N": sorted(q.N for q, r in zip(probs, routes) if r == lgp.LGP_BATCH_TENSOR),
+            "persistent_splits": {"tuned_equal_to_rule": sum(1 for _, a, b in splits if a == b),
+                                  "tuned_differs": [[n, a, b] for n, a, b in sorted(splits) if a != b],
+                                  "note": "[N, timed split count, fixed rule's count] of persistent-route problems"}}
 
 
 def bench_predict(lgp, ctx, p, args, dev, prec, rank):

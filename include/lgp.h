@@ -333,6 +333,17 @@ lgp_status lgp_batch_cg_solve(lgp_ctx *ctx, int32_t n_gp, const lgp_hyper *hyp, 
 enum { LGP_BATCH_UNTUNED = 0, LGP_BATCH_PERSISTENT = 1, LGP_BATCH_TENSOR = 2 };
 int32_t lgp_batch_route_choice(const lgp_ctx *ctx, int64_t N, int32_t D, int32_t kind, int32_t t);
 
+/* Column splits of the persistent batched product that lgp_batch_cg_solve chose for a problem of N rows,
+ * dimension D, kernel `kind` and t columns (diagnostic; no counterpart in the paper). Each problem's
+ * 256-row blocks are split S ways over whole 64-column tiles. S is timed per shape on the caller's own
+ * data, with the problem alone in the work list (its last iterations, when no other problem is left),
+ * among the fixed rule's count and a quarter, half, double and four times it. Returns S >= 1, 0 before
+ * the first batched solve with that shape, or a negative lgp_status for invalid arguments. */
+int32_t lgp_batch_split_choice(const lgp_ctx *ctx, int64_t N, int32_t D, int32_t kind, int32_t t);
+/* The fixed rule's split count for a problem of N rows alone: about two items per CTA slot of the
+ * persistent launch, at least four 64-column tiles per split (diagnostic). */
+int32_t lgp_batch_split_rule(const lgp_ctx *ctx, int64_t N);
+
 /*
  * Measurement support (no counterpart in the paper): throughput of one GPU pipe on the
  * current device, timed with CUDA events on `stream` at the clock the GPU runs.

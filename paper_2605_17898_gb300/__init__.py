@@ -56,7 +56,7 @@ EXPORTED = [
     "lgp_kernel_matvec", "lgp_kernel_matvec_grad", "lgp_cg_solve", "lgp_lml_and_grad",
     "lgp_rademacher_probes", "lgp_batch_cg_solve", "lgp_kernel_matvec_noalloc",
     "lgp_measure_pipe_peak", "lgp_tc_kernel_choice", "lgp_predict", "lgp_tc_distance_form",
-    "lgp_kernel_matvec_noalloc_status", "lgp_batch_route_choice",
+    "lgp_kernel_matvec_noalloc_status", "lgp_batch_route_choice", "lgp_batch_split_choice", "lgp_batch_split_rule",
 ]
 
 
@@ -131,6 +131,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
                                                   vp]),
         "lgp_kernel_matvec_noalloc_status": (c.c_int32, [vp]),
         "lgp_batch_route_choice": (c.c_int32, [vp, c.c_int64, c.c_int32, c.c_int32, c.c_int32]),
+        "lgp_batch_split_choice": (c.c_int32, [vp, c.c_int64, c.c_int32, c.c_int32, c.c_int32]),
+        "lgp_batch_split_rule": (c.c_int32, [vp, c.c_int64]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -229,6 +231,14 @@ class Context:
     def batch_route_choice(self, N: int, D: int, kind: int, t: int) -> int:
         """LGP_BATCH_UNTUNED / LGP_BATCH_PERSISTENT / LGP_BATCH_TENSOR for that batched-problem shape."""
         return int(self.lib.lgp_batch_route_choice(self.h, int(N), int(D), int(kind), int(t)))
+
+    def batch_split_choice(self, N: int, D: int, kind: int, t: int) -> int:
+        """Column splits the batched solver chose for that persistent-route problem shape (0: untuned)."""
+        return int(self.lib.lgp_batch_split_choice(self.h, int(N), int(D), int(kind), int(t)))
+
+    def batch_split_rule(self, N: int) -> int:
+        """The fixed rule's column-split count for a problem of N rows alone."""
+        return int(self.lib.lgp_batch_split_rule(self.h, int(N)))
 
     def tc_distance_form(self, stream=None) -> tuple[int, float]:
         """(LGP_DIST_NONE / LGP_DIST_DIFF / LGP_DIST_DOT, max |u|^2 or -1) of the last symmetric product."""

@@ -368,7 +368,7 @@ cudaError_t launch_batch_init(const BatchArgs &a, double tol, int max_iter, cuda
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch_iteration(const BatchArgs &a, int num_sms, cudaStream_t st) {
+cudaError_t launch_batch_product(const BatchArgs &a, int num_sms, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(a.item_counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
     const int grid = std::max(1, std::min(a.n_items, num_sms * 6));
@@ -380,10 +380,16 @@ cudaError_t launch_batch_iteration(const BatchArgs &a, int num_sms, cudaStream_t
         case 16: batch_mv_kernel<16><<<grid, kBatchThreads, 0, st>>>(a); break;
         default: return cudaErrorInvalidValue;
     }
+    bsplit_reduce_kernel<<<a.n_vblocks, vec_threads(a.t), 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_iteration(const BatchArgs &a, int num_sms, cudaStream_t st) {
+    cudaError_t e = launch_batch_product(a, num_sms, st);
+    if (e != cudaSuccess) return e;
     const int n = a.n_gp * a.t;
     const int sb = (n + 255) / 256;
     const int vt = vec_threads(a.t);
-    bsplit_reduce_kernel<<<a.n_vblocks, vt, 0, st>>>(a);
     bpkp_kernel<<<a.n_vblocks, vt, 0, st>>>(a);
     balpha_kernel<<<sb, 256, 0, st>>>(a);
     bxr_kernel<<<a.n_vblocks, vt, 0, st>>>(a);

@@ -57,6 +57,9 @@ struct BatchArgs {
 
 int batch_item_rows();
 cudaError_t launch_batch_init(const BatchArgs &a, double tol, int max_iter, cudaStream_t st);
+// The product alone (K_y p of every active problem, column-split partial sums reduced): the part of an
+// iteration that the split choice changes, timed by the split tuner.
+cudaError_t launch_batch_product(const BatchArgs &a, int num_sms, cudaStream_t st);
 cudaError_t launch_batch_iteration(const BatchArgs &a, int num_sms, cudaStream_t st);
 cudaError_t launch_batch_copy_out(const BatchArgs &a, cudaStream_t st);
 // Body tail of the device-side batch loop: condition = not done and under the chunk cap.

@@ -60,6 +60,7 @@ struct lgp_ctx {
     // route of a batched problem shape, keyed by (Np, D, kind, t): 0 = the persistent batch launch,
     // 1 = its own solve with the tensor-core product (timed once per shape, batch_route)
     std::map<std::vector<int64_t>, int> batch_routes;
+    std::map<std::vector<int64_t>, int> batch_splits;  // column splits of a persistent-batch problem, per shape
     // the last symmetric-tile product: its kind, padded rows and columns (for the distance-form query)
     int sym_kind = -1, sym_D = 0, sym_t = 0;
     int64_t sym_Np = 0;
@@ -943,6 +944,214 @@ lgp_status batch_tc_solve(lgp_ctx *ctx, const lgp_hyper *h, const float *X, cons
     return LGP_OK;
 }
 
+// The work list of a persistent batched solve: per problem its layout in the shared buffers, its vector
+// blocks, and its (row block, column split) items.
+struct BatchPlan {
+    std::vector<BatchGp> gps;
+    std::vector<KernelParams> kps;
+    std::vector<const float *> X;
+    std::vector<BatchItem> items;
+    std::vector<BatchVecBlock> vblocks;
+    int64_t xs_total = 0, rows_total = 0, part_total = 0;
+};
+
+// Appends one problem (rows N, parameters kp, caller's X, B, Xsol) with its row blocks split S ways over
+// whole 64-column tiles.
+void plan_add_problem(BatchPlan &P, int64_t N, const KernelParams &kp, const float *X, const float *B, float *Xsol,
+                      int t, int64_t S) {
+    const int q = (int)P.gps.size();
+    const int rows_per_vblock = std::max(1, 4096 / t);
+    const int bm = batch_item_rows();
+    BatchGp G;
+    G.N = N;
+    G.Np = pad_rows(N);
+    G.xs_off = P.xs_total;
+    G.vec_off = P.rows_total;
+    G.kind = kp.kind;
+    G.dpad = kp.dpad;
+    G.D = kp.D;
+    G.log2s2 = kp.log2_s2;
+    G.noise = kp.noise;
+    G.B = B;
+    G.Xsol = Xsol;
+    G.blk0 = (int)P.vblocks.size();
+    for (int64_t r0 = 0; r0 < G.N; r0 += rows_per_vblock)
+        P.vblocks.push_back({q, r0, std::min<int64_t>(G.N, r0 + rows_per_vblock)});
+    G.blk1 = (int)P.vblocks.size();
+    const int64_t rb_n = (G.N + bm - 1) / bm;
+    const int64_t col_tiles = (G.N + 63) / 64;
+    S = std::max<int64_t>(1, std::min<int64_t>(S, col_tiles));
+    G.cols_per_split = (col_tiles + S - 1) / S * 64;
+    G.splits = (int)((G.N + G.cols_per_split - 1) / G.cols_per_split);
+    G.part_off = P.part_total;
+    if (G.splits > 1) P.part_total += (int64_t)G.splits * G.Np * t;
+    for (int64_t rb = 0; rb < rb_n; ++rb)
+        for (int sp = 0; sp < G.splits; ++sp) P.items.push_back({q, (int)rb, sp});
+    P.xs_total += G.Np * G.dpad;
+    P.rows_total += G.Np;
+    P.gps.push_back(G);
+    P.kps.push_back(kp);
+    P.X.push_back(X);
+}
+
+// Column splits of a problem alone in the persistent product by the fixed rule: about two items per CTA
+// slot (its last iterations may run with no other problem left), at least four column tiles per split.
+int64_t batch_split_rule(const lgp_ctx *ctx, int64_t N) {
+    const int bm = batch_item_rows();
+    const int64_t rb_n = (N + bm - 1) / bm;
+    const int64_t col_tiles = (N + 63) / 64;
+    const int64_t S = std::max<int64_t>(1, (2 * ctx->num_sms + rb_n - 1) / rb_n);
+    return std::min<int64_t>(S, std::max<int64_t>(1, col_tiles / 4));
+}
+
+// Sorts the plan's items (longest first: an item of problem g costs ~min(N_g, cols_per_split_g)), places
+// the plan in the context's buffers, uploads it, prescales every problem's X and fills the device
+// arguments A. Stream-ordered on st.
+lgp_status upload_batch_plan(lgp_ctx *ctx, BatchPlan &P, int t, cudaStream_t st, BatchArgs *Aout) {
+    lgp_status s;
+    const int n_b = (int)P.gps.size();
+    std::stable_sort(P.items.begin(), P.items.end(), [&](const BatchItem &a, const BatchItem &b) {
+        return std::min(P.gps[a.gp].N, P.gps[a.gp].cols_per_split) > std::min(P.gps[b.gp].N, P.gps[b.gp].cols_per_split);
+    });
+    const int ng_t = n_b * t;
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    size_t off = 0;
+    const size_t o_gps = off; off = al(off + P.gps.size() * sizeof(BatchGp));
+    const size_t o_items = off; off = al(off + P.items.size() * sizeof(BatchItem));
+    const size_t o_vb = off; off = al(off + P.vblocks.size() * sizeof(BatchVecBlock));
+    const size_t o_rr = off; off = al(off + 4 * (size_t)ng_t * sizeof(double));
+    const size_t o_act = off; off = al(off + 2 * (size_t)ng_t * sizeof(int));
+    const size_t o_gpd = off; off = al(off + (size_t)n_b * sizeof(int));
+    const size_t o_misc = off; off = al(off + 256);
+    if ((s = ensure(ctx, ctx->batch_meta, off)) != LGP_OK) return s;
+    if ((s = ensure(ctx, ctx->xs, (size_t)P.xs_total * sizeof(float))) != LGP_OK) return s;
+    if ((s = ensure(ctx, ctx->cg_vec, (size_t)4 * P.rows_total * t * sizeof(float))) != LGP_OK) return s;
+    if ((s = ensure(ctx, ctx->cg_partial, P.vblocks.size() * (size_t)t * sizeof(double))) != LGP_OK) return s;
+    if ((s = ensure(ctx, ctx->batch_part, (size_t)std::max<int64_t>(P.part_total, 1) * sizeof(float))) != LGP_OK)
+        return s;
+    if ((s = ensure(ctx, ctx->flags, 64)) != LGP_OK) return s;
+    unsigned char *meta = (unsigned char *)ctx->batch_meta.p;
+    BatchArgs A;
+    A.gps = (const BatchGp *)(meta + o_gps);
+    A.items = (const BatchItem *)(meta + o_items);
+    A.vblocks = (const BatchVecBlock *)(meta + o_vb);
+    A.n_gp = n_b;
+    A.n_items = (int)P.items.size();
+    A.n_vblocks = (int)P.vblocks.size();
+    A.t = t;
+    A.tt = 1;
+    while (A.tt < t) A.tt *= 2;
+    A.Xs = (const float *)ctx->xs.p;
+    float *v = (float *)ctx->cg_vec.p;
+    A.x = v;
+    A.r = v + P.rows_total * t;
+    A.p = v + 2 * P.rows_total * t;
+    A.kp = v + 3 * P.rows_total * t;
+    A.part = (float *)ctx->batch_part.p;
+    A.partial = (double *)ctx->cg_partial.p;
+    double *dd = (double *)(meta + o_rr);
+    A.rr = dd;
+    A.bnorm2 = dd + ng_t;
+    A.alpha = dd + 2 * ng_t;
+    A.beta = dd + 3 * ng_t;
+    int *ii = (int *)(meta + o_act);
+    A.active = ii;
+    A.iters = ii + ng_t;
+    A.gp_done = (int *)(meta + o_gpd);
+    A.done = (int *)(meta + o_misc);
+    A.item_counter = (int *)(meta + o_misc + 4);
+    A.st = (BatchState *)(meta + o_misc + 64);
+    LGP_CUDA(cudaMemcpyAsync(meta + o_gps, P.gps.data(), P.gps.size() * sizeof(BatchGp), cudaMemcpyHostToDevice, st));
+    LGP_CUDA(cudaMemcpyAsync(meta + o_items, P.items.data(), P.items.size() * sizeof(BatchItem),
+                             cudaMemcpyHostToDevice, st));
+    LGP_CUDA(cudaMemcpyAsync(meta + o_vb, P.vblocks.data(), P.vblocks.size() * sizeof(BatchVecBlock),
+                             cudaMemcpyHostToDevice, st));
+    for (int q = 0; q < n_b; ++q)
+        launch_prep_x(P.X[q], P.gps[q].N, P.kps[q].D, P.kps[q].dpad, P.kps[q].scale,
+                      (float *)ctx->xs.p + P.gps[q].xs_off, P.gps[q].Np, (int *)ctx->flags.p, st);
+    LGP_CUDA(cudaGetLastError());
+    *Aout = A;
+    return LGP_OK;
+}
+
+// Column splits of one problem of the persistent batch, timed per shape (padded N, D, kind, t) on the
+// caller's own X and right-hand sides: the problem alone in the work list (the case its split count
+// decides: its last iterations, with no other problem left) with the fixed rule's count and with a
+// quarter, half, double and four times that many (at least one, at most one 64-column tile per split).
+// Each candidate: one untimed and three timed products (the persistent launch and its split
+// reduction, CUDA events). Cached in the context and, with LGP_AUTOTUNE_CACHE, in the product-choice
+// file (key suffix |split); LGP_AUTOTUNE=0 keeps the rule.
+lgp_status batch_split_choice(lgp_ctx *ctx, const KernelParams &kp, const lgp_hyper *h, const float *X,
+                              const float *B, int64_t N, int t, int64_t *S_out) {
+    const std::vector<int64_t> key = {pad_rows(N), (int64_t)h->D, (int64_t)h->kind, (int64_t)t};
+    const int64_t rule = batch_split_rule(ctx, N);
+    *S_out = rule;
+    auto it = ctx->batch_splits.find(key);
+    if (it != ctx->batch_splits.end()) {
+        *S_out = it->second;
+        return LGP_OK;
+    }
+    const char *env = std::getenv("LGP_AUTOTUNE");
+    const int64_t col_tiles = (N + 63) / 64;
+    if ((env && env[0] == '0') || col_tiles < 2) {
+        ctx->batch_splits[key] = (int)rule;
+        return LGP_OK;
+    }
+    const char *cache_path = std::getenv("LGP_AUTOTUNE_CACHE");
+    const std::string cache_key = cache_path ? tune_cache_key(ctx, key) + "|split" : std::string();
+    int cached = 0;
+    if (cache_path && tune_cache_lookup(cache_path, cache_key, &cached) && cached >= 1) {
+        ctx->batch_splits[key] = cached;
+        *S_out = cached;
+        return LGP_OK;
+    }
+    std::vector<int64_t> cands;
+    for (int64_t c : {rule / 4, rule / 2, rule, 2 * rule, 4 * rule}) {
+        c = std::max<int64_t>(1, std::min<int64_t>(c, col_tiles));
+        if (std::find(cands.begin(), cands.end(), c) == cands.end()) cands.push_back(c);
+    }
+    cudaStream_t st = ctx->work;
+    cudaEvent_t e0, e1;
+    LGP_CUDA(cudaEventCreate(&e0));
+    LGP_CUDA(cudaEventCreate(&e1));
+    lgp_status s = LGP_OK;
+    float best_ms = 0.0f;
+    int64_t best = rule;
+    for (size_t k = 0; k < cands.size() && s == LGP_OK; ++k) {
+        BatchPlan P;
+        plan_add_problem(P, N, kp, X, B, nullptr, t, cands[k]);
+        BatchArgs A;
+        if ((s = upload_batch_plan(ctx, P, t, st, &A)) != LGP_OK) break;
+        if (launch_batch_init(A, 0.0, 1, st) != cudaSuccess) {
+            s = fail(ctx, LGP_ERR_CUDA, "batch split tuning: init failed");
+            break;
+        }
+        float ms = 0.0f;
+        for (int rep = 0; rep < 4 && s == LGP_OK; ++rep) {
+            cudaEventRecord(e0, st);
+            const cudaError_t ce = launch_batch_product(A, ctx->num_sms, st);
+            cudaEventRecord(e1, st);
+            float m = 0.0f;
+            if (ce != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&m, e0, e1) != cudaSuccess)
+                s = fail(ctx, LGP_ERR_CUDA, "batch split tuning: timing failed");
+            else if (rep > 0)
+                ms += m;
+        }
+        if (s == LGP_OK && (k == 0 || ms < best_ms)) {
+            best_ms = ms;
+            best = cands[k];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != LGP_OK) return s;
+    ctx->batch_splits[key] = (int)best;
+    *S_out = best;
+    if (cache_path) tune_cache_store(cache_path, cache_key, (int)best);
+    return LGP_OK;
+}
+
 }  // namespace
 
 // ============================================================================ C ABI
@@ -1058,6 +1267,18 @@ int32_t lgp_batch_route_choice(const lgp_ctx *ctx, int64_t N, int32_t D, int32_t
     auto it = ctx->batch_routes.find(key);
     if (it == ctx->batch_routes.end()) return LGP_BATCH_UNTUNED;
     return it->second ? LGP_BATCH_TENSOR : LGP_BATCH_PERSISTENT;
+}
+
+int32_t lgp_batch_split_choice(const lgp_ctx *ctx, int64_t N, int32_t D, int32_t kind, int32_t t) {
+    if (!ctx || N < 1 || D < 1 || D > kMaxD || !kind_supported(kind) || t < 1 || t > 16) return LGP_ERR_INVALID_ARG;
+    const std::vector<int64_t> key = {pad_rows(N), (int64_t)D, (int64_t)kind, (int64_t)t};
+    auto it = ctx->batch_splits.find(key);
+    return it == ctx->batch_splits.end() ? 0 : it->second;
+}
+
+int32_t lgp_batch_split_rule(const lgp_ctx *ctx, int64_t N) {
+    if (!ctx || N < 1) return LGP_ERR_INVALID_ARG;
+    return (int32_t)batch_split_rule(ctx, N);
 }
 
 lgp_status lgp_tc_distance_form(lgp_ctx *ctx, lgp_stream stream, int32_t *form, float *norm_max) {
@@ -1547,109 +1768,18 @@ lgp_status lgp_batch_cg_solve(lgp_ctx *ctx, int32_t n_gp, const lgp_hyper *hyp, 
         return LGP_OK;
     }
     const int n_b = (int)bids.size();
-    std::vector<BatchGp> gps(n_b);
-    std::vector<KernelParams> kps(n_b);
-    std::vector<BatchItem> items;
-    std::vector<BatchVecBlock> vblocks;
-    const int rows_per_vblock = std::max(1, 4096 / t);
-    const int bm = batch_item_rows();
-    int64_t xs_total = 0, rows_total = 0, part_total = 0;
+    // the work list of the persistent launch: each problem's column splits timed per shape (the problem
+    // alone), then every persistent-route problem with its own splits
+    BatchPlan P;
     for (int q = 0; q < n_b; ++q) {
         const int g = bids[q];
-        kps[q] = kps_all[g];
-        BatchGp &G = gps[q];
-        G.N = N[g];
-        G.Np = pad_rows(N[g]);
-        G.xs_off = xs_total;
-        G.vec_off = rows_total;
-        G.kind = kps[q].kind;
-        G.dpad = kps[q].dpad;
-        G.D = kps[q].D;
-        G.log2s2 = kps[q].log2_s2;
-        G.noise = kps[q].noise;
-        G.B = B[g];
-        G.Xsol = Xsol[g];
-        G.blk0 = (int)vblocks.size();
-        for (int64_t r0 = 0; r0 < G.N; r0 += rows_per_vblock)
-            vblocks.push_back({q, r0, std::min<int64_t>(G.N, r0 + rows_per_vblock)});
-        G.blk1 = (int)vblocks.size();
-        // column splits so that this problem alone gives about two items per CTA slot of the persistent
-        // product (its last iterations may run with no other problem left), each split a whole number
-        // of 64-column tiles
-        const int64_t rb_n = (G.N + bm - 1) / bm;
-        const int64_t col_tiles = (G.N + 63) / 64;
-        int64_t S = std::max<int64_t>(1, (2 * ctx->num_sms + rb_n - 1) / rb_n);
-        S = std::min<int64_t>(S, std::max<int64_t>(1, col_tiles / 4));
-        G.cols_per_split = (col_tiles + S - 1) / S * 64;
-        G.splits = (int)((G.N + G.cols_per_split - 1) / G.cols_per_split);
-        G.part_off = part_total;
-        if (G.splits > 1) part_total += (int64_t)G.splits * G.Np * t;
-        for (int64_t rb = 0; rb < rb_n; ++rb)
-            for (int sp = 0; sp < G.splits; ++sp) items.push_back({q, (int)rb, sp});
-        xs_total += G.Np * G.dpad;
-        rows_total += G.Np;
+        int64_t S = 1;
+        if ((s = batch_split_choice(ctx, kps_all[g], &hyp[g], X[g], B[g], N[g], t, &S)) != LGP_OK) return s;
+        plan_add_problem(P, N[g], kps_all[g], X[g], B[g], Xsol[g], t, S);
     }
-    // longest items first: an item of problem g costs ~min(N_g, cols_per_split_g)
-    std::stable_sort(items.begin(), items.end(), [&](const BatchItem &a, const BatchItem &b) {
-        return std::min(gps[a.gp].N, gps[a.gp].cols_per_split) > std::min(gps[b.gp].N, gps[b.gp].cols_per_split);
-    });
     const int ng_t = n_b * t;
-    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    size_t off = 0;
-    const size_t o_gps = off; off = al(off + gps.size() * sizeof(BatchGp));
-    const size_t o_items = off; off = al(off + items.size() * sizeof(BatchItem));
-    const size_t o_vb = off; off = al(off + vblocks.size() * sizeof(BatchVecBlock));
-    const size_t o_rr = off; off = al(off + 4 * (size_t)ng_t * sizeof(double));
-    const size_t o_act = off; off = al(off + 2 * (size_t)ng_t * sizeof(int));
-    const size_t o_gpd = off; off = al(off + (size_t)n_b * sizeof(int));
-    const size_t o_misc = off; off = al(off + 256);
-    if ((s = ensure(ctx, ctx->batch_meta, off)) != LGP_OK) return s;
-    if ((s = ensure(ctx, ctx->xs, (size_t)xs_total * sizeof(float))) != LGP_OK) return s;
-    if ((s = ensure(ctx, ctx->cg_vec, (size_t)4 * rows_total * t * sizeof(float))) != LGP_OK) return s;
-    if ((s = ensure(ctx, ctx->cg_partial, vblocks.size() * (size_t)t * sizeof(double))) != LGP_OK) return s;
-    if ((s = ensure(ctx, ctx->batch_part, (size_t)std::max<int64_t>(part_total, 1) * sizeof(float))) != LGP_OK)
-        return s;
-    if ((s = ensure(ctx, ctx->flags, 64)) != LGP_OK) return s;
-    unsigned char *meta = (unsigned char *)ctx->batch_meta.p;
     BatchArgs A;
-    A.gps = (const BatchGp *)(meta + o_gps);
-    A.items = (const BatchItem *)(meta + o_items);
-    A.vblocks = (const BatchVecBlock *)(meta + o_vb);
-    A.n_gp = n_b;
-    A.n_items = (int)items.size();
-    A.n_vblocks = (int)vblocks.size();
-    A.t = t;
-    A.tt = 1;
-    while (A.tt < t) A.tt *= 2;
-    A.Xs = (const float *)ctx->xs.p;
-    float *v = (float *)ctx->cg_vec.p;
-    A.x = v;
-    A.r = v + rows_total * t;
-    A.p = v + 2 * rows_total * t;
-    A.kp = v + 3 * rows_total * t;
-    A.part = (float *)ctx->batch_part.p;
-    A.partial = (double *)ctx->cg_partial.p;
-    double *dd = (double *)(meta + o_rr);
-    A.rr = dd;
-    A.bnorm2 = dd + ng_t;
-    A.alpha = dd + 2 * ng_t;
-    A.beta = dd + 3 * ng_t;
-    int *ii = (int *)(meta + o_act);
-    A.active = ii;
-    A.iters = ii + ng_t;
-    A.gp_done = (int *)(meta + o_gpd);
-    A.done = (int *)(meta + o_misc);
-    A.item_counter = (int *)(meta + o_misc + 4);
-    A.st = (BatchState *)(meta + o_misc + 64);
-
-    LGP_CUDA(cudaMemcpyAsync(meta + o_gps, gps.data(), gps.size() * sizeof(BatchGp), cudaMemcpyHostToDevice, st));
-    LGP_CUDA(cudaMemcpyAsync(meta + o_items, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice,
-                             st));
-    LGP_CUDA(cudaMemcpyAsync(meta + o_vb, vblocks.data(), vblocks.size() * sizeof(BatchVecBlock),
-                             cudaMemcpyHostToDevice, st));
-    for (int q = 0; q < n_b; ++q)
-        launch_prep_x(X[bids[q]], gps[q].N, kps[q].D, kps[q].dpad, kps[q].scale, (float *)ctx->xs.p + gps[q].xs_off,
-                      gps[q].Np, (int *)ctx->flags.p, st);
+    if ((s = upload_batch_plan(ctx, P, t, st, &A)) != LGP_OK) return s;
     LGP_CUDA(launch_batch_init(A, opt->tol, opt->max_iter, st));
 
     // one graph: a conditional WHILE node whose body is a chunk of iterations plus the condition kernel,

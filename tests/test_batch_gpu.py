@@ -134,3 +134,40 @@ def test_batch_routes_reach_the_same_backward_error(lgp):
         assert all(r in (lgp.LGP_BATCH_PERSISTENT, lgp.LGP_BATCH_TENSOR) for r in routes)
     assert ctx.batch_route_choice(100, 2, wl.RBF, 8) == lgp.LGP_BATCH_UNTUNED
     ctx.close()
+
+
+def test_batch_split_counts_are_timed_and_both_choices_solve(lgp, monkeypatch):
+    """The persistent launch's column-split count is chosen per problem shape by timing: after a batched
+    solve every persistent-route problem has a count among the tuner's candidates (the fixed rule's count
+    r and r/4, r/2, 2r, 4r, clamped to [1, 64-column tiles]); with LGP_AUTOTUNE=0 it is the rule's. Both
+    solves meet the Cholesky gate of test_batch_small_against_cholesky."""
+    probs = wl.cfg5_batch(n_gp=8, t=8, seed=31, n_lo=400, n_hi=3000)
+    Bs = [_rhs(p, 8, g) for g, p in enumerate(probs)]
+    refs = []
+    for p, B in zip(probs, Bs):
+        Ky = go.noisy_kernel_matrix(p.X, go.hyper_of(p))
+        ev = np.linalg.eigvalsh(Ky)
+        refs.append((go.cholesky_solve(Ky, B.astype(np.float64)), max(1e-4, 2e-8 * ev[-1] / ev[0])))
+    for tuned in (True, False):
+        if not tuned:
+            monkeypatch.setenv("LGP_AUTOTUNE", "0")
+        ctx = lgp.Context(0)
+        sols, iters, rel, s = lgp.lgp_batch_cg_solve([_dev(p.X) for p in probs], probs, [_dev(B) for B in Bs],
+                                                     tol=1e-6, max_iter=3000, ctx=ctx)
+        assert s == lgp.LGP_OK and (rel <= 1e-6).all()
+        for x, (ref, gate) in zip(sols, refs):
+            err = np.linalg.norm(x.cpu().numpy() - ref, axis=0) / np.linalg.norm(ref, axis=0)
+            assert err.max() <= gate
+        chosen = []
+        for p in probs:
+            if ctx.batch_route_choice(p.N, p.D, p.kind, 8) != lgp.LGP_BATCH_PERSISTENT:
+                continue
+            S, r = ctx.batch_split_choice(p.N, p.D, p.kind, 8), ctx.batch_split_rule(p.N)
+            tiles = (p.N + 63) // 64
+            cands = {max(1, min(c, tiles)) for c in (r // 4, r // 2, r, 2 * r, 4 * r)}
+            chosen.append((p.N, S, r))
+            assert (S in cands) if tuned else (S == r), (p.N, S, r)
+        print(f"{'timed' if tuned else 'rule'}: [N, split, rule] {sorted(chosen)}")
+        assert chosen  # the persistent route is exercised
+        assert ctx.batch_split_choice(100, 2, wl.RBF, 8) == 0
+        ctx.close()
