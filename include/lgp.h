@@ -353,6 +353,18 @@ int32_t lgp_batch_split_rule(const lgp_ctx *ctx, int64_t N);
 lgp_status lgp_measure_pipe_peak(int32_t which, double *ops_per_s, lgp_stream stream);
 
 /*
+ * Measurement support (no counterpart in the paper): the duration of the product kernel alone.
+ * With timing on, every K_y V product that is not being captured into a CUDA graph records two
+ * CUDA events on the stream it launches on. They sit immediately before and after the product
+ * kernel's launch(es), after the per-call V split and the operand kernels. lgp_last_kernel_ms
+ * synchronises on the second event of the last such product and returns the time between the
+ * two, in milliseconds. It returns LGP_ERR_INVALID_ARG if no product was timed since timing was
+ * switched on. Switching timing on creates the two events once per context.
+ */
+lgp_status lgp_set_kernel_timing(lgp_ctx *ctx, int32_t on);
+lgp_status lgp_last_kernel_ms(lgp_ctx *ctx, float *ms);
+
+/*
  * Allocation-free K_y V for callers that cannot allocate device memory: programs whose
  * device memory belongs to another allocator (a framework's caching pool, a fixed arena
  * sized at start-up) and must not have a library allocate behind their back; services

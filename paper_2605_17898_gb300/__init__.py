@@ -57,6 +57,7 @@ EXPORTED = [
     "lgp_rademacher_probes", "lgp_batch_cg_solve", "lgp_kernel_matvec_noalloc",
     "lgp_measure_pipe_peak", "lgp_tc_kernel_choice", "lgp_predict", "lgp_tc_distance_form",
     "lgp_kernel_matvec_noalloc_status", "lgp_batch_route_choice", "lgp_batch_split_choice", "lgp_batch_split_rule",
+    "lgp_set_kernel_timing", "lgp_last_kernel_ms",
 ]
 
 
@@ -133,6 +134,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "lgp_batch_route_choice": (c.c_int32, [vp, c.c_int64, c.c_int32, c.c_int32, c.c_int32]),
         "lgp_batch_split_choice": (c.c_int32, [vp, c.c_int64, c.c_int32, c.c_int32, c.c_int32]),
         "lgp_batch_split_rule": (c.c_int32, [vp, c.c_int64]),
+        "lgp_set_kernel_timing": (c.c_int32, [vp, c.c_int32]),
+        "lgp_last_kernel_ms": (c.c_int32, [vp, c.POINTER(c.c_float)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -235,6 +238,16 @@ class Context:
     def batch_split_choice(self, N: int, D: int, kind: int, t: int) -> int:
         """Column splits the batched solver chose for that persistent-route problem shape (0: untuned)."""
         return int(self.lib.lgp_batch_split_choice(self.h, int(N), int(D), int(kind), int(t)))
+
+    def set_kernel_timing(self, on: bool) -> None:
+        """Record CUDA events around the product kernel of every uncaptured K_y V product."""
+        self._check(self.lib.lgp_set_kernel_timing(self.h, 1 if on else 0))
+
+    def last_kernel_ms(self) -> float:
+        """Duration of the last timed product kernel (synchronises on its end event)."""
+        ms = ctypes.c_float(0.0)
+        self._check(self.lib.lgp_last_kernel_ms(self.h, ctypes.byref(ms)))
+        return float(ms.value)
 
     def batch_split_rule(self, N: int) -> int:
         """The fixed rule's column-split count for a problem of N rows alone."""

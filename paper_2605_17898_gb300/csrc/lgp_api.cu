@@ -74,6 +74,10 @@ struct lgp_ctx {
     size_t opnd_buf_bytes = 0;  // with opnd_buf: the workspace allocation the operands were written to
     int cg_dist_form = -1;      // distance form baked into the last CG graph (-1: both instances launch)
     int last_batch_tc = 0;      // problems of the last batched solve that took the tensor-core route
+    // kernel timing (lgp_set_kernel_timing): events recorded around the product kernel's launch by
+    // products outside stream capture; kev_set once a pair has been recorded
+    bool kernel_timing = false, kev_set = false;
+    cudaEvent_t kev[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -373,6 +377,13 @@ lgp_status ensure_tc_operands(lgp_ctx *ctx, const Prepared &pp, int t, int prec,
 
 // K_y V for prepared X. V has row stride ldv; out has row stride ldo.
 // dist_form: see launch_mv_tc (-1 unless the caller read the dot-form gate word of this X).
+// Whether this product records the kernel-timing events: timing switched on and st not capturing.
+bool kernel_timing_on(const lgp_ctx *ctx, cudaStream_t st) {
+    if (!ctx->kernel_timing || !ctx->kev[0] || !ctx->kev[1]) return false;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    return cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone;
+}
+
 lgp_status matvec_prepared(lgp_ctx *ctx, const Prepared &pp, const float *V, int64_t ldv, float *out, int64_t ldo,
                            int t, int prec, const int *skip, cudaStream_t st, int dist_form = -1) {
     if (is_tc(prec)) {
@@ -383,11 +394,13 @@ lgp_status matvec_prepared(lgp_ctx *ctx, const Prepared &pp, const float *V, int
         s = ensure(ctx, ctx->mv_partial, (size_t)std::max<int64_t>(pf, 1) * sizeof(float));
         if (s != LGP_OK) return s;
         if ((s = ensure_tc_operands(ctx, pp, t, prec, st)) != LGP_OK) return s;
+        const bool timed = kernel_timing_on(ctx, st);
         LGP_CUDA(launch_mv_tc(pp.kp, pp.xs, pp.N, pp.Np, V, ldv, out, ldo, t, tc_fmt(prec), ctx->vsplit.p,
                               (float *)ctx->mv_partial.p,
                               (int64_t)(ctx->mv_partial.bytes / sizeof(float)), skip, (int *)ctx->flags.p + 1,
                               ctx->wait_budget, ctx->num_sms, st, forced, tc_operands_valid(ctx, pp, t, prec),
-                              dist_form));
+                              dist_form, timed ? ctx->kev[0] : nullptr, timed ? ctx->kev[1] : nullptr));
+        if (timed) ctx->kev_set = true;
         if (forced == kTcSymmetric) {
             ctx->sym_kind = pp.kp.kind;
             ctx->sym_D = pp.kp.D;
@@ -413,7 +426,13 @@ lgp_status matvec_prepared(lgp_ctx *ctx, const Prepared &pp, const float *V, int
     m.partial_cap = (int64_t)(ctx->mv_partial.bytes / sizeof(float));
     m.skip = skip;
     m.num_sms = ctx->num_sms;
+    const bool timed = kernel_timing_on(ctx, st);
+    if (timed) cudaEventRecord(ctx->kev[0], st);
     LGP_CUDA(launch_mv_simt(m, st));
+    if (timed) {
+        cudaEventRecord(ctx->kev[1], st);
+        ctx->kev_set = true;
+    }
     return LGP_OK;
 }
 
@@ -1215,6 +1234,8 @@ void lgp_destroy(lgp_ctx *ctx) {
     cudaSetDevice(ctx->device);
     if (ctx->work) cudaStreamSynchronize(ctx->work);
     if (ctx->cg_exec) cudaGraphExecDestroy(ctx->cg_exec);
+    for (cudaEvent_t e : ctx->kev)
+        if (e) cudaEventDestroy(e);
     DevBuf *bufs[] = {&ctx->pc_l64,     &ctx->pc_l32,   &ctx->pc_d,      &ctx->pc_info,    &ctx->pc_part,
                       &ctx->pc_u,       &ctx->pc_cinv,  &ctx->pc_gram,   &ctx->pc_e,       &ctx->pc_rhs,
                       &ctx->batch_part, &ctx->pred_xs,  &ctx->pred_z,    &ctx->pred_q,     &ctx->xs,
@@ -1267,6 +1288,27 @@ int32_t lgp_batch_route_choice(const lgp_ctx *ctx, int64_t N, int32_t D, int32_t
     auto it = ctx->batch_routes.find(key);
     if (it == ctx->batch_routes.end()) return LGP_BATCH_UNTUNED;
     return it->second ? LGP_BATCH_TENSOR : LGP_BATCH_PERSISTENT;
+}
+
+lgp_status lgp_set_kernel_timing(lgp_ctx *ctx, int32_t on) {
+    if (!ctx) return LGP_ERR_INVALID_ARG;
+    LGP_CUDA(cudaSetDevice(ctx->device));
+    if (on) {
+        for (cudaEvent_t &e : ctx->kev)
+            if (!e) LGP_CUDA(cudaEventCreate(&e));
+    }
+    ctx->kernel_timing = on != 0;
+    ctx->kev_set = false;
+    return LGP_OK;
+}
+
+lgp_status lgp_last_kernel_ms(lgp_ctx *ctx, float *ms) {
+    if (!ctx || !ms) return LGP_ERR_INVALID_ARG;
+    if (!ctx->kev_set) return fail(ctx, LGP_ERR_INVALID_ARG, "no product has been timed since timing was switched on");
+    LGP_CUDA(cudaSetDevice(ctx->device));
+    LGP_CUDA(cudaEventSynchronize(ctx->kev[1]));
+    LGP_CUDA(cudaEventElapsedTime(ms, ctx->kev[0], ctx->kev[1]));
+    return LGP_OK;
 }
 
 int32_t lgp_batch_split_choice(const lgp_ctx *ctx, int64_t N, int32_t D, int32_t kind, int32_t t) {

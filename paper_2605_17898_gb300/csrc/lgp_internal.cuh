@@ -214,10 +214,13 @@ constexpr int kTcSymmetric = -1;
 // dist_form (symmetric product with the dot form allowed): -1 = not known on the host, so both distance
 // instances launch and the device gate word lets one of them work; 0 / 1 = only the difference / dot
 // instance launches (the caller read the gate word, which must then give the same answer).
+// ev_begin / ev_end (optional): recorded on st immediately before and after the product kernel's
+// launch(es), after the V split and operand kernels (the kernel timing of lgp_last_kernel_ms).
 cudaError_t launch_mv_tc(const KernelParams &kp, const float *Xs, int64_t N, int64_t Np, const float *V, int64_t ldv,
                          float *out, int64_t ldo, int t, int fmt, void *vsplit, float *partial, int64_t partial_cap,
                          const int *skip, int *err_flag, long long wait_budget, int num_sms, cudaStream_t st,
-                         int forced_splits = 0, bool operands_ready = false, int dist_form = -1);
+                         int forced_splits = 0, bool operands_ready = false, int dist_form = -1,
+                         cudaEvent_t ev_begin = nullptr, cudaEvent_t ev_end = nullptr);
 // The operands of the tensor-core products that depend on X alone, into the t-column V-split workspace:
 // the transposed prescaled X, and with dot = true the dot-form distance data of the symmetric product
 // (box, centred split operands, squared norms, the gate word).

@@ -433,7 +433,11 @@ cudaError_t launch_tc_operands(const KernelParams &kp, const float *Xs, int64_t 
 cudaError_t launch_mv_tc(const KernelParams &kp, const float *Xs, int64_t N, int64_t Np, const float *V, int64_t ldv,
                          float *out, int64_t ldo, int t, int fmt, void *vsplit, float *partial, int64_t partial_cap,
                          const int *skip, int *err_flag, long long wait_budget, int num_sms, cudaStream_t st,
-                         int forced_splits, bool operands_ready, int dist_form) {
+                         int forced_splits, bool operands_ready, int dist_form, cudaEvent_t ev_begin,
+                         cudaEvent_t ev_end) {
+    auto mark = [&](cudaEvent_t ev) {
+        if (ev) cudaEventRecord(ev, st);
+    };
     if (!(t == 16 || t == 32) || Np % 256 != 0) return cudaErrorInvalidValue;
     uint16_t *vs = (uint16_t *)vsplit;  // stacked [V_hi; V_lo], 2 * Np * t entries
     unsigned int *vmax = (unsigned int *)(vs + 2 * Np * t);
@@ -505,7 +509,12 @@ cudaError_t launch_mv_tc(const KernelParams &kp, const float *Xs, int64_t N, int
             return fmt == kFmtF16 ? tcs::dispatch_f16(kp.kind, kp.D, t, grid, mx, mv, mo, a, st)
                                   : tcs::dispatch_bf16(kp.kind, kp.D, t, grid, mx, mv, mo, a, st);
         };
-        if (!dot_form_allowed(kp.kind, kp.D)) return launch();
+        if (!dot_form_allowed(kp.kind, kp.D)) {
+            mark(ev_begin);
+            e = launch();
+            mark(ev_end);
+            return e;
+        }
         // dot form: operands (unless the caller built them for this X), then the instance of the known
         // distance form, or both instances, of which the gate word lets exactly one work
         if (!operands_ready && (e = launch_dot_operands(kp, Xs, N, Np, t, vsplit, skip, st)) != cudaSuccess)
@@ -519,13 +528,17 @@ cudaError_t launch_mv_tc(const KernelParams &kp, const float *Xs, int64_t N, int
         a.arow = arow;
         a.ua = ua;
         a.ub = ub;
+        mark(ev_begin);
         if (dist_form != 0) {
             a.dot = 1;
             if ((e = launch()) != cudaSuccess) return e;
         }
-        if (dist_form == 1) return cudaSuccess;
-        a.dot = 0;
-        return launch();
+        if (dist_form != 1) {
+            a.dot = 0;
+            if ((e = launch()) != cudaSuccess) return e;
+        }
+        mark(ev_end);
+        return cudaSuccess;
     }
     const TcGrid g = tc_grid(Np, num_sms, forced_splits);
     if (g.S > 1 && (partial == nullptr || (int64_t)g.S * Np * t > partial_cap)) return cudaErrorInvalidValue;
@@ -552,8 +565,10 @@ cudaError_t launch_mv_tc(const KernelParams &kp, const float *Xs, int64_t N, int
     a.col_scale = fmt == kFmtF16 ? col_scale : nullptr;
     a.budget = wait_budget;
     const dim3 grid((unsigned)g.rb, (unsigned)g.S, 1);
+    mark(ev_begin);
     e = fmt == kFmtF16 ? tc::dispatch_f16(kp.kind, kp.D, t, grid, mx, mv, a, st)
                        : tc::dispatch_bf16(kp.kind, kp.D, t, grid, mx, mv, a, st);
+    mark(ev_end);
     if (e != cudaSuccess || g.S == 1) return e;
     const int rblocks = (int)std::min<int64_t>((N * t + 255) / 256, 4096);
     tc_reduce_kernel<<<rblocks, 256, 0, st>>>(partial, g.S, Np, N, t, V, ldv, out, ldo, kp.noise, skip);

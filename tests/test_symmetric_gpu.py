@@ -208,3 +208,32 @@ def test_autotune_cache_file(lgp, tmp_path):
         assert choices[0] == choices[1] and choices[0] in (lgp.LGP_TC_ROW, lgp.LGP_TC_SYMMETRIC)
     finally:
         os.environ.pop("LGP_AUTOTUNE_CACHE", None)
+
+
+def test_kernel_timing_hook(lgp):
+    """lgp_set_kernel_timing / lgp_last_kernel_ms: with timing on, a product records CUDA events around its
+    kernel alone; the kernel time is positive and no longer than the whole call (which also splits V).
+    Reading it before any timed product is refused."""
+    import torch
+    p = wl.cfg3(N=20000, t=32)
+    ctx = lgp.Context(0)
+    X = torch.as_tensor(p.X, device="cuda")
+    V = torch.as_tensor(wl.rhs_block(p.N, 32, seed=3, kind="sign"), device="cuda")
+    out = torch.empty_like(V)
+    ctx.set_kernel_timing(True)
+    with pytest.raises(lgp.LGPError) as e:
+        ctx.last_kernel_ms()
+    assert e.value.status == lgp.LGP_ERR_INVALID_ARG
+    lgp.lgp_kernel_matvec(X, p, V, prec=lgp.LGP_PREC_SPLIT_F16, out=out, ctx=ctx)
+    for _ in range(3):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        lgp.lgp_kernel_matvec(X, p, V, prec=lgp.LGP_PREC_SPLIT_F16, out=out, ctx=ctx)
+        b.record()
+        torch.cuda.synchronize()
+        call_ms, kernel_ms = a.elapsed_time(b), ctx.last_kernel_ms()
+        print(f"call {call_ms:.4f} ms, kernel {kernel_ms:.4f} ms")
+        assert 0.0 < kernel_ms <= call_ms
+    ctx.set_kernel_timing(False)
+    ctx.close()
