@@ -255,14 +255,14 @@ __global__ void bpkp_kernel(BatchArgs a) {
     const BatchGp g = a.gps[vb.gp];
     const int t = a.t;
     const int c = threadIdx.x % t;
-    double s = 0.0;
+    float hi = 0.0f, lo = 0.0f;
     if (!a.gp_done[vb.gp]) {
         for (int64_t i = vb.r0 + threadIdx.x / t; i < vb.r1; i += blockDim.x / t) {
             const int64_t e = (g.vec_off + i) * t + c;
-            s += (double)a.p[e] * (double)a.kp[e];
+            acc_prod2(hi, lo, a.p[e], a.kp[e]);
         }
     }
-    seg_col_reduce(s, t, red, a.partial + (int64_t)blockIdx.x * t);
+    seg_col_reduce((double)hi + (double)lo, t, red, a.partial + (int64_t)blockIdx.x * t);
 }
 
 __global__ void balpha_kernel(BatchArgs a) {
@@ -293,7 +293,7 @@ __global__ void bxr_kernel(BatchArgs a) {
     const int t = a.t;
     const int c = threadIdx.x % t;
     const float alpha = (float)a.alpha[vb.gp * t + c];
-    double s = 0.0;
+    float hi = 0.0f, lo = 0.0f;
     for (int64_t i = vb.r0 + threadIdx.x / t; i < vb.r1; i += blockDim.x / t) {
         const int64_t e = (g.vec_off + i) * t + c;
         float rv = a.r[e];
@@ -302,9 +302,9 @@ __global__ void bxr_kernel(BatchArgs a) {
             rv = fmaf(-alpha, a.kp[e], rv);
             a.r[e] = rv;
         }
-        s += (double)rv * (double)rv;
+        acc_prod2(hi, lo, rv, rv);
     }
-    seg_col_reduce(s, t, red, a.partial + (int64_t)blockIdx.x * t);
+    seg_col_reduce((double)hi + (double)lo, t, red, a.partial + (int64_t)blockIdx.x * t);
 }
 
 __global__ void bbeta_kernel(BatchArgs a) {

@@ -55,6 +55,23 @@ __device__ __forceinline__ float sqrt_approx(float x) {
     return y;
 }
 
+// Accumulates a * b into the float pair (hi, lo) without float64 arithmetic: the product's rounding
+// error exactly by FMA (TwoProduct) and the running sum's by Knuth's TwoSum, as in the compensated
+// dot product of Ogita, Rump and Oishi ("Accurate sum and dot product", SIAM J. Sci. Comput. 2005).
+// Each operation is an explicitly rounded intrinsic, so the compiler cannot contract it into an FMA.
+// hi + lo carries the partial sum to about 2^-44 relative; the block and column reductions then run in
+// float64. (The float64 pipe of this GPU is slow enough that converting every element to double set
+// the time of these kernels.)
+__device__ __forceinline__ void acc_prod2(float &hi, float &lo, float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float pe = fmaf(a, b, -p);
+    const float s = __fadd_rn(hi, p);
+    const float bb = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(e, pe));
+}
+
 template <int KIND> struct Entry;
 
 template <> struct Entry<LGP_RBF> {

@@ -13,16 +13,24 @@ namespace {
 using tc::kBK;
 using tc::kBM;
 
-// Per-column largest |V| as float bits (non-negative floats order like their bit patterns).
-__global__ void col_absmax_kernel(const float *__restrict__ V, int64_t ldv, int64_t N, int T,
-                                  unsigned int *__restrict__ vmax, const int *skip) {
+// Per-column largest |V| as float bits (non-negative floats order like their bit patterns). Thread
+// (row r, column c) of a block of 256 (T divides 256) scans rows r, r + rows-per-grid, ...; the block
+// reduces its columns in shared memory and adds one atomicMax per column.
+__global__ void __launch_bounds__(256) col_absmax_kernel(const float *__restrict__ V, int64_t ldv, int64_t N, int T,
+                                                         unsigned int *__restrict__ vmax, const int *skip) {
     if (skip && *skip) return;
+    __shared__ unsigned int red[256];
     const int c = threadIdx.x % T;
     unsigned int m = 0;
     for (int64_t j = (int64_t)blockIdx.x * (blockDim.x / T) + threadIdx.x / T; j < N;
          j += (int64_t)gridDim.x * (blockDim.x / T))
         m = max(m, __float_as_uint(fabsf(V[j * ldv + c])));
-    atomicMax(vmax + c, m);
+    red[threadIdx.x] = m;
+    __syncthreads();
+    if ((int)threadIdx.x < T) {
+        for (int k = threadIdx.x + T; k < (int)blockDim.x; k += T) m = max(m, red[k]);
+        atomicMax(vmax + c, m);
+    }
 }
 
 // Power-of-two exponent e_c with max_c * 2^e_c < 2^15 (clamped to keep the epilogue factor normal).
@@ -36,7 +44,8 @@ __device__ __forceinline__ int col_exponent(unsigned int maxbits) {
 
 // V -> stacked [V_hi; V_lo] in the tile order the MMA reads: B row c' = c (hi) or t + c (lo);
 // element (j, c') of chunk q = j / 64 sits at q*64*2t + ((j%64)/8 * 2t/8 + c'/8) * 64 + (c'%8) * 8 + j%8;
-// rows j >= N are zero.
+// rows j >= N are zero. One thread per (8-row group, column): its 8 hi and 8 lo values are contiguous
+// in that order and go out as one 16-byte store each; the warp's loads of a row are contiguous.
 // FMT f16: V is first scaled per column by 2^e_c and col_scale[c] = s^2 2^-15 2^-e_c is written.
 // With out_init set, also out_init[j, c] = noise * V[j, c] for j < N (the symmetric product adds
 // onto it).
@@ -46,32 +55,47 @@ __global__ void split_v_kernel(const float *__restrict__ V, int64_t ldv, int64_t
                                const unsigned int *__restrict__ vmax, float *__restrict__ col_scale, float s2,
                                float *__restrict__ out_init, int64_t ldo, float noise, const int *skip) {
     if (skip && *skip) return;
-    const int64_t total = Np * T;
+    const int64_t total = (Np / 8) * T;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t j = e / T;
-        const int c = (int)(e - j * T);
-        float v = j < N ? V[j * ldv + c] : 0.0f;
-        if (out_init && j < N) out_init[j * ldo + c] = noise * v;
-        uint16_t h, l;
-        if (FMT == kFmtBF16) {
-            const __nv_bfloat16 hb = __float2bfloat16_rn(v);
-            const __nv_bfloat16 lb = __float2bfloat16_rn(v - __bfloat162float(hb));
-            h = *reinterpret_cast<const uint16_t *>(&hb);
-            l = *reinterpret_cast<const uint16_t *>(&lb);
-        } else {
-            const int ec = col_exponent(vmax[c]);
-            v = ldexpf(v, ec);
-            const __half hh = __float2half_rn(v);
-            const __half lh = __float2half_rn(v - __half2float(hh));
-            h = *reinterpret_cast<const uint16_t *>(&hh);
-            l = *reinterpret_cast<const uint16_t *>(&lh);
-            if (j == 0) col_scale[c] = ldexpf(s2, -15 - ec);
+        const int64_t g = e / T;  // rows 8g .. 8g + 7
+        const int c = (int)(e - g * T);
+        int ec = 0;
+        if (FMT == kFmtF16) {
+            ec = col_exponent(vmax[c]);
+            if (g == 0) col_scale[c] = ldexpf(s2, -15 - ec);
         }
-        const int64_t q = j / kBK;
-        const int jj = (int)(j - q * kBK);
-        const int64_t chunk = q * kBK * 2 * T + (int64_t)(jj >> 3) * (2 * T / 8) * 64 + (c & 7) * 8 + (jj & 7);
-        vs[chunk + (int64_t)(c >> 3) * 64] = h;
-        vs[chunk + (int64_t)((T + c) >> 3) * 64] = l;
+        uint32_t hw[4], lw[4];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int64_t j = 8 * g + k;
+            float v = j < N ? V[j * ldv + c] : 0.0f;
+            if (out_init && j < N) out_init[j * ldo + c] = noise * v;
+            uint16_t h, l;
+            if (FMT == kFmtBF16) {
+                const __nv_bfloat16 hb = __float2bfloat16_rn(v);
+                const __nv_bfloat16 lb = __float2bfloat16_rn(v - __bfloat162float(hb));
+                h = *reinterpret_cast<const uint16_t *>(&hb);
+                l = *reinterpret_cast<const uint16_t *>(&lb);
+            } else {
+                v = ldexpf(v, ec);
+                const __half hh = __float2half_rn(v);
+                const __half lh = __float2half_rn(v - __half2float(hh));
+                h = *reinterpret_cast<const uint16_t *>(&hh);
+                l = *reinterpret_cast<const uint16_t *>(&lh);
+            }
+            if (k & 1) {
+                hw[k >> 1] |= (uint32_t)h << 16;
+                lw[k >> 1] |= (uint32_t)l << 16;
+            } else {
+                hw[k >> 1] = h;
+                lw[k >> 1] = l;
+            }
+        }
+        const int64_t q = (8 * g) / kBK;
+        const int jj = (int)(8 * g - q * kBK);  // multiple of 8
+        const int64_t chunk = q * kBK * 2 * T + (int64_t)(jj >> 3) * (2 * T / 8) * 64 + (c & 7) * 8;
+        *reinterpret_cast<uint4 *>(vs + chunk + (int64_t)(c >> 3) * 64) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        *reinterpret_cast<uint4 *>(vs + chunk + (int64_t)((T + c) >> 3) * 64) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
     }
 }
 
@@ -443,14 +467,14 @@ cudaError_t launch_mv_tc(const KernelParams &kp, const float *Xs, int64_t N, int
     unsigned int *vmax = (unsigned int *)(vs + 2 * Np * t);
     float *col_scale = (float *)(vmax + 64);
     float *XsT = col_scale + 64;
-    const int blocks = (int)std::min<int64_t>((Np * t + 255) / 256, 8192);
+    const int blocks = (int)std::min<int64_t>((Np / 8 * t + 255) / 256, 8192);  // split_v: (8-row group, column)
     const bool symmetric = forced_splits == kTcSymmetric;
     float *out_init = symmetric ? out : nullptr;
     cudaError_t e;
     if (fmt == kFmtF16) {
         e = cudaMemsetAsync(vmax, 0, 64 * sizeof(unsigned int), st);
         if (e != cudaSuccess) return e;
-        const int mb = (int)std::min<int64_t>((N * t + 255) / 256, 1024);
+        const int mb = (int)std::max<int64_t>(1, std::min<int64_t>((N * t + 255) / 256, 4 * num_sms));
         col_absmax_kernel<<<mb, (256 / t) * t, 0, st>>>(V, ldv, N, t, vmax, skip);
         if (t == 16)
             split_v_kernel<16, kFmtF16><<<blocks, 256, 0, st>>>(V, ldv, N, Np, vs, vmax, col_scale, kp.s2, out_init,

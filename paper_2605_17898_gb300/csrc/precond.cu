@@ -189,7 +189,7 @@ __global__ void pc_apply_kernel(const float *__restrict__ L, int64_t Np, int k, 
     float u[kMaxRank];
 #pragma unroll
     for (int q = 0; q < kMaxRank; ++q) u[q] = q < k ? (float)U[q * t + c] : 0.0f;
-    double s = 0.0;
+    float s_hi = 0.0f, s_lo = 0.0f;
     for (int64_t i = r0 + threadIdx.x / t; i < r1; i += blockDim.x / t) {
         const float rv = R[i * ldr + c];
         float acc = rv;
@@ -199,11 +199,11 @@ __global__ void pc_apply_kernel(const float *__restrict__ L, int64_t Np, int k, 
         const float zv = (float)((double)acc * inv_noise);
         Z[i * ldz + c] = zv;
         if (Pc) Pc[i * ldz + c] = zv;
-        s += (double)rv * (double)zv;
+        acc_prod2(s_hi, s_lo, rv, zv);
     }
     if (!rz_partial) return;
     // per-column block reduction (threads tid, tid + t, ... own column tid % t)
-    red[threadIdx.x] = s;
+    red[threadIdx.x] = (double)s_hi + (double)s_lo;
     __syncthreads();
     const int nr = blockDim.x / t;
     int w = 1;

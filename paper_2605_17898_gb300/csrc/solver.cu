@@ -146,10 +146,9 @@ __global__ void cg_pkp_kernel(const float *__restrict__ p, const float *__restri
     int64_t r0, r1;
     block_rows(N, &r0, &r1);
     const int c = threadIdx.x % t;
-    double s = 0.0;
-    for (int64_t i = r0 + threadIdx.x / t; i < r1; i += blockDim.x / t)
-        s += (double)p[i * t + c] * (double)Kp[i * t + c];
-    block_col_reduce(s, t, red, partial + (int64_t)blockIdx.x * t);
+    float hi = 0.0f, lo = 0.0f;
+    for (int64_t i = r0 + threadIdx.x / t; i < r1; i += blockDim.x / t) acc_prod2(hi, lo, p[i * t + c], Kp[i * t + c]);
+    block_col_reduce((double)hi + (double)lo, t, red, partial + (int64_t)blockIdx.x * t);
 }
 
 __global__ void cg_alpha_kernel(CgState *st, const double *__restrict__ partial, int G, double *hist_alpha) {
@@ -191,7 +190,7 @@ __global__ void cg_xr_kernel(float *__restrict__ x, float *__restrict__ r, const
     block_rows(N, &r0, &r1);
     const int c = threadIdx.x % t;
     const float alpha = (float)st->alpha[c];
-    double s = 0.0;
+    float hi = 0.0f, lo = 0.0f;
     for (int64_t i = r0 + threadIdx.x / t; i < r1; i += blockDim.x / t) {
         const int64_t e = i * t + c;
         float rv = r[e];
@@ -200,9 +199,9 @@ __global__ void cg_xr_kernel(float *__restrict__ x, float *__restrict__ r, const
             rv = fmaf(-alpha, Kp[e], rv);
             r[e] = rv;
         }
-        s += (double)rv * (double)rv;
+        acc_prod2(hi, lo, rv, rv);
     }
-    block_col_reduce(s, t, red, partial + (int64_t)blockIdx.x * t);
+    block_col_reduce((double)hi + (double)lo, t, red, partial + (int64_t)blockIdx.x * t);
 }
 
 __global__ void cg_beta_kernel(CgState *st, const double *__restrict__ partial, int G, double *hist_beta,
