@@ -171,3 +171,31 @@ def test_batch_split_counts_are_timed_and_both_choices_solve(lgp, monkeypatch):
         assert chosen  # the persistent route is exercised
         assert ctx.batch_split_choice(100, 2, wl.RBF, 8) == 0
         ctx.close()
+
+
+def test_batch_choices_persist_in_the_autotune_cache(lgp, monkeypatch, tmp_path):
+    """LGP_AUTOTUNE_CACHE holds the batched solver's choices too: after one batched solve the file has a
+    route line for every shape of at least 2048 rows and a split line for every persistent-route shape, and
+    a fresh context reads the same route and split choices from it."""
+    path = tmp_path / "tune.txt"
+    monkeypatch.setenv("LGP_AUTOTUNE_CACHE", str(path))
+    probs = wl.cfg5_batch(n_gp=5, t=8, seed=41, n_lo=600, n_hi=5000)
+    Bs = [_rhs(p, 8, g) for g, p in enumerate(probs)]
+    choices = []
+    for _ in range(2):
+        ctx = lgp.Context(0)
+        sols, iters, rel, s = lgp.lgp_batch_cg_solve([_dev(p.X) for p in probs], probs, [_dev(B) for B in Bs],
+                                                     tol=1e-6, max_iter=3000, ctx=ctx)
+        assert s == lgp.LGP_OK and (rel <= 1e-6).all()
+        choices.append([(ctx.batch_route_choice(p.N, p.D, p.kind, 8), ctx.batch_split_choice(p.N, p.D, p.kind, 8))
+                        for p in probs])
+        ctx.close()
+    assert choices[0] == choices[1]
+    lines = path.read_text().splitlines()
+    def shape(p):  # the cache key's shape: rows padded to 256, D, kernel
+        return ((p.N + 255) // 256 * 256, p.D, p.kind)
+
+    n_route = len({shape(p) for p in probs if p.N >= 2048})
+    n_split = len({shape(p) for p, (r, _) in zip(probs, choices[0]) if r == lgp.LGP_BATCH_PERSISTENT})
+    assert sum(1 for l in lines if "|route " in l) >= n_route
+    assert sum(1 for l in lines if "|split " in l) >= n_split >= 1
