@@ -198,6 +198,20 @@ int resolve_prec(int t, int prec) {
     return LGP_ERR_INVALID_ARG;
 }
 
+// resolve_prec for the entry points that zero-pad the caller's columns (lgp_kernel_matvec, lgp_cg_solve): an
+// explicit split precision with t not in {16, 32} runs with *tp = 16 (t < 16) or 32 (16 < t < 32) columns, the
+// extra ones zero. AUTO is unchanged (split only at t in {16, 32}). *tp = t otherwise.
+int resolve_prec_padded(int t, int prec, int *tp) {
+    *tp = t;
+    if ((prec == LGP_PREC_SPLIT_BF16 || prec == LGP_PREC_SPLIT_F16) && t != 16 && t != 32) {
+        const int padded = t < 16 ? 16 : (t < 32 ? 32 : 0);
+        if (padded == 0 || !tc_supported(padded)) return LGP_ERR_UNSUPPORTED;
+        *tp = padded;
+        return prec;
+    }
+    return resolve_prec(t, prec);
+}
+
 bool is_tc(int prec) { return prec == LGP_PREC_SPLIT_BF16 || prec == LGP_PREC_SPLIT_F16; }
 int tc_fmt(int prec) { return prec == LGP_PREC_SPLIT_F16 ? 1 : 0; }
 
@@ -1267,7 +1281,8 @@ int64_t lgp_workspace_bytes(const lgp_ctx *ctx) { return ctx ? ctx->ws_bytes : 0
 int32_t lgp_matvec_precision(const lgp_ctx *ctx, int32_t t, int32_t prec) {
     (void)ctx;
     if (t < 1 || t > kMaxT) return LGP_ERR_UNSUPPORTED;
-    return resolve_prec(t, prec);
+    int tp = t;
+    return resolve_prec_padded(t, prec, &tp);
 }
 
 int32_t lgp_tc_kernel_choice(const lgp_ctx *ctx, int64_t N, int32_t D, int32_t kind, int32_t t, int32_t prec) {
@@ -1374,17 +1389,38 @@ lgp_status lgp_kernel_matvec(lgp_ctx *ctx, const lgp_hyper *hyp, const float *X,
     if ((s = check_dev_ptr(ctx, X, "X")) || (s = check_dev_ptr(ctx, V, "V")) || (s = check_dev_ptr(ctx, out, "out")))
         return s;
     if (out == V || (const float *)out == X) return fail(ctx, LGP_ERR_INVALID_ARG, "out aliases an input");
-    const int p = resolve_prec(t, prec);
+    int tp = t;
+    const int p = resolve_prec_padded(t, prec, &tp);
     if (p < 0) return fail(ctx, (lgp_status)p, "precision %d unsupported for t=%d", prec, t);
     cudaStream_t st = (cudaStream_t)stream;
     Prepared pp;
     if ((s = prepare_x(ctx, hyp, X, N, st, &pp)) != LGP_OK) return s;
+    // an explicit split precision at other t: the product runs on tp zero-padded columns
+    const float *Vu = V;
+    float *Ou = out;
+    if (tp != t) {
+        if ((s = ensure(ctx, ctx->rhs, (size_t)pp.Np * tp * sizeof(float))) != LGP_OK ||
+            (s = ensure(ctx, ctx->sr_x, (size_t)pp.Np * tp * sizeof(float))) != LGP_OK)
+            return s;
+        float *vpad = (float *)ctx->rhs.p;
+        LGP_CUDA(cudaMemsetAsync(vpad, 0, (size_t)pp.Np * tp * sizeof(float), st));
+        launch_copy_cols(V, t, vpad, tp, N, t, 0, st);
+        LGP_CUDA(cudaGetLastError());
+        Vu = vpad;
+        Ou = (float *)ctx->sr_x.p;
+    }
     if (is_tc(p)) {
         cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
         LGP_CUDA(cudaStreamIsCapturing(st, &cap));
-        if (cap == cudaStreamCaptureStatusNone && (s = autotune_tc(ctx, pp, V, t, out, t, t, p, st)) != LGP_OK) return s;
+        if (cap == cudaStreamCaptureStatusNone && (s = autotune_tc(ctx, pp, Vu, tp, Ou, tp, tp, p, st)) != LGP_OK)
+            return s;
     }
-    return matvec_prepared(ctx, pp, V, t, out, t, t, p, nullptr, st);
+    if ((s = matvec_prepared(ctx, pp, Vu, tp, Ou, tp, tp, p, nullptr, st)) != LGP_OK) return s;
+    if (tp != t) {
+        launch_copy_cols(Ou, tp, out, t, N, t, 0, st);
+        LGP_CUDA(cudaGetLastError());
+    }
+    return LGP_OK;
 }
 
 lgp_status lgp_kernel_matvec_grad(lgp_ctx *ctx, const lgp_hyper *hyp, const float *X, const float *W, float *dK_W,
@@ -1432,20 +1468,45 @@ lgp_status lgp_cg_solve(lgp_ctx *ctx, const lgp_hyper *hyp, const float *X, cons
     if ((s = check_dev_ptr(ctx, X, "X")) || (s = check_dev_ptr(ctx, B, "B")) || (s = check_dev_ptr(ctx, Xsol, "Xsol")))
         return s;
     if ((const float *)Xsol == B) return fail(ctx, LGP_ERR_INVALID_ARG, "Xsol aliases B");
-    const int prec = resolve_prec(t, opt->prec);
+    int tp = t;
+    const int prec = resolve_prec_padded(t, opt->prec, &tp);
     if (prec < 0) return fail(ctx, (lgp_status)prec, "precision %d unsupported for t=%d", opt->prec, t);
     cudaStream_t user = (cudaStream_t)stream;
     if ((s = enter(ctx, user)) != LGP_OK) return s;
-    LGP_CUDA(cudaMemsetAsync(ctx->flags.p, 0, 4 * sizeof(int), ctx->work));
+    cudaStream_t st = ctx->work;
+    LGP_CUDA(cudaMemsetAsync(ctx->flags.p, 0, 4 * sizeof(int), st));
     Prepared pp;
-    if ((s = prepare_x(ctx, hyp, X, N, ctx->work, &pp)) != LGP_OK) return s;
-    Precond pc;
-    if (opt->precond_rank > 0 && (s = build_precond(ctx, hyp, X, pp, opt->precond_rank, t, &pc)) != LGP_OK) return s;
-    CgBuffers b;
+    if ((s = prepare_x(ctx, hyp, X, N, st, &pp)) != LGP_OK) return s;
+    // an explicit split precision at other t: the solve runs on tp columns, the extra ones zero (a zero
+    // column takes no iteration), and the warm start, if any, is padded the same way
+    const float *Bu = B;
     const float *x0 = (opt->flags & LGP_OPT_WARM_START) ? Xsol : nullptr;
-    if ((s = run_cg(ctx, pp, B, t, t, opt, 0, prec, &b, nullptr, opt->precond_rank > 0 ? &pc : nullptr, x0)) != LGP_OK)
+    if (tp != t) {
+        if ((s = ensure(ctx, ctx->rhs, (size_t)pp.Np * tp * sizeof(float))) != LGP_OK ||
+            (s = ensure(ctx, ctx->sr_x, (size_t)pp.Np * tp * sizeof(float))) != LGP_OK)
+            return s;
+        float *bpad = (float *)ctx->rhs.p;
+        LGP_CUDA(cudaMemsetAsync(bpad, 0, (size_t)pp.Np * tp * sizeof(float), st));
+        launch_copy_cols(B, t, bpad, tp, N, t, 0, st);
+        if (x0) {
+            float *x0pad = (float *)ctx->sr_x.p;
+            LGP_CUDA(cudaMemsetAsync(x0pad, 0, (size_t)pp.Np * tp * sizeof(float), st));
+            launch_copy_cols(Xsol, t, x0pad, tp, N, t, 0, st);
+            x0 = x0pad;
+        }
+        LGP_CUDA(cudaGetLastError());
+        Bu = bpad;
+    }
+    Precond pc;
+    if (opt->precond_rank > 0 && (s = build_precond(ctx, hyp, X, pp, opt->precond_rank, tp, &pc)) != LGP_OK) return s;
+    CgBuffers b;
+    if ((s = run_cg(ctx, pp, Bu, tp, tp, opt, 0, prec, &b, nullptr, opt->precond_rank > 0 ? &pc : nullptr, x0)) !=
+        LGP_OK)
         return s;
-    launch_cg_copy_out(b, N, t, Xsol, t, ctx->work);
+    if (tp != t)
+        launch_copy_cols(b.x, tp, Xsol, t, N, t, 0, st);
+    else
+        launch_cg_copy_out(b, N, t, Xsol, t, st);
     LGP_CUDA(cudaGetLastError());
     LGP_CUDA(cudaMemcpyAsync(ctx->h_flags, ctx->flags.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, ctx->work));
     if ((s = leave_sync(ctx, user)) != LGP_OK) return s;

@@ -168,6 +168,23 @@ def test_split_matvec(lgp, kind, t, N, fmt):
     assert err <= (TOL if fmt == "f16" else BF16_TOL)
 
 
+@pytest.mark.parametrize("fmt", ["f16", "bf16"])
+@pytest.mark.parametrize("t", [1, 5, 8, 20, 31])
+@pytest.mark.parametrize("N", [129, 4099])
+def test_split_matvec_zero_padded_columns(lgp, t, N, fmt):
+    """An explicit split precision at t not in {16, 32}: the product runs on the columns zero-padded to 16 or
+    32 and returns the caller's t columns, held to the same gates as the unpadded split products."""
+    p = wl.random_problem(N, 3, wl.MATERN52, seed=N + 3 * t)
+    V = wl.rhs_block(N, t, seed=N + t)
+    prec = lgp.LGP_PREC_SPLIT_F16 if fmt == "f16" else lgp.LGP_PREC_SPLIT_BF16
+    got = _run(lgp, p, V, prec=prec)
+    assert got.shape == (N, t)
+    ref = go.matvec(p.X, V, go.hyper_of(p))
+    err = _colerr(got, ref).max()
+    print(f"padded split-{fmt} t={t} N={N}: max column rel err {err:.2e}")
+    assert err <= (TOL if fmt == "f16" else BF16_TOL)
+
+
 @pytest.mark.parametrize("D", [1, 2, 3, 4, 5, 6, 7, 8])
 def test_split_f16_every_dimension(lgp, D):
     p = wl.random_problem(2000, D, wl.MATERN52 if D % 2 else wl.RBF, seed=40 + D)
@@ -197,7 +214,10 @@ def test_split_f16_selected_by_auto(lgp):
     assert ctx.matvec_precision(32) == lgp.LGP_PREC_SPLIT_F16
     assert ctx.matvec_precision(16) == lgp.LGP_PREC_SPLIT_F16
     assert ctx.matvec_precision(8) == lgp.LGP_PREC_FP32
-    assert ctx.matvec_precision(8, lgp.LGP_PREC_SPLIT_BF16) == lgp.LGP_ERR_UNSUPPORTED
+    # an explicit split precision at other t runs on zero-padded columns; above 32 columns it has none
+    assert ctx.matvec_precision(8, lgp.LGP_PREC_SPLIT_BF16) == lgp.LGP_PREC_SPLIT_BF16
+    assert ctx.matvec_precision(1, lgp.LGP_PREC_SPLIT_F16) == lgp.LGP_PREC_SPLIT_F16
+    assert ctx.matvec_precision(33, lgp.LGP_PREC_SPLIT_F16) == lgp.LGP_ERR_UNSUPPORTED
     assert ctx.matvec_precision(32, lgp.LGP_PREC_SPLIT_BF16) == lgp.LGP_PREC_SPLIT_BF16
 
 

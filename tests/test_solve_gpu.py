@@ -40,6 +40,39 @@ def test_cfg1_cg_solve(lgp):
     assert err.max() <= 1e-4
 
 
+@pytest.mark.parametrize("t", [1, 3])
+def test_cg_solve_split_precision_zero_padded(lgp, t):
+    """lgp_cg_solve with an explicit split precision at t < 16: the solve runs on 16 zero-padded columns (the
+    zero ones take no iteration) and returns t columns. Against the Cholesky solve with the gates of the
+    full-size split solves: forward error <= max(1e-4, 2e-8 kappa) and componentwise backward error <= 1e-5
+    (the split product's own error, ~1e-6, is amplified by kappa in the forward error). A warm start from
+    that solution (padded the same way) needs fewer iterations than the solve from zero."""
+    p = wl.cfg2(N=3000, kind=wl.MATERN52)
+    B = wl.rhs_block(p.N, t, seed=7)
+    B[:, 0] = p.y
+    Ky = go.noisy_kernel_matrix(p.X, go.hyper_of(p))
+    ev = np.linalg.eigvalsh(Ky)
+    ref = go.cholesky_solve(Ky, B.astype(np.float64))
+    x, iters, rel, status = lgp.lgp_cg_solve(_dev(p.X), p, _dev(B), tol=1e-6, max_iter=3000,
+                                             prec=lgp.LGP_PREC_SPLIT_F16)
+    assert status == lgp.LGP_OK and x.shape == (p.N, t) and len(iters) == t
+    assert (rel <= 1e-6).all()
+    xs = x.cpu().numpy().astype(np.float64)
+    err = _solve_err(xs, ref)
+    berr = np.abs(B - Ky @ xs) / (Ky @ np.abs(xs) + np.abs(B))
+    gate = max(1e-4, 2e-8 * ev[-1] / ev[0])
+    print(f"padded split t={t}: iterations {list(iters)}, forward error {err.max():.2e} (gate {gate:.2e}), "
+          f"backward error {berr.max():.2e}")
+    assert err.max() <= gate
+    assert berr.max() <= 1e-5
+    x2, iters2, rel2, status2 = lgp.lgp_cg_solve(_dev(p.X), p, _dev(B), tol=1e-6, max_iter=3000,
+                                                 prec=lgp.LGP_PREC_SPLIT_F16, x0=x)
+    assert status2 == lgp.LGP_OK and (rel2 <= 1e-6).all()
+    # the restart recomputes the true residual with the split product, above the recursive one that met tol,
+    # so it iterates again, but from the padded warm start: fewer iterations than from zero
+    assert int(np.max(iters2)) < int(np.min(iters))
+
+
 @pytest.mark.parametrize("kind", [wl.RBF, wl.MATERN52])
 def test_cfg2_cg_multi_rhs(lgp, kind):
     p = wl.cfg2(N=3000, kind=kind)
