@@ -39,7 +39,7 @@ METRIC = "matvec pair·RHS evals/s and LML+grad time, N=100k t=32, vs plain FP32
 # `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum` capture (profiles/), valid only for the
 # kernel source it was taken on: the bench reports null once a header of that kernel changes.
 TRAFFIC = {"mv_tc_kernel": {"bytes": None, "source_sha256_16": None},
-           "mv_tcs_kernel": {"bytes": 38.475776e6, "source_sha256_16": "112abec8c7746381"}}
+           "mv_tcs_kernel": {"bytes": 38.475776e6, "source_sha256_16": "5d13e9ef307b2fb0"}}
 KERNEL_SOURCES = {"mv_tc_kernel": ["mv_tc.cuh"], "mv_tcs_kernel": ["mv_tcs.cuh", "mv_tc.cuh"]}
 UNIT = "pair*RHS/s"
 SM_COUNT_NOMINAL = 152
@@ -72,9 +72,10 @@ def parse():
                          "memory: device memory of the LML+grad call for N in 1e3..5e5")
     ap.add_argument("--precond-rank", type=int, default=0,
                     help="pivoted-Cholesky preconditioner rank of the CG solves (0: the paper's plain CG)")
-    ap.add_argument("--workload", choices=["cfg3", "cfg4"], default="cfg3",
+    ap.add_argument("--workload", choices=["cfg3", "cfg4", "cfg5-large"], default="cfg3",
                     help="--mode lml problem: cfg3 (N=100000, D=8, Matern-5/2, t=32; the default) or cfg4 "
-                         "(N=50000, D=8, RBF, t=16, 10 hyperparameters; the line adds the adjoint pass's own time)")
+                         "(N=50000, D=8, RBF, t=16, 10 hyperparameters; the line adds the adjoint pass's own time); "
+                         "cfg5-large (--mode matvec only): one RBF product at N=500000, D=2, t=32 on a N(0,1) block")
     ap.add_argument("--ref-tol", type=float, default=1e-6,
                     help="tolerance of the tight solve the timed step's LML and gradient are compared with")
     ap.add_argument("--no-accuracy", action="store_true", help="skip the accuracy record of the timed step")
@@ -253,14 +254,14 @@ def binding_pipe(entries: float, pairs: float, ops_pair: float, mufu_pair: dict,
 
     FP32 pipe: entries x FP32 ops over n_sm x 128 lanes x 2070 MHz. MUFU: entries x (ex2 + 2 sqrt)
     ex2 slots over n_sm x 32 ex2/cycle x 2070 MHz (sqrt runs at half the ex2 rate). Tensor: N^2 6t
-    contraction flops (+ 2 kg per entry for the dot form's Gram tile, kg = 16 or 32) over the bf16
+    contraction flops (+ 2 kg per entry for the dot form's Gram tile, kg = 32) over the bf16
     burst peak. Returns achieved and peak in the binding pipe's unit, frac = achieved / peak, and the
     three time fractions.
     """
     fp32_peak = n_sm * FP32_LANES_PER_SM * MAX_SM_MHZ_NOMINAL * 1e6
     ex2_peak = n_sm * MUFU_EX2_PER_SM * MAX_SM_MHZ_NOMINAL * 1e6
     mufu_work = entries * (mufu_pair["ex2"] + 2.0 * mufu_pair["sqrt"])
-    kg = 16 if D <= 4 else 32
+    kg = 32  # the Gram operand rows: 3 Dp split coordinates + 6 norm and unit columns, padded to 32
     tensor_flops = (pairs * 6 * t + (entries * 2 * kg if dot else 0.0)) if split else 0.0
     bf16_peak = bf16_tflops * 1e12
     times = {"fp32": entries * ops_pair / fp32_peak, "mufu": mufu_work / ex2_peak, "tensor": tensor_flops / bf16_peak}
@@ -344,12 +345,19 @@ def main():
     prec = {"auto": lgp.LGP_PREC_AUTO, "fp32": lgp.LGP_PREC_FP32, "split_bf16": lgp.LGP_PREC_SPLIT_BF16,
             "split_f16": lgp.LGP_PREC_SPLIT_F16}[args.prec]
 
+    V_large = None
     if args.workload == "cfg4":
         if args.N == 100000:
             args.N = 50000
         if args.t == 32:
             args.t = 16
         p = wl.cfg4(N=args.N, t=args.t)
+    elif args.workload == "cfg5-large":
+        if args.mode != "matvec":
+            raise SystemExit("--workload cfg5-large is a single product: use it with --mode matvec")
+        if args.N == 100000:
+            args.N = 500000
+        p, V_large = wl.cfg5_large(N=args.N, t=args.t)
     else:
         p = wl.cfg3(N=args.N, t=args.t)
     kernel_name = {wl.RBF: "rbf", wl.MATERN52: "matern52"}.get(p.kind, str(p.kind))
@@ -358,7 +366,7 @@ def main():
         bench_memory(lgp, args, dev, prec, rank)
         return
     if args.mode == "matvec":
-        bench_matvec_only(lgp, ctx, p, args, dev, prec, rank)
+        bench_matvec_only(lgp, ctx, p, args, dev, prec, rank, V_large)
         return
     if args.mode == "predict":
         bench_predict(lgp, ctx, p, args, dev, prec, rank)
@@ -672,12 +680,16 @@ def bench_predict(lgp, ctx, p, args, dev, prec, rank):
                           "prec_used": infos[-1]["prec_used"]}), flush=True)
 
 
-def bench_matvec_only(lgp, ctx, p, args, dev, prec, rank):
-    """Only the product K_y V on the workload (a small, fast command for kernel profiling)."""
+def bench_matvec_only(lgp, ctx, p, args, dev, prec, rank, V_host=None):
+    """Only the product K_y V on the workload (a small, fast command for kernel profiling). Reports the
+    whole call and, from the library's kernel-timing events, the product kernel alone with its binding
+    pipe (the same bounds as the LML line's roofline)."""
     import torch
     import workloads as wl
     X = torch.as_tensor(p.X, device=dev)
-    V = torch.as_tensor(wl.rhs_block(p.N, args.t, seed=3, kind="sign"), device=dev)
+    if V_host is None:
+        V_host = wl.rhs_block(p.N, args.t, seed=3, kind="sign")
+    V = torch.as_tensor(V_host, device=dev)
     out = torch.empty_like(V)
     kprec = ctx.matvec_precision(args.t, prec)
     for _ in range(args.warmup):
@@ -693,9 +705,28 @@ def bench_matvec_only(lgp, ctx, p, args, dev, prec, rank):
         evs.append((a, b))
     torch.cuda.synchronize()
     ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
+    ctx.set_kernel_timing(True)
+    kms = []
+    for _ in range(args.steps):
+        lgp.lgp_kernel_matvec(X, p, V, prec=kprec, out=out, ctx=ctx)
+        kms.append(ctx.last_kernel_ms())
+    ctx.set_kernel_timing(False)
+    kernel_ms = statistics.mean(kms)
+    split = kprec in (lgp.LGP_PREC_SPLIT_BF16, lgp.LGP_PREC_SPLIT_F16)
+    symmetric = split and ctx.tc_kernel_choice(p.N, p.D, p.kind, args.t, kprec) == lgp.LGP_TC_SYMMETRIC
+    form = ctx.tc_distance_form()[0] if symmetric else lgp.LGP_DIST_NONE
+    dot = form == lgp.LGP_DIST_DOT
+    ops_pair, mufu_pair = per_pair_ops(p.kind, p.D, split, args.t, dot)
+    entries = float(p.N) * (p.N + 1) / 2 if symmetric else float(p.N) ** 2
+    bp = binding_pipe(entries, float(p.N) ** 2, ops_pair, mufu_pair, args.t, p.D, split, dot, kernel_ms / 1e3,
+                      torch.cuda.get_device_properties(dev).multi_processor_count, measured_peaks()["bf16_tflops"])
     if rank == 0:
         print(json.dumps({"mode": "matvec", "workload": p.name, "precision": kprec, "ms": ms,
-                          "pair_rhs_per_s": float(p.N) ** 2 * args.t / (ms / 1e3)}), flush=True)
+                          "pair_rhs_per_s": float(p.N) ** 2 * args.t / (ms / 1e3), "kernel_ms": kernel_ms,
+                          "kernel": "mv_tcs_kernel" if symmetric else ("mv_tc_kernel" if split else "mv_simt_kernel"),
+                          "distance_form": {lgp.LGP_DIST_DOT: "dot", lgp.LGP_DIST_DIFF: "difference"}.get(form),
+                          "binding_pipe": bp["binding"], "frac": bp["frac"], "pipe_fracs": bp["pipe_fracs"]}),
+              flush=True)
 
 
 def estimate_plain(lgp, ctx, p, X, y, args, dev, iters, ms_per_step):

@@ -368,7 +368,7 @@ float dot_gate_limit(int kind) {
 
 // LGP_DISTANCE=diff keeps the symmetric product on the difference form.
 bool dot_form_allowed(int kind, int D) {
-    if (dot_gate_limit(kind) <= 0.0f || D < 3) return false;
+    if (dot_gate_limit(kind) <= 0.0f || D < 1) return false;
     const char *env = std::getenv("LGP_DISTANCE");
     return !(env && std::strcmp(env, "diff") == 0);
 }

@@ -34,7 +34,7 @@
 //   warps 18-21 drain: tensor memory -> registers -> staging tile -> TMA reduce-add.
 // Accumulators: two buffers of [out_I (128 columns) | out_J (128 columns)].
 //
-// Dot form (DOT = true; RBF, Matern-3/2, Matern-5/2 at D >= 3, when the data's spread allows):
+// Dot form (DOT = true; RBF, Matern-3/2, Matern-5/2 at any D, when the data's spread allows):
 // r^2 = a_i + a_j - 2 u_i . u_j for the box-centred coordinates u, as one 128 x 128 tensor-core Gram
 // tile per tile whose float16 hi/lo operand rows also carry the squared norms a (built once per X by
 // mv_tc.cu), so the tensor core returns -r^2 and an entry costs the kernel value and the split. CTA: 24 warps:
