@@ -196,3 +196,27 @@ def test_operands_follow_each_new_x(lgp, sym):
         errx = (np.linalg.norm(x.cpu().numpy() - refx, axis=0) / np.linalg.norm(refx, axis=0)).max()
         print(f"product err {err:.2e}; solve err {errx:.2e} (gate {gate:.1e}, iterations {it.max()})")
         assert errx <= gate
+
+
+@pytest.mark.parametrize("N", [1024, 4000])
+def test_dot_form_cg_solve_two_dimensions(lgp, sym, N):
+    """The plain-CG workload's distribution (X ~ U[0,1]^2, RBF, lengthscale 0.2, sigma^2 = 0.01) solved with the
+    split product, whose distances at D = 2 now come from the tensor-core Gram tile: the solution of
+    [y | 15 probes] against the dense Cholesky solution, at the gate that the product's error allows for the
+    problem's condition number (1e-4, or 2e-8 kappa when that is larger)."""
+    import torch
+    p = wl.cfg1(N=N)
+    B = wl.rhs_block(p.N, 16, seed=21)
+    B[:, 0] = p.y
+    Ky = go.noisy_kernel_matrix(p.X, go.hyper_of(p))
+    ev = np.linalg.eigvalsh(Ky)
+    gate = max(1e-4, 2e-8 * ev[-1] / ev[0])
+    ref = go.cholesky_solve(Ky, B.astype(np.float64))
+    x, iters, rel, status = lgp.lgp_cg_solve(torch.as_tensor(p.X, device="cuda"), p,
+                                             torch.as_tensor(B, device="cuda"), tol=1e-6, max_iter=3000,
+                                             prec=lgp.LGP_PREC_SPLIT_F16, ctx=sym)
+    assert status == lgp.LGP_OK and (rel <= 1e-6).all()
+    assert sym.tc_distance_form()[0] == lgp.LGP_DIST_DOT
+    err = np.linalg.norm(x.cpu().numpy() - ref, axis=0) / np.linalg.norm(ref, axis=0)
+    print(f"N={N}: kappa {ev[-1] / ev[0]:.2e}, iterations {iters.max()}, err {err.max():.2e} (gate {gate:.1e})")
+    assert err.max() <= gate
