@@ -169,7 +169,12 @@ const char *lgp_status_string(int32_t status);
  *                       a device-side while loop; meant for profilers;
  *   LGP_DISTANCE=diff   keep the symmetric-tile kernel on the difference form of the squared
  *                       distance (see lgp_tc_distance_form); its results then differ from the
- *                       default dot form by that form's rounding (column errors of a few 1e-6). */
+ *                       default dot form by that form's rounding (column errors of a few 1e-6);
+ *   LGP_TC_BANDS=1      let the symmetric-tile kernel's dot form visit its tiles in column bands
+ *                       whose operands stay in L2 (N above about 157000 at t = 32, 262000 at
+ *                       t = 16): at N = 500000, t = 32 about 1 GB of DRAM traffic per product
+ *                       instead of 115 GB, for a product about 4% slower (measured 68.2 against
+ *                       65.6 ms); for GPUs whose memory bandwidth other work needs meanwhile. */
 
 /* Create a context bound to CUDA device `device` (its workspace starts empty).
  * Returns LGP_ERR_INVALID_ARG for a NULL ctx or a device that does not exist,

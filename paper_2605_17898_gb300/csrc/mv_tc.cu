@@ -350,6 +350,22 @@ int64_t tc_vsplit_bytes(int64_t Np, int t) {
     return 2 * Np * t * 2 + 2 * 64 * 4 + 8 * Np * 4 + 32 * 4 + Np * 4 + 2 * Np * 64;
 }
 
+// Column-band width of the symmetric product's tile order (tile_walk.cuh), in 128-column tiles: a
+// band's column-side operands (the split V rows, 4t bytes each; the B-role Gram operand, 64; and
+// the rows of out its reductions add onto, 4t) take at most 48 MiB, about a third of the 129 MB
+// L2, so that they stay cached while all CTAs sweep the band. Measured at N = 500000, t = 32, the
+// one-band order (every CTA on its own rows across all columns) read 80.6 GB and wrote 34.0 GB of
+// DRAM per product, against about 0.26 GB of operands.
+bool tcs_bands_enabled() {
+    const char *env = std::getenv("LGP_TC_BANDS");
+    return env && std::strcmp(env, "1") == 0;
+}
+
+int tcs_band_tiles(int t) {
+    const int64_t bytes_per_tile = (int64_t)tcs::kTile * (8 * t + 64);
+    return (int)std::max<int64_t>(1, (48ll << 20) / bytes_per_tile);
+}
+
 int64_t tc_dot_gate_offset(int64_t Np, int t) { return 2 * Np * t * 2 + 2 * 64 * 4 + 8 * Np * 4 + 16 * 4; }
 
 // Squared-norm limits of the dot form, per kernel: with a = max_j |u_j|^2 the rounding error of
@@ -511,6 +527,7 @@ cudaError_t launch_mv_tc(const KernelParams &kp, const float *Xs, int64_t N, int
         a.ldo = ldo;
         a.nb = (int)(Np / tcs::kTile);
         a.tiles = (int64_t)a.nb * (a.nb + 1) / 2;
+        a.band = tcs_bands_enabled() ? tcs_band_tiles(t) : a.nb;
         a.log2s2 = fmt == kFmtF16 ? 15.0f : kp.log2_s2;
         a.col_scale = fmt == kFmtF16 ? col_scale : nullptr;
         // the drain's blocks go to out by TMA reduce when out's rows are 16-byte aligned

@@ -10,11 +10,14 @@
 // direction is the same three-product split (K_hi [V_hi V_lo] as one N = 2t MMA, K_lo V_hi as an
 // N = t MMA) into float32 accumulators in tensor memory, drained after every tile (K = 128).
 //
-// Work split: the nb (nb + 1) / 2 tiles of the triangle, numbered row by row, are cut into one
-// contiguous range per CTA (persistent grid of min(SMs, tiles) CTAs, equal tile counts to within
-// one). A CTA's range crosses a few tile rows; within one row, out_I accumulates in the drain
-// warps' registers and is added to HBM when the row ends, while out_J is added after every
-// tile. Both additions are float32 adds onto out, which the V-splitting kernel initialised to
+// Work split (tile_walk.cuh): the nb (nb + 1) / 2 tiles of the triangle, numbered row by row within
+// column bands of W tiles, are cut into one contiguous range per CTA and band (persistent grid of
+// min(SMs, tiles) CTAs, equal tile counts to within one per band). W keeps a band's column-side
+// operands within a share of L2, so that every CTA sweeping the same band reuses them; at the
+// sizes where they fit L2 whole (N up to about 157000 at t = 32, 262000 at t = 16) there is one
+// band. A CTA's range
+// crosses a few tile rows; within one row segment, out_I accumulates in the drain warps'
+// registers and is added to HBM when the segment ends, while out_J is added after every tile. Both additions are float32 adds onto out, which the V-splitting kernel initialised to
 // sigma^2 V: the drain writes the 128 x t block to a swizzled shared-memory tile and one thread
 // hands it to the TMA unit as a bulk tensor reduce-add (cp.reduce.async.bulk.tensor), so the
 // drain warps release the accumulator after their tensor-memory reads alone. (Outputs whose rows
@@ -51,6 +54,7 @@
 #include <type_traits>
 
 #include "mv_tc.cuh"
+#include "tile_walk.cuh"
 
 namespace lgp {
 namespace tcs {
@@ -148,30 +152,6 @@ __device__ __forceinline__ uint32_t instr_desc_amn() {
     return tc::instr_desc<NCOLS, FMT>() | (1u << 15);
 }
 
-// Tile number -> (I, J) in the row-by-row numbering of the upper triangle; first tile of row I
-// is I nb - I (I - 1) / 2.
-struct TileWalk {
-    int nb, I, J;
-    __device__ __forceinline__ static int64_t row_start(int64_t I, int64_t nb) { return I * nb - I * (I - 1) / 2; }
-    __device__ __forceinline__ void init(int64_t t0, int nb_) {
-        nb = nb_;
-        int lo = 0, hi = nb - 1;  // largest I with row_start(I) <= t0
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (row_start(mid, nb) <= t0) lo = mid;
-            else hi = mid - 1;
-        }
-        I = lo;
-        J = I + (int)(t0 - row_start(I, nb));
-    }
-    __device__ __forceinline__ void next() {
-        if (++J == nb) {
-            ++I;
-            J = I;
-        }
-    }
-};
-
 struct TcsArgs {
     const float *Xs;         // prescaled x [Np, DP] row-major (x_I rows for the generation threads)
     float *out;              // [N, ldo], holds sigma^2 V on entry
@@ -180,6 +160,7 @@ struct TcsArgs {
     int64_t N, Np, ldo;
     int nb;                  // Np / 128
     int64_t tiles;           // nb (nb + 1) / 2
+    int band;                // column-band width of the tile order, in tiles (tile_walk.cuh)
     float log2s2;            // exponent offset of the entries: log2 s^2 (bf16) or 15 (f16)
     const float *col_scale;  // [T] multiplier per column (f16 mode), or nullptr
     int add_mode;            // kAddTma (tm_out is valid), kAddVec4 or kAddScalar
@@ -335,8 +316,10 @@ __device__ __forceinline__ void split_pair(float2 k, uint32_t &h, uint32_t &l) {
 // The dot form's three issuers poll their barriers without a back-off sleep (measured ~0.5% faster
 // than a 32 ns sleep between polls).
 //
-// DOT selects the dot form of the squared distance (D is then 4 or 8, the padded width DP).
-template <int KIND, int D, int T, int FMT, bool DOT = false>
+// DOT selects the dot form of the squared distance (D is then 4 or 8, the padded width DP). BANDED
+// selects the banded tile order (tile_walk.cuh); the instance without it walks the single-band
+// order in fewer registers.
+template <int KIND, int D, int T, int FMT, bool DOT = false, bool BANDED = false>
 __global__ void __launch_bounds__(DOT ? kDotThreads : kThreads, 1)
     mv_tcs_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ CUtensorMap tm_v,
                   const __grid_constant__ CUtensorMap tm_out, const TcsArgs a) {
@@ -353,9 +336,9 @@ __global__ void __launch_bounds__(DOT ? kDotThreads : kThreads, 1)
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int64_t t0 = (int64_t)blockIdx.x * a.tiles / gridDim.x;
-    const int64_t t1 = (int64_t)(blockIdx.x + 1) * a.tiles / gridDim.x;
-    const int n_it = (int)(t1 - t0);
+    using Walk = std::conditional_t<BANDED, TileWalk, RowWalk>;
+    const TileOrder ord = tile_order(a.nb, BANDED ? a.band : a.nb, (int)blockIdx.x, (int)gridDim.x);
+    const int n_it = (int)Walk::count(ord);
 
     // bars: full[2], ready[2], empty[2], acc_full[2], acc_empty[2], vi_full[2], vi_empty[2], fin
     auto bar_full = [&](int s) { return smem_u32(&bars[s]); };
@@ -419,8 +402,8 @@ __global__ void __launch_bounds__(DOT ? kDotThreads : kThreads, 1)
     tc_fence_after();
     const uint32_t tmem_acc = *tmem_slot;
 
-    TileWalk w;
-    w.init(t0, a.nb);
+    Walk w;
+    w.init(ord);
 
     if (warp == kProducerWarp) {
         if constexpr (DOT) {
@@ -431,8 +414,8 @@ __global__ void __launch_bounds__(DOT ? kDotThreads : kThreads, 1)
                 int last_v[2] = {-1, -1};
                 int last_sg = -1;
                 int sg = -1;
-                for (int it = 0; it < n_it; ++it, w.next()) {
-                    if (it == 0 || w.J == w.I) {
+                for (int it = 0; it < n_it; ++it, w.next(ord)) {
+                    if (w.first) {
                         ++sg;
                         if (sg >= 1 &&
                             !mbar_wait(bar_vi_empty(0), (sg - 1) & 1, a.budget, abort_flag, a.err, kErrWaitVi, 64))
@@ -462,7 +445,7 @@ __global__ void __launch_bounds__(DOT ? kDotThreads : kThreads, 1)
                 }
             } else if (lane == 1) {
                 int last_u[2] = {-1, -1};
-                for (int it = 0; it < n_it; ++it, w.next()) {
+                for (int it = 0; it < n_it; ++it, w.next(ord)) {
                     const int s = it & 1;
                     if (it >= 2 &&
                         !mbar_wait(bar_u_empty(s), ((it >> 1) - 1) & 1, a.budget, abort_flag, a.err, kErrWaitEmpty, 64))
@@ -484,8 +467,8 @@ __global__ void __launch_bounds__(DOT ? kDotThreads : kThreads, 1)
                 int last_it[kStages] = {-1, -1};
                 int last_sg[2] = {-1, -1};
                 int sg = -1;
-                for (int it = 0; it < n_it; ++it, w.next()) {
-                    if (it == 0 || w.J == w.I) {
+                for (int it = 0; it < n_it; ++it, w.next(ord)) {
+                    if (w.first) {
                         // new tile row: V_I [hi; lo] (two 64-row chunks) into slot sg & 1
                         ++sg;
                         const int b = sg & 1;
@@ -575,11 +558,10 @@ __global__ void __launch_bounds__(DOT ? kDotThreads : kThreads, 1)
                 bool issued = false;
                 int sg = -1;
                 for (int it = 0; it < n_it; ++it) {
-                    const bool seg_first = it == 0 || w.J == w.I;
+                    const bool seg_first = w.first;
                     const bool diag = w.J == w.I;
-                    const int I = w.I;
-                    w.next();
-                    const bool seg_last = it == n_it - 1 || w.I != I;
+                    w.next(ord);
+                    const bool seg_last = it == n_it - 1 || w.first;
                     if (seg_first) ++sg;
                     const int s = it % kStages;
                     const int buf = it & 1;
@@ -640,7 +622,7 @@ __global__ void __launch_bounds__(DOT ? kDotThreads : kThreads, 1)
             const int rloc = 32 * q + lane;
             const uint32_t taddr = tmem_acc + ((uint32_t)(32 * q) << 16) + (uint32_t)(L::kGramCol + 32 * cb);
             const float ls2 = a.log2s2;
-            for (int it = 0; it < n_it; ++it, w.next()) {
+            for (int it = 0; it < n_it; ++it) {  // (the tile order is not needed here)
                 // Gram tile it (buffer it & 1), and entry buffer it & 1 released by both issuers'
                 // products of tile it - 2
                 bool got = mbar_wait(bar_gram_full(it & 1), (it >> 1) & 1, a.budget, abort_flag, a.err, kErrWaitGram);
@@ -682,8 +664,8 @@ __global__ void __launch_bounds__(DOT ? kDotThreads : kThreads, 1)
             const float2 ls2 = make_float2(a.log2s2, a.log2s2);
             const float2 acc_init = tc::Entry2<KIND>::acc0(ls2);
             float2 xi2[2][D];
-            for (int it = 0; it < n_it; ++it, w.next()) {
-                if (it == 0 || w.J == w.I) {
+            for (int it = 0; it < n_it; ++it, w.next(ord)) {
+                if (w.first) {
                     // this thread's 2 rows of tile row I, each coordinate duplicated into both halves of
                     // a float2 (rows < Np because Np % 128 == 0)
     #pragma unroll
@@ -769,11 +751,10 @@ __global__ void __launch_bounds__(DOT ? kDotThreads : kThreads, 1)
                 bool issued = false;
                 int sg = -1;
                 for (int it = 0; it < n_it; ++it) {
-                    const bool seg_first = it == 0 || w.J == w.I;
+                    const bool seg_first = w.first;
                     const bool diag = w.J == w.I;
-                    const int I = w.I;
-                    w.next();
-                    const bool seg_last = it == n_it - 1 || w.I != I;
+                    w.next(ord);
+                    const bool seg_last = it == n_it - 1 || w.first;
                     if (seg_first) ++sg;
                     const int s = it & 1;
                     const int buf = it % NB;
@@ -819,10 +800,9 @@ __global__ void __launch_bounds__(DOT ? kDotThreads : kThreads, 1)
                 bool issued = false;
                 int sg = -1;
                 for (int k = 0; k < n_it; ++k) {
-                    const bool seg_first = k == 0 || w.J == w.I;
-                    const int I = w.I;
-                    w.next();
-                    const bool seg_last = k == n_it - 1 || w.I != I;
+                    const bool seg_first = w.first;
+                    w.next(ord);
+                    const bool seg_last = k == n_it - 1 || w.first;
                     if (seg_first) ++sg;
                     const int b = k & 1;  // Gram buffer and U_J ring slot
                     if (k >= 2 &&
@@ -878,8 +858,8 @@ __global__ void __launch_bounds__(DOT ? kDotThreads : kThreads, 1)
         for (int it = 0; it < n_it; ++it) {
             const bool diag = w.J == w.I;
             const int I = w.I, J = w.J;
-            w.next();
-            const bool seg_last = it == n_it - 1 || w.I != I;
+            w.next(ord);
+            const bool seg_last = it == n_it - 1 || w.first;
             const int buf = it % NB;
             const bool got = mbar_wait(bar_acc_full(buf), (it / NB) & 1, a.budget, abort_flag, a.err, kErrWaitAcc, 128);
             if (!drain_all(got)) break;

@@ -7,7 +7,7 @@
 namespace lgp {
 namespace tcs {
 
-template <int KIND, int D, int T, int FMT, bool DOT = false>
+template <int KIND, int D, int T, int FMT, bool DOT = false, bool BANDED = false>
 cudaError_t launch_tcs_inst(dim3 grid, const CUtensorMap &mx, const CUtensorMap &mv, const CUtensorMap &mo,
                             const TcsArgs &a,
                             cudaStream_t st) {
@@ -15,16 +15,26 @@ cudaError_t launch_tcs_inst(dim3 grid, const CUtensorMap &mx, const CUtensorMap 
     constexpr int bytes = DOT ? TcdLayout<T, DP>::kBytes : TcsLayout<T, DP>::kBytes;
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(mv_tcs_kernel<KIND, D, T, FMT, DOT>,
+        cudaError_t e = cudaFuncSetAttribute(mv_tcs_kernel<KIND, D, T, FMT, DOT, BANDED>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    mv_tcs_kernel<KIND, D, T, FMT, DOT><<<grid, DOT ? kDotThreads : kThreads, bytes, st>>>(mx, mv, mo, a);
+    mv_tcs_kernel<KIND, D, T, FMT, DOT, BANDED><<<grid, DOT ? kDotThreads : kThreads, bytes, st>>>(mx, mv, mo, a);
     return cudaGetLastError();
 }
 
-// Dot-form instances exist for RBF, Matern-5/2 and Matern-3/2 at the padded widths 4 and 8.
+// The dot-form instance: the banded tile order when the band is narrower than the triangle
+// (TcsArgs::band < nb), else the single-band one.
+template <int KIND, int DP, int T, int FMT>
+cudaError_t launch_tcs_dot(dim3 grid, const CUtensorMap &mx, const CUtensorMap &mv, const CUtensorMap &mo,
+                           const TcsArgs &a, cudaStream_t st) {
+    return a.band < a.nb ? launch_tcs_inst<KIND, DP, T, FMT, true, true>(grid, mx, mv, mo, a, st)
+                         : launch_tcs_inst<KIND, DP, T, FMT, true, false>(grid, mx, mv, mo, a, st);
+}
+
+// Dot-form instances exist for RBF, Matern-5/2 and Matern-3/2 at the padded widths 4 and 8, each with
+// and without the banded tile order. The difference form walks the single-band order at every size.
 template <int KIND>
 constexpr bool has_dot_form() { return KIND == LGP_RBF || KIND == LGP_MATERN52 || KIND == LGP_MATERN32; }
 
@@ -54,10 +64,10 @@ cudaError_t dispatch_kind(int D, int T, dim3 grid, const CUtensorMap &mx, const 
         if constexpr (has_dot_form<KIND>()) {
             if (D < 1 || D > 8) return cudaErrorInvalidValue;
             if (D <= 4)
-                return T == 16 ? launch_tcs_inst<KIND, 4, 16, FMT, true>(grid, mx, mv, mo, a, st)
-                               : launch_tcs_inst<KIND, 4, 32, FMT, true>(grid, mx, mv, mo, a, st);
-            return T == 16 ? launch_tcs_inst<KIND, 8, 16, FMT, true>(grid, mx, mv, mo, a, st)
-                           : launch_tcs_inst<KIND, 8, 32, FMT, true>(grid, mx, mv, mo, a, st);
+                return T == 16 ? launch_tcs_dot<KIND, 4, 16, FMT>(grid, mx, mv, mo, a, st)
+                               : launch_tcs_dot<KIND, 4, 32, FMT>(grid, mx, mv, mo, a, st);
+            return T == 16 ? launch_tcs_dot<KIND, 8, 16, FMT>(grid, mx, mv, mo, a, st)
+                           : launch_tcs_dot<KIND, 8, 32, FMT>(grid, mx, mv, mo, a, st);
         }
         return cudaErrorInvalidValue;
     }

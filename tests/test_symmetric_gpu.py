@@ -109,6 +109,35 @@ def test_symmetric_full_size_cfg3_sampled_rows(lgp, sym):
     assert _colerr(got[rows], ref).max() <= TOL
 
 
+@pytest.mark.parametrize("t", [16, 32])
+@pytest.mark.parametrize("kind", [wl.RBF, wl.MATERN52])
+def test_banded_tile_order(lgp, sym, kind, t):
+    """LGP_TC_BANDS=1: the dot-form product walks the triangle in column bands (48 MiB of column-side
+    operands each: 1228 tiles at t = 32, 2048 at t = 16), so N = 280000 (2188 tiles a side) takes two
+    bands with a narrow second one. Sampled rows against the FP64 row oracle at the product gate, and
+    the whole result against the single-band order (the two differ only in the order of the float32
+    additions onto out). Lengthscales in [0.1, 0.3] keep the draw inside the dot form's gate and its
+    cancellation (sum_j |k_ij v_j| over |(K v)_i|, below ~400 on sampled rows) below that of the
+    N = 500000 workload, whose product meets the same gate."""
+    import torch
+    p = wl.random_problem(280000, 3, kind, seed=280 + t + kind, lo=0.1, hi=0.3)
+    V = wl.rhs_block(p.N, t, seed=t)
+    one = _run(lgp, sym, p, V, lgp.LGP_PREC_SPLIT_F16)
+    os.environ["LGP_TC_BANDS"] = "1"
+    try:
+        banded = _run(lgp, sym, p, V, lgp.LGP_PREC_SPLIT_F16)
+    finally:
+        os.environ.pop("LGP_TC_BANDS", None)
+    assert sym.tc_distance_form()[0] == lgp.LGP_DIST_DOT
+    rows = np.random.default_rng(3).choice(p.N, 96, replace=False)
+    ref, _ = oracle.kyv_rows_c(p.X, V, go.hyper_of(p), rows=rows)
+    err = _colerr(banded[rows], ref).max()
+    diff = _colerr(banded, one.astype(np.float64)).max()
+    print(f"banded kind={kind} t={t}: sampled-row err {err:.2e}, against the single-band order {diff:.2e}")
+    assert err <= TOL
+    assert diff <= TOL
+
+
 def test_symmetric_agrees_with_row_kernel(lgp):
     """The two tensor-core kernels give the same product to the split error level, and repeated
     symmetric products agree to float32 summation-order level."""
