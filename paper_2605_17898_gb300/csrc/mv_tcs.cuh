@@ -15,9 +15,9 @@
 // min(SMs, tiles) CTAs, equal tile counts to within one per band). W keeps a band's column-side
 // operands within a share of L2, so that every CTA sweeping the same band reuses them; at the
 // sizes where they fit L2 whole (N up to about 157000 at t = 32, 262000 at t = 16) there is one
-// band. A CTA's range
-// crosses a few tile rows; within one row segment, out_I accumulates in the drain warps'
-// registers and is added to HBM when the segment ends, while out_J is added after every tile. Both additions are float32 adds onto out, which the V-splitting kernel initialised to
+// band. A CTA's range crosses a few tile rows; within one row segment, out_I accumulates in the
+// drain warps' registers and is added to HBM when the segment ends, while out_J is added after
+// every tile. Both additions are float32 adds onto out, which the V-splitting kernel initialised to
 // sigma^2 V: the drain writes the 128 x t block to a swizzled shared-memory tile and one thread
 // hands it to the TMA unit as a bulk tensor reduce-add (cp.reduce.async.bulk.tensor), so the
 // drain warps release the accumulator after their tensor-memory reads alone. (Outputs whose rows
@@ -316,6 +316,15 @@ __device__ __forceinline__ void split_pair(float2 k, uint32_t &h, uint32_t &l) {
 // The dot form's three issuers poll their barriers without a back-off sleep (measured ~0.5% faster
 // than a 32 ns sleep between polls).
 //
+// The dot-form generation reads nothing of the tile order. The single-band instance steps its walk
+// there all the same: a version without that step (and with the segment flag kept per thread)
+// allocated its registers differently and measured 2.99 against 2.94 ms at N = 100000, t = 32. The
+// banded instance leaves the step out, which saves it spills.
+template <bool STEP, class Walk>
+__device__ __forceinline__ void step_unread(Walk &w, const TileOrder &o) {
+    if constexpr (STEP) w.next(o);
+}
+
 // DOT selects the dot form of the squared distance (D is then 4 or 8, the padded width DP). BANDED
 // selects the banded tile order (tile_walk.cuh); the instance without it walks the single-band
 // order in fewer registers.
@@ -415,7 +424,7 @@ __global__ void __launch_bounds__(DOT ? kDotThreads : kThreads, 1)
                 int last_sg = -1;
                 int sg = -1;
                 for (int it = 0; it < n_it; ++it, w.next(ord)) {
-                    if (w.first) {
+                    if (w.starts_segment(it)) {
                         ++sg;
                         if (sg >= 1 &&
                             !mbar_wait(bar_vi_empty(0), (sg - 1) & 1, a.budget, abort_flag, a.err, kErrWaitVi, 64))
@@ -468,7 +477,7 @@ __global__ void __launch_bounds__(DOT ? kDotThreads : kThreads, 1)
                 int last_sg[2] = {-1, -1};
                 int sg = -1;
                 for (int it = 0; it < n_it; ++it, w.next(ord)) {
-                    if (w.first) {
+                    if (w.starts_segment(it)) {
                         // new tile row: V_I [hi; lo] (two 64-row chunks) into slot sg & 1
                         ++sg;
                         const int b = sg & 1;
@@ -558,10 +567,11 @@ __global__ void __launch_bounds__(DOT ? kDotThreads : kThreads, 1)
                 bool issued = false;
                 int sg = -1;
                 for (int it = 0; it < n_it; ++it) {
-                    const bool seg_first = w.first;
+                    const bool seg_first = w.starts_segment(it);
                     const bool diag = w.J == w.I;
+                    const int I = w.I;
                     w.next(ord);
-                    const bool seg_last = it == n_it - 1 || w.first;
+                    const bool seg_last = it == n_it - 1 || w.segment_changed(I);
                     if (seg_first) ++sg;
                     const int s = it % kStages;
                     const int buf = it & 1;
@@ -622,7 +632,7 @@ __global__ void __launch_bounds__(DOT ? kDotThreads : kThreads, 1)
             const int rloc = 32 * q + lane;
             const uint32_t taddr = tmem_acc + ((uint32_t)(32 * q) << 16) + (uint32_t)(L::kGramCol + 32 * cb);
             const float ls2 = a.log2s2;
-            for (int it = 0; it < n_it; ++it) {  // (the tile order is not needed here)
+            for (int it = 0; it < n_it; ++it, step_unread<!BANDED>(w, ord)) {
                 // Gram tile it (buffer it & 1), and entry buffer it & 1 released by both issuers'
                 // products of tile it - 2
                 bool got = mbar_wait(bar_gram_full(it & 1), (it >> 1) & 1, a.budget, abort_flag, a.err, kErrWaitGram);
@@ -665,7 +675,7 @@ __global__ void __launch_bounds__(DOT ? kDotThreads : kThreads, 1)
             const float2 acc_init = tc::Entry2<KIND>::acc0(ls2);
             float2 xi2[2][D];
             for (int it = 0; it < n_it; ++it, w.next(ord)) {
-                if (w.first) {
+                if (w.starts_segment(it)) {
                     // this thread's 2 rows of tile row I, each coordinate duplicated into both halves of
                     // a float2 (rows < Np because Np % 128 == 0)
     #pragma unroll
@@ -751,10 +761,11 @@ __global__ void __launch_bounds__(DOT ? kDotThreads : kThreads, 1)
                 bool issued = false;
                 int sg = -1;
                 for (int it = 0; it < n_it; ++it) {
-                    const bool seg_first = w.first;
+                    const bool seg_first = w.starts_segment(it);
                     const bool diag = w.J == w.I;
+                    const int I = w.I;
                     w.next(ord);
-                    const bool seg_last = it == n_it - 1 || w.first;
+                    const bool seg_last = it == n_it - 1 || w.segment_changed(I);
                     if (seg_first) ++sg;
                     const int s = it & 1;
                     const int buf = it % NB;
@@ -800,9 +811,10 @@ __global__ void __launch_bounds__(DOT ? kDotThreads : kThreads, 1)
                 bool issued = false;
                 int sg = -1;
                 for (int k = 0; k < n_it; ++k) {
-                    const bool seg_first = w.first;
+                    const bool seg_first = w.starts_segment(k);
+                    const int I = w.I;
                     w.next(ord);
-                    const bool seg_last = k == n_it - 1 || w.first;
+                    const bool seg_last = k == n_it - 1 || w.segment_changed(I);
                     if (seg_first) ++sg;
                     const int b = k & 1;  // Gram buffer and U_J ring slot
                     if (k >= 2 &&
@@ -859,7 +871,7 @@ __global__ void __launch_bounds__(DOT ? kDotThreads : kThreads, 1)
             const bool diag = w.J == w.I;
             const int I = w.I, J = w.J;
             w.next(ord);
-            const bool seg_last = it == n_it - 1 || w.first;
+            const bool seg_last = it == n_it - 1 || w.segment_changed(I);
             const int buf = it % NB;
             const bool got = mbar_wait(bar_acc_full(buf), (it / NB) & 1, a.budget, abort_flag, a.err, kErrWaitAcc, 128);
             if (!drain_all(got)) break;

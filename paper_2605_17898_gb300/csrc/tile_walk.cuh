@@ -98,6 +98,17 @@ struct TileWalk {
         enter_band(o);
     }
 
+    // whether tile `it` of the walk starts a segment; after next(), whether the tile just left ended one
+    // (prev_I: its row)
+    LGP_TW_FN bool starts_segment(int it) const {
+        (void)it;
+        return first;
+    }
+    LGP_TW_FN bool segment_changed(int prev_I) const {
+        (void)prev_I;
+        return first;
+    }
+
     LGP_TW_FN void next(const TileOrder &o) {
         if (band >= o.nbands) return;
         if (--left == 0) {
@@ -128,37 +139,35 @@ struct TileWalk {
 };
 
 // The same order with a single band (the row-by-row numbering of the whole triangle, cut into one
-// contiguous range per CTA), kept in fewer registers: the kernel instance that never needs a second
-// band walks with this one.
+// contiguous range per CTA), in fewer registers: a segment is then a tile row, so its start and end
+// follow from (I, J) alone. The kernel instance that never needs a second band walks with this one.
 struct RowWalk {
-    int I, J;
-    bool first;
+    int nb, I, J;
 
     LGP_TW_FN static int64_t row_start(int64_t I, int64_t nb) { return I * nb - I * (I - 1) / 2; }
 
     LGP_TW_FN void init(const TileOrder &o) {
-        const int64_t T = band_tiles(0, o.nb);
-        const int64_t t0 = (int64_t)o.cta * T / o.ncta;
-        int lo = 0, hi = o.nb - 1;  // largest I with row_start(I) <= t0
+        nb = o.nb;
+        const int64_t t0 = (int64_t)o.cta * band_tiles(0, o.nb) / o.ncta;
+        int lo = 0, hi = nb - 1;  // largest I with row_start(I) <= t0
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (row_start(mid, o.nb) <= t0) lo = mid;
+            if (row_start(mid, nb) <= t0) lo = mid;
             else hi = mid - 1;
         }
         I = lo;
-        J = I + (int)(t0 - row_start(I, o.nb));
-        first = true;
+        J = I + (int)(t0 - row_start(I, nb));
     }
 
-    LGP_TW_FN void next(const TileOrder &o) {
-        if (++J == o.nb) {
+    LGP_TW_FN void next(const TileOrder &) {
+        if (++J == nb) {
             ++I;
             J = I;
-            first = true;
-        } else {
-            first = false;
         }
     }
+
+    LGP_TW_FN bool starts_segment(int it) const { return it == 0 || J == I; }
+    LGP_TW_FN bool segment_changed(int prev_I) const { return I != prev_I; }
 
     LGP_TW_FN static int64_t count(const TileOrder &o) {
         const int64_t T = band_tiles(0, o.nb);

@@ -43,12 +43,21 @@ int main(int argc, char **argv) {
             if (J < w.band * o.W || J >= lgp::tcs::band_end(o, w.band * o.W)) return fail("tile outside its band", c, it);
             if (seen[(size_t)I * nb + J]++) return fail("tile visited twice", c, it);
             const bool expect_first = it == 0 || w.band != prevBand || I != prevI;
-            if (w.first != expect_first) return fail("segment start flag", c, it);
+            if (w.first != expect_first || w.starts_segment((int)it) != expect_first)
+                return fail("segment start flag", c, it);
             per_band[(size_t)w.band * ncta + c] += 1;
             if (Wc >= nb) {
                 // one band: the single-band walk takes the same steps
-                if (rw.I != I || rw.J != J || rw.first != w.first) return fail("single-band walk differs", c, it);
+                if (rw.I != I || rw.J != J || rw.starts_segment((int)it) != expect_first)
+                    return fail("single-band walk differs", c, it);
                 rw.next(o);
+                // after the step, both walks tell whether the tile just left ended its segment
+                if (it + 1 < n) {
+                    TileWalk ahead = w;
+                    ahead.next(o);
+                    if (rw.segment_changed(I) != ahead.segment_changed(I))
+                        return fail("single-band walk: segment end", c, it);
+                }
                 // and the tile index is the row-by-row numbering of the whole triangle
                 const long long idx = (long long)I * nb - (long long)I * (I - 1) / 2 + (J - I);
                 const long long t0 = (long long)c * total / ncta;
