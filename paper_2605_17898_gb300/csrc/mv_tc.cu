@@ -350,17 +350,19 @@ int64_t tc_vsplit_bytes(int64_t Np, int t) {
     return 2 * Np * t * 2 + 2 * 64 * 4 + 8 * Np * 4 + 32 * 4 + Np * 4 + 2 * Np * 64;
 }
 
-// Column-band width of the symmetric product's tile order (tile_walk.cuh), in 128-column tiles: a
-// band's column-side operands (the split V rows, 4t bytes each; the B-role Gram operand, 64; and
-// the rows of out its reductions add onto, 4t) take at most 48 MiB, about a third of the 129 MB
-// L2, so that they stay cached while all CTAs sweep the band. Measured at N = 500000, t = 32, the
-// one-band order (every CTA on its own rows across all columns) read 80.6 GB and wrote 34.0 GB of
-// DRAM per product, against about 0.26 GB of operands.
+// LGP_TC_BANDS=1 lets the dot-form symmetric product walk its tiles in column bands (tile_walk.cuh).
+// Measured at N = 500000, t = 32: the one-band order (every CTA on its own rows across all columns)
+// read 80.6 GB and wrote 34.0 GB of DRAM per product, against about 0.26 GB of operands, and took
+// 65.6 ms; the banded order moved 0.96 GB and took 68.2 ms (its walk costs registers in a kernel at
+// its register limit). So the default keeps the single band.
 bool tcs_bands_enabled() {
     const char *env = std::getenv("LGP_TC_BANDS");
     return env && std::strcmp(env, "1") == 0;
 }
 
+// Column-band width in 128-column tiles: a band's column-side operands (the split V rows, 4t bytes
+// each; the B-role Gram operand, 64; and the rows of out its reductions add onto, 4t) take at most
+// 48 MiB, about a third of the 129 MB L2, so that they stay cached while all CTAs sweep the band.
 int tcs_band_tiles(int t) {
     const int64_t bytes_per_tile = (int64_t)tcs::kTile * (8 * t + 64);
     return (int)std::max<int64_t>(1, (48ll << 20) / bytes_per_tile);
