@@ -207,8 +207,8 @@ int32_t lgp_tc_kernel_choice(const lgp_ctx *ctx, int64_t N, int32_t D, int32_t k
  * form takes r^2 = |u_i|^2 + |u_j|^2 - 2 u_i . u_j for the box-centred coordinates u, with the
  * inner products on the tensor cores (split float16 operands, float32 accumulation; Sec. 3 names
  * this rewriting of the distance as the reason its product time barely depends on D). The dot
- * form is used for RBF, Matern-3/2 and Matern-5/2 at every D when max_j |u_j|^2 stays below a
- * per-kernel limit that bounds its rounding error; otherwise, for Matern-1/2, or with
+ * form is used for RBF, Matern-3/2 and Matern-5/2 at D >= 2 when max_j |u_j|^2 stays below a
+ * per-kernel limit that bounds its rounding error; otherwise, for Matern-1/2, D = 1, or with
  * LGP_DISTANCE=diff in the environment, the difference form runs.
  * *form receives LGP_DIST_NONE (no symmetric product yet), LGP_DIST_DIFF or LGP_DIST_DOT;
  * *norm_max (may be NULL) the measured max_j |u_j|^2 when the dot form was considered, else -1.
