@@ -59,3 +59,17 @@ def test_dot_form_rbf_is_tensor_bound(bench):
     r = _cfg3(bench, 5.0, {"ex2": 1.0, "sqrt": 0.0}, True, 2.93e-3)
     assert r["binding"] == "tensor"
     assert r["tensor_flops"] == pytest.approx(1e10 * 6 * 32 + 5.00005e9 * 64, rel=1e-12)
+
+
+def test_low_dimension_gram_tile_counts_its_full_width(bench):
+    """The Gram operand rows are 32 values wide at every D (3 x 4 split coordinates and 6 norm and
+    unit columns need more than 16 at D <= 4), so the Gram tile costs 64 flops per entry at D = 2 as
+    at D = 8. The N = 500000, D = 2, t = 32 RBF product's line (65.5735 ms kernel) reported the tensor
+    pipe at 0.4526 of the 1887 TFLOP/s burst."""
+    N = 500000
+    e = N * (N + 1) / 2
+    r = bench.binding_pipe(e, float(N) ** 2, 5.0, {"ex2": 1.0, "sqrt": 0.0}, 32, 2, True, True,
+                           65.57327270507812e-3, 152, 1887.0)
+    assert r["binding"] == "tensor"
+    assert r["tensor_flops"] == pytest.approx(float(N) ** 2 * 6 * 32 + e * 64, rel=1e-12)
+    assert r["frac"] == pytest.approx(0.45257, rel=1e-4)
